@@ -1,0 +1,103 @@
+"""Structured meshes and their face connectivity.
+
+Faces are deduplicated by their sorted vertex tuple.  Face ids are assigned in
+order of first appearance when elements are visited in order and, within an
+element, local faces in order; so the first element of a face (e1) always has
+the smaller element id.  This gives the maps the assembly needs: f(e, l)
+(elem_face) and face -> (e1, l1, e2, l2) (face_elem), as described for the
+face-based assembly and for the ASM update (Welter & Nguyen, Sec. 4.2, 4.6).
+"""
+from dataclasses import dataclass
+import numpy as np
+
+from .basis import hex_face_vertices, TRI_EDGES
+
+
+@dataclass
+class Mesh:
+    dim: int
+    kind: str                   # 'tri' or 'hex'
+    verts: np.ndarray           # (NV, dim)
+    elems: np.ndarray           # (NE, 3) or (NE, 8) vertex ids
+    elem_face: np.ndarray       # (NE, nlfe) int32 global face id
+    face_elem: np.ndarray       # (NF, 4) int32: e1, l1, e2, l2 (e2 = l2 = -1 on the boundary)
+    face_boundary: np.ndarray   # (NF,) uint8
+
+    @property
+    def n_elem(self):
+        return self.elems.shape[0]
+
+    @property
+    def n_face(self):
+        return self.face_elem.shape[0]
+
+    @property
+    def n_lfe(self):
+        return self.elem_face.shape[1]
+
+
+def _build_faces(local_face_verts, elems):
+    ne = elems.shape[0]
+    nlfe = len(local_face_verts)
+    elem_face = np.empty((ne, nlfe), np.int32)
+    key_to_face = {}
+    face_elem = []
+    for e in range(ne):
+        for l, lv in enumerate(local_face_verts):
+            key = tuple(sorted(int(elems[e, v]) for v in lv))
+            f = key_to_face.get(key)
+            if f is None:
+                f = len(face_elem)
+                key_to_face[key] = f
+                face_elem.append([e, l, -1, -1])
+            else:
+                assert face_elem[f][2] == -1, "face shared by more than two elements"
+                face_elem[f][2] = e
+                face_elem[f][3] = l
+            elem_face[e, l] = f
+    face_elem = np.array(face_elem, np.int32)
+    boundary = (face_elem[:, 2] < 0).astype(np.uint8)
+    return elem_face, face_elem, boundary
+
+
+def tri_mesh(n):
+    """Unit square with n x n squares, each split along the diagonal from
+    (x_i, y_j) to (x_{i+1}, y_{j+1}) into two counter-clockwise triangles."""
+    xs = np.linspace(0.0, 1.0, n + 1)
+    verts = np.array([[xs[i], xs[j]] for j in range(n + 1) for i in range(n + 1)])
+    vid = lambda i, j: j * (n + 1) + i
+    elems = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            elems.append([a, b, c])
+            elems.append([a, c, d])
+    elems = np.array(elems, np.int64)
+    ef, fe, fb = _build_faces([list(e) for e in TRI_EDGES], elems)
+    return Mesh(2, 'tri', verts, elems, ef, fe, fb)
+
+
+def hex_mesh(n, perturb=0.0, seed=None):
+    """n^3 hexahedra on [0,1]^3.  With perturb > 0, every interior vertex moves
+    by perturb * h * r * s, s a uniform random unit vector and r ~ U[0,1]
+    (seeded); boundary vertices stay fixed."""
+    xs = np.linspace(0.0, 1.0, n + 1)
+    h = 1.0 / n
+    verts = np.array([[xs[i], xs[j], xs[l]] for l in range(n + 1) for j in range(n + 1) for i in range(n + 1)])
+    if perturb > 0.0:
+        rng = np.random.default_rng(seed)
+        nv = verts.shape[0]
+        s = rng.normal(size=(nv, 3))
+        s /= np.linalg.norm(s, axis=1, keepdims=True)
+        r = rng.uniform(0.0, 1.0, size=(nv, 1))
+        interior = np.all((verts > 1e-12) & (verts < 1 - 1e-12), axis=1)
+        verts = verts + (perturb * h * r * s) * interior[:, None]
+    vid = lambda i, j, l: (l * (n + 1) + j) * (n + 1) + i
+    elems = []
+    for l in range(n):
+        for j in range(n):
+            for i in range(n):
+                elems.append([vid(i + di, j + dj, l + dl) for dl in (0, 1) for dj in (0, 1) for di in (0, 1)])
+    elems = np.array(elems, np.int64)
+    ef, fe, fb = _build_faces([hex_face_vertices(l) for l in range(6)], elems)
+    return Mesh(3, 'hex', verts, elems, ef, fe, fb)

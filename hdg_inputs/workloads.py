@@ -1,0 +1,195 @@
+"""The named synthetic workloads, with their seeds.
+
+  tri_poisson     : unit square, n x n squares split into 2n^2 triangles, P^k,
+                    tau = 1, u = sin(pi x) sin(pi y)       (default n=8, k=2)
+  hex_poisson     : unit cube, n^3 hexahedra, Q^k, tau = 1,
+                    u = prod sin(pi x_i)                    (default n=16, k=3)
+  hex_elasticity  : n^3 hexahedra with interior vertices moved by up to 0.2h
+                    (seed 3), Q^k, E = 1, nu = 0.3, tau = 1, R right-hand sides
+                    from nodal N(0,1) body forces (seeds 300..)  (n=32, k=2, R=8)
+  hex_cdr         : n^3 hexahedra, Q^k, 5 components, beta = (1,1,1)/sqrt 3,
+                    kappa = 1, reaction A = S + W + I from a seeded (5) Gaussian
+                    G (S = G G^T / 5, W = (G - G^T)/2), tau = |beta| + kappa,
+                    R right-hand sides from nodal N(0,1) forces (seeds 500..)
+                                                             (n=40, k=2, R=4)
+  hex_convdiff    : one serving request: n^3 hexahedra, Q^k, kappa, unit beta,
+                    f = 1, tau = 1 + kappa
+All faces on the domain boundary are Dirichlet faces.
+"""
+from dataclasses import dataclass
+import numpy as np
+
+from . import mesh as meshmod
+from . import blocks as blk
+
+
+@dataclass
+class Workload:
+    name: str
+    mesh: object
+    ref: object
+    perm: np.ndarray
+    phys: object
+    R: int
+    rhs_kind: str                 # 'function' or 'nodal'
+    f_exact: object = None        # callable x -> (..., M)
+    u_exact: object = None        # callable x -> (..., M)
+    q_exact: object = None        # callable x -> (..., M, D)
+    rhs_seeds: tuple = ()
+    k: int = 1
+
+    # sizes
+    @property
+    def M(self): return self.phys.M
+
+    @property
+    def D(self): return self.phys.D
+
+    @property
+    def PE(self): return self.ref.PE
+
+    @property
+    def PF(self): return self.ref.PF
+
+    @property
+    def n_lfe(self): return self.ref.n_lfe
+
+    @property
+    def n_elem(self): return self.mesh.n_elem
+
+    @property
+    def n_face(self): return self.mesh.n_face
+
+    @property
+    def face_dirichlet(self):
+        return self.mesh.face_boundary.astype(np.uint8)
+
+    @property
+    def n_free(self):
+        return int(self.n_face - self.face_dirichlet.sum())
+
+    @property
+    def n_dof(self):
+        return self.n_free * self.M * self.PF
+
+    def blocks(self, e0=0, e1=None):
+        """Element blocks for elements [e0, e1) (row-major, float64)."""
+        e1 = self.n_elem if e1 is None else e1
+        elems = np.arange(e0, e1)
+        mats = blk.element_matrices(self.mesh, self.ref, self.perm, elems)
+        out = blk.hdg_blocks(mats, self.phys)
+        E = len(elems)
+        if self.rhs_kind == 'function':
+            ru = blk.load_vector_from_function(mats, self.ref, self.f_exact, self.M)[:, :, None]
+            ru = np.repeat(ru, self.R, axis=2)
+        else:
+            cols = []
+            for s in self.rhs_seeds:
+                rng = np.random.default_rng(s)
+                fn = rng.standard_normal((self.n_elem, self.M, self.PE))[e0:e1]
+                cols.append(blk.load_vector_from_nodal(mats, fn))
+            ru = np.stack(cols, axis=2)
+        out['ru'] = np.ascontiguousarray(ru)
+        out['ruh'] = np.zeros((E, self.n_lfe * self.M * self.PF, self.R))
+        out['_mats'] = mats
+        return out
+
+    def uhat_dirichlet(self):
+        """(NF, M*PF, R) Dirichlet trace values (zero rows on interior faces)."""
+        if self.u_exact is None:
+            v = np.zeros((self.n_face, self.M * self.PF))
+        else:
+            v = blk.dirichlet_face_values(self.mesh, self.ref, self.perm, self.u_exact, self.M)
+        return np.ascontiguousarray(np.repeat(v[:, :, None], self.R, axis=2))
+
+    def random_vector(self, seed):
+        """Seeded N(0,1) vector over the free trace dofs, e.g. the starting
+        vector of the Arnoldi cycle that defines a polynomial preconditioner."""
+        return np.random.default_rng(seed).standard_normal(self.n_dof)
+
+
+def _sin_product(D):
+    def u(x):
+        return np.prod(np.sin(np.pi * x), axis=-1)[..., None]
+
+    def f(x):
+        return (D * np.pi ** 2) * u(x)
+
+    def q(x):
+        s = np.sin(np.pi * x)
+        c = np.cos(np.pi * x)
+        out = np.empty(x.shape[:-1] + (1, D))
+        for d in range(D):
+            others = np.prod(np.delete(s, d, axis=-1), axis=-1)
+            out[..., 0, d] = np.pi * c[..., d] * others
+        return out
+    return u, f, q
+
+
+def tri_poisson(n=8, k=2, R=1):
+    m = meshmod.tri_mesh(n)
+    ref = blk.reference_element(m, k)
+    u, f, q = _sin_product(2)
+    return Workload('tri_poisson', m, ref, blk.face_permutations(m, ref), blk.poisson(2), R,
+                    'function', f, u, q, k=k)
+
+
+def hex_poisson(n=16, k=3, R=1):
+    m = meshmod.hex_mesh(n)
+    ref = blk.reference_element(m, k)
+    u, f, q = _sin_product(3)
+    return Workload('hex_poisson', m, ref, blk.face_permutations(m, ref), blk.poisson(3), R,
+                    'function', f, u, q, k=k)
+
+
+def hex_elasticity(n=32, k=2, R=8, young=1.0, nu=0.3, perturb=0.2, mesh_seed=3, rhs_seed0=300):
+    lam = young * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = young / (2 * (1 + nu))
+    m = meshmod.hex_mesh(n, perturb, mesh_seed)
+    ref = blk.reference_element(m, k, (k + 4) if perturb > 0 else None)
+    return Workload('hex_elasticity', m, ref, blk.face_permutations(m, ref), blk.elasticity(3, lam, mu, 1.0),
+                    R, 'nodal', rhs_seeds=tuple(range(rhs_seed0, rhs_seed0 + R)), k=k)
+
+
+def cdr_reaction_matrix(M=5, seed=5):
+    G = np.random.default_rng(seed).standard_normal((M, M))
+    return G @ G.T / M + (G - G.T) / 2 + np.eye(M)
+
+
+def hex_cdr(n=40, k=2, R=4, M=5, kappa=1.0, a_seed=5, rhs_seed0=500):
+    m = meshmod.hex_mesh(n)
+    ref = blk.reference_element(m, k)
+    beta = np.ones(3) / np.sqrt(3.0)
+    phys = blk.cdr(3, M, beta, kappa, cdr_reaction_matrix(M, a_seed), np.linalg.norm(beta) + kappa)
+    return Workload('hex_cdr', m, ref, blk.face_permutations(m, ref), phys, R, 'nodal',
+                    rhs_seeds=tuple(range(rhs_seed0, rhs_seed0 + R)), k=k)
+
+
+def hex_convdiff(n, k, kappa, beta, R=1):
+    m = meshmod.hex_mesh(n)
+    ref = blk.reference_element(m, k)
+    beta = np.asarray(beta, float)
+    phys = blk.cdr(3, 1, beta, kappa, np.zeros((1, 1)), np.linalg.norm(beta) + kappa)
+    one = lambda x: np.ones(x.shape[:-1] + (1,))
+    return Workload('hex_convdiff', m, ref, blk.face_permutations(m, ref), phys, R, 'function', one, k=k)
+
+
+def serving_requests(n_requests=512, seed=4, n_range=(8, 24), k_range=(1, 3)):
+    """Request parameters of the serving stream: kappa log-uniform in
+    [1e-3, 1], a uniform random unit velocity, n and k uniform integers."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n_requests):
+        kappa = 10.0 ** rng.uniform(-3.0, 0.0)
+        b = rng.standard_normal(3)
+        b /= np.linalg.norm(b)
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        reqs.append(dict(id=i, kappa=kappa, beta=b, n=n, k=k))
+    return reqs
+
+
+def poisson_arrivals(n, rate, seed=41):
+    """Arrival times (s) of a Poisson process with the given rate (1/s)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))

@@ -1,0 +1,154 @@
+"""Pins of the oracle's condensation / assembly / recovery against the
+mathematics: manufactured-solution rates, the polynomial patch test, the
+monolithic dense solve, symmetry, and structural counts (Welter & Nguyen,
+Sec. 2.3-2.4, 4.1-4.2)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from hdg_inputs import workloads as W
+from hdg_inputs import blocks as blk
+from oracle.condense import condense_direct, condense_local
+from oracle.assemble import monolithic_solve
+from oracle.postprocess import postprocess_tri
+from tests.oracle_helpers import OracleSystem, l2_errors
+
+GOLDEN = os.path.join(os.path.dirname(__file__), 'golden')
+
+
+def _solve_errors(w):
+    s = OracleSystem(w)
+    uh = s.direct()
+    u, q = s.recover(uh)
+    return s, u, q, l2_errors(w, s.b, u, q)
+
+
+def test_tri_mms_rates_k2():
+    """L2 errors of u and q decrease at order k+1 = 3 (P^2 triangles)."""
+    errs = [_solve_errors(W.tri_poisson(n=n, k=2))[3] for n in (4, 8, 16)]
+    for (eu0, eq0), (eu1, eq1) in zip(errs[:-1], errs[1:]):
+        assert 2.85 < np.log2(eu0 / eu1) < 3.2
+        assert 2.85 < np.log2(eq0 / eq1) < 3.2
+
+
+def test_tri_postprocessing_superconvergence():
+    """u* converges at order k+2 = 4."""
+    errs = []
+    for n in (4, 8, 16):
+        w = W.tri_poisson(n=n, k=2)
+        s, u, q, _ = _solve_errors(w)
+        phs, coef, xq, wq = postprocess_tri(w.mesh, 2, u[:, :, 0], q[:, :, 0])
+        us = np.einsum('qi,ei->eq', phs, coef)
+        errs.append(np.sqrt((wq * (us - w.u_exact(xq)[..., 0]) ** 2).sum()))
+    for e0, e1 in zip(errs[:-1], errs[1:]):
+        assert 3.8 < np.log2(e0 / e1) < 4.3
+
+
+@pytest.mark.parametrize('k', [1, 3])
+def test_hex_mms_rates(k):
+    """Q^k hexahedra: errors of u and q decrease at about order k+1."""
+    ns = (2, 4) if k == 3 else (4, 8)
+    errs = [_solve_errors(W.hex_poisson(n=n, k=k))[3] for n in ns]
+    (eu0, eq0), (eu1, eq1) = errs
+    assert np.log2(eu0 / eu1) > k + 0.5
+    assert np.log2(eq0 / eq1) > k + 0.4
+
+
+def _patch(mesh_w, k):
+    """Replace the manufactured solution of a Poisson workload by a
+    polynomial of degree k (in each variable for Q^k)."""
+    D = mesh_w.D
+    if D == 2:
+        c = np.array([0.3, -1.2, 0.7, 0.5, -0.4, 0.9])
+        def u(x):
+            X, Y = x[..., 0], x[..., 1]
+            return (c[0] + c[1] * X + c[2] * Y + c[3] * X * X + c[4] * X * Y + c[5] * Y * Y)[..., None]
+        def qf(x):
+            X, Y = x[..., 0], x[..., 1]
+            return np.stack([c[1] + 2 * c[3] * X + c[4] * Y, c[2] + c[4] * X + 2 * c[5] * Y], -1)[..., None, :]
+        lap = 2 * c[3] + 2 * c[5]
+        f = lambda x: np.full(x.shape[:-1] + (1,), -lap)
+    else:
+        def u(x):
+            X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+            return (0.5 + X * X * Y - 0.3 * Y * Z * Z + 0.2 * X * Y * Z)[..., None]
+        def qf(x):
+            X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+            return np.stack([2 * X * Y + 0.2 * Y * Z, X * X - 0.3 * Z * Z + 0.2 * X * Z,
+                             -0.6 * Y * Z + 0.2 * X * Y], -1)[..., None, :]
+        f = lambda x: -(2 * x[..., 1] - 0.6 * x[..., 1])[..., None]
+    mesh_w.u_exact, mesh_w.q_exact, mesh_w.f_exact = u, qf, f
+    return mesh_w
+
+
+@pytest.mark.parametrize('case', ['tri', 'hex'])
+def test_patch_test_exact(case):
+    """HDG reproduces a polynomial solution in the discrete space exactly
+    (consistency + uniqueness): errors at round-off level."""
+    w = _patch(W.tri_poisson(n=3, k=2) if case == 'tri' else W.hex_poisson(n=2, k=2), 2)
+    s, u, q, (eu, eq) = _solve_errors(w)
+    assert eu < 1e-11 and eq < 1e-10
+
+
+@pytest.mark.parametrize('make', [
+    lambda: W.tri_poisson(n=4, k=2),
+    lambda: W.hex_poisson(n=2, k=2),
+    lambda: W.hex_elasticity(n=2, k=1, R=2),
+    lambda: W.hex_cdr(n=2, k=1, R=2),
+])
+def test_condensed_then_recovered_equals_monolithic(make):
+    """Condensation + trace solve + recovery equals the dense monolithic
+    solve of Eq. matrixform to 1e-12 (relative)."""
+    w = make()
+    s = OracleSystem(w)
+    uh = s.direct()
+    if uh.ndim == 1:
+        uh = uh[:, None]
+    u, q = s.recover(uh)
+    qm, um, uhm = monolithic_solve(s.b, w.mesh.elem_face, w.face_dirichlet, s.uD, w.M, w.n_lfe)
+    rel = lambda a, b: np.abs(a - b).max() / np.abs(b).max()
+    assert rel(uh, uhm) < 1e-12
+    assert rel(u, um) < 1e-12
+    assert rel(q, qm) < 1e-12
+
+
+def test_condensation_routes_agree():
+    """Eq. 13b-c (dense local inverse) equals the route of Eqs. w15-w22."""
+    w = W.hex_elasticity(n=2, k=2, R=3)
+    b = w.blocks()
+    K1, r1 = condense_direct(b, w.M, w.n_lfe)
+    K2, r2, _ = condense_local(b, w.M, w.n_lfe)
+    assert np.abs(K1 - K2).max() < 1e-12 * np.abs(K1).max()
+    assert np.abs(r1 - r2).max() < 1e-12 * np.abs(r1).max()
+
+
+@pytest.mark.parametrize('make', [lambda: W.hex_poisson(n=3, k=2), lambda: W.hex_elasticity(n=2, k=2, R=1)])
+def test_trace_matrix_symmetric_definite(make):
+    """For Poisson and elasticity K is symmetric and (with the sign of Eq.
+    HDGd) negative definite."""
+    s = OracleSystem(make())
+    K = s.K.toarray()
+    assert np.abs(K - K.T).max() < 1e-12 * np.abs(K).max()
+    np.linalg.cholesky(-K)
+
+
+def test_structural_counts_golden():
+    """N_dof = M P_F N_F (Sec. 2.4) and the number of nonzero face blocks
+    (each pair of free faces sharing an element) for the named workloads."""
+    gold = json.load(open(os.path.join(GOLDEN, 'structural_counts.json')))
+    for name, ref in gold['cases'].items():
+        w = {'tri_poisson_8_k2': lambda: W.tri_poisson(8, 2),
+             'hex_poisson_16_k3': lambda: W.hex_poisson(16, 3)}[name]()
+        assert w.n_dof == ref['n_dof']
+        assert w.n_free == ref['n_free_faces']
+        fd = w.face_dirichlet
+        nfree_e = (fd[w.mesh.elem_face] == 0).sum(axis=1)
+        nnzb = int((nfree_e ** 2).sum() - w.n_free)
+        assert nnzb == ref['n_nonzero_blocks']
+    # and the oracle's assembled matrix has exactly that block pattern
+    s = OracleSystem(W.tri_poisson(8, 2))
+    b = s.bsz
+    pat = (abs(s.K) > 0).toarray().reshape(s.K.shape[0] // b, b, -1, b).any(axis=(1, 3))
+    assert int(pat.sum()) == gold['cases']['tri_poisson_8_k2']['n_nonzero_blocks']
