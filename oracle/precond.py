@@ -87,7 +87,7 @@ def harmonic_ritz(H):
     P = H.shape[1]
     Hs = H[:P, :P]
     hn = H[P, P - 1] if H.shape[0] > P else 0.0
-    if hn == 0.0 or np.linalg.cond(Hs) > 1e12:
+    if hn == 0.0 or np.linalg.cond(Hs, 1) > 1e12:
         return np.linalg.eigvals(Hs)
     eP = np.zeros(P)
     eP[-1] = 1.0
