@@ -1,0 +1,247 @@
+/*
+ * hdg.h -- C ABI of the GB300 HDG trace-solver library (libhdg.so).
+ *
+ * The library implements the data-parallel hot path of the HDG solver of
+ * Welter & Nguyen, "Preconditioning Techniques for Hybridizable Discontinuous
+ * Galerkin Discretizations on GPU Architectures" (arXiv 2512.13619):
+ * batched static condensation of element blocks, face-based assembly of the
+ * trace matrix K in face-block format, and restarted left-preconditioned
+ * GMRES on K with block-Jacobi, additive-Schwarz and polynomial
+ * preconditioners, followed by element-wise recovery.
+ *
+ * Conventions shared by every entry point
+ *  - Plain pointers and sizes only.  A pointer argument documented as
+ *    "host or device" is a device pointer when the call's `on_device` flag is
+ *    non-zero, otherwise a host pointer.  Arguments documented as "device"
+ *    are always device pointers on the problem's device.
+ *  - The library owns every buffer it allocates and frees them in
+ *    hdg_problem_destroy.  Caller buffers are never retained after a call
+ *    returns (except the stream handle, which is only used during the call).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  All device work is stream-ordered on it.  Calls that
+ *    return values computed on the device (iteration counts, residuals)
+ *    synchronise that stream before returning; no call synchronises the whole
+ *    device.
+ *  - Every call returns an hdg_status.  No C++ exception crosses the ABI.  On
+ *    an error the problem stays valid (it can be destroyed) unless the status
+ *    is HDG_ERR_CUDA, after which only hdg_problem_destroy is allowed.
+ *  - All matrices are row-major, element-contiguous (strided batches).
+ *
+ * Unknown ordering (M components, D dimensions, P_E element and P_F face
+ * basis functions, N_lfe local faces per element, R right-hand sides):
+ *    element u   : (a, i)     -> a*P_E + i
+ *    element q   : (a, c, i)  -> (a*D + c)*P_E + i
+ *    element uhat: (l, a, j)  -> (l*M + a)*P_F + j
+ *    face trace  : (a, j)     -> a*P_F + j            (b = M*P_F per face)
+ * Face basis functions of every element are ordered as the global face's
+ * nodes, so both elements of a face address the same face unknowns.
+ * Vectors with R right-hand sides keep the RHS index fastest:
+ *    v[dof*R + r].
+ * The trace unknowns of the linear solver are the "free" faces (faces not
+ * marked Dirichlet), numbered in increasing global face id; n_dof = n_free*b.
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_problem_s* hdg_problem;
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_ERR_ARG = 1,           /* invalid argument or size                            */
+  HDG_ERR_OOM = 2,           /* device allocation failed                             */
+  HDG_ERR_BUDGET = 3,        /* request exceeds the configured memory budget         */
+  HDG_ERR_SINGULAR = 4,      /* zero pivot in a batched inverse (M^e, Ebar, BJ, ASM) */
+  HDG_ERR_NOT_CONVERGED = 5, /* max iterations reached above the tolerance           */
+  HDG_ERR_BREAKDOWN = 6,     /* GMRES / Arnoldi breakdown that is not a lucky one     */
+  HDG_ERR_NAN = 7,           /* NaN or Inf met in a norm                              */
+  HDG_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up                   */
+  HDG_ERR_CUDA = 9,          /* CUDA runtime error                                    */
+  HDG_ERR_STATE = 10         /* call out of order (e.g. solve before assemble)        */
+} hdg_status;
+
+typedef enum { HDG_FP64 = 0, HDG_FP32 = 1, HDG_BF16 = 2 } hdg_prec;
+typedef enum { HDG_PC_NONE = 0, HDG_PC_BJ = 1, HDG_PC_ASM = 2 } hdg_pc;
+typedef enum { HDG_POLY_NONE = 0, HDG_POLY_GMRES = 1, HDG_POLY_CHEBYSHEV = 2 } hdg_poly;
+typedef enum { HDG_ORTH_CGS = 0, HDG_ORTH_MGS = 1, HDG_ORTH_CGS2 = 2 } hdg_orth;
+
+/* Mesh connectivity (Sec. 4.2 face-based assembly, Sec. 4.6 ASM update).
+ *  elem_face      host, n_elem*n_lfe int32: global face id f(e, l)
+ *  face_elem      host, n_face*4 int32: (e1, l1, e2, l2); e2 = l2 = -1 for a
+ *                 face with one element
+ *  face_dirichlet host, n_face uint8: 1 = Dirichlet face (trace known,
+ *                 eliminated from K), 0 = free face
+ * Copied by hdg_problem_create. */
+typedef struct {
+  int dim, n_lfe, M, PE, PF;
+  int64_t n_elem, n_face;
+  const int32_t* elem_face;
+  const int32_t* face_elem;
+  const uint8_t* face_dirichlet;
+} hdg_mesh;
+
+/* Solver options (Sec. 3.1-3.4 and Sec. 5 solver parameters: restart 50,
+ * CGS, max 1000 iterations).
+ *  restart      GMRES restart length m (1..200)
+ *  max_iters    total iteration cap (inner iterations in mixed mode)
+ *  rtol         accepted when ||b - K x||_2 / ||b||_2 <= rtol, computed in
+ *               FP64 per right-hand side
+ *  orth         Gram-Schmidt variant
+ *  pc           base preconditioner M^{-1} (none, block-Jacobi, ASM)
+ *  poly         polynomial preconditioner p(M^{-1} K) composed with pc
+ *  poly_degree  number of Ritz values P (GMRES polynomial) or polynomial
+ *               degree (Chebyshev)
+ *  inner_prec   HDG_FP64: plain FP64 GMRES.  HDG_FP32 / HDG_BF16: FP64
+ *               iterative refinement around an inner GMRES whose matrix and
+ *               preconditioner blocks are stored in FP32 (the polynomial
+ *               smoother's matrix in poly_prec) and accumulated in FP32; the
+ *               Krylov basis, Gram-Schmidt and Givens stay in FP64
+ *  poly_prec    storage precision of K inside the polynomial smoother
+ *  inner_rtol   relative tolerance of each inner solve in mixed mode
+ *  max_outer    refinement-step cap in mixed mode */
+typedef struct {
+  int restart;
+  int max_iters;
+  double rtol;
+  int orth;
+  int pc;
+  int poly;
+  int poly_degree;
+  int inner_prec;
+  int poly_prec;
+  double inner_rtol;
+  int max_outer;
+} hdg_solver_opts;
+
+typedef struct {
+  int iters;          /* GMRES iterations (max over right-hand sides)        */
+  int restarts;       /* restart cycles                                       */
+  int outer;          /* refinement steps (mixed mode), 0 otherwise           */
+  int converged;      /* 1 if every right-hand side met rtol                  */
+  double rel_resid;   /* max over RHS of ||b - K x|| / ||b|| (FP64)           */
+} hdg_solve_info;
+
+/* Human-readable name of a status. */
+const char* hdg_status_str(hdg_status s);
+
+/* Create a problem on CUDA device `device` for `nrhs` right-hand sides.
+ * Builds the face-row neighbour tables (free-face numbering, 2N_lfe-1 slots
+ * per face row, Sec. 2.4) on the host and uploads them.  *out owns all device
+ * memory of the problem.  Errors: HDG_ERR_ARG (bad sizes, inconsistent maps),
+ * HDG_ERR_OOM. */
+hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_problem* out);
+
+/* Release every buffer of the problem.  NULL is accepted. */
+hdg_status hdg_problem_destroy(hdg_problem p);
+
+/* Device bytes the problem currently holds (for admission by budget). */
+size_t hdg_problem_device_bytes(hdg_problem p);
+
+/* Device bytes a problem of this mesh would hold after create, condense,
+ * assemble and setup with `opts` (an estimate used for admission control). */
+size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts* opts);
+
+/* Batched static condensation of elements [e0, e0+count) (Eq. 13; Sec. 4.1
+ * Eqs. w15-w19, Sec. 4.2 Eqs. w21-w22), FP64:
+ *   A^{-1} from (M^e)^{-1}; Ebar = E - D A^{-1} B; Fbar = F - D A^{-1} C;
+ *   Hbar = H - G A^{-1} B; Jbar = J - G A^{-1} C;
+ *   Kbar^e = Jbar - Hbar Ebar^{-1} Fbar;  rbar^e = r_uh - Hbar Ebar^{-1} r_u.
+ * Inputs (host or device per on_device), `count` elements each, row-major:
+ *   Me  P_E x P_E           mass matrix M^e of Eq. w16
+ *   Bd  D x P_E x P_E       B_d of Eq. w16 (matrix of (u, div r) of Eq. HDGa)
+ *   Cd  D x P_E x N_lfe*P_F C_d of Eq. w16
+ *   D   M*P_E x M*D*P_E     E   M*P_E x M*P_E     F  M*P_E x N_lfe*M*P_F
+ *   G   N_lfe*M*P_F x M*D*P_E  H  N_lfe*M*P_F x M*P_E
+ *   J   N_lfe*M*P_F x N_lfe*M*P_F
+ *   ru  M*P_E x R           ruh N_lfe*M*P_F x R
+ * r_q = 0 as in Sec. 4.1.  Results stay on the device (Kbar^e, rbar^e and the
+ * recovery data (M^e)^{-1}B_d, (M^e)^{-1}C_d, Ebar^{-1}Fbar, Ebar^{-1}r_u).
+ * Elements may be condensed in any number of calls, in any order; assembly
+ * requires all of them.  Errors: HDG_ERR_ARG, HDG_ERR_SINGULAR (zero pivot in
+ * M^e or Ebar; reported at the next synchronising call), HDG_ERR_CUDA. */
+hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count,
+                        const double* Me, const double* Bd, const double* Cd,
+                        const double* D, const double* E, const double* F,
+                        const double* G, const double* H, const double* J,
+                        const double* ru, const double* ruh, int on_device, void* stream);
+
+/* Dirichlet trace values u_D (b_hat = uhat - u_D on Dirichlet faces, Sec.
+ * 2.1): host or device, n_face x b x R; rows of free faces are ignored.
+ * Defaults to zero.  Must be set before hdg_assemble. */
+hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhat_dirichlet, int on_device, void* stream);
+
+/* Face-based assembly (Sec. 4.2): for every free face f the face row of K,
+ * (2N_lfe-1) blocks of b x b (diagonal K_ff = Kbar^{e1}_{l1l1} +
+ * Kbar^{e2}_{l2l2}, off-diagonal K_fg = Kbar^e_{l(f)l(g)}), stored in FP64 and,
+ * when `opts` needs them, FP32/BF16 copies; r_f = sum_e rbar^e_l minus the
+ * Dirichlet columns times u_D.  Errors: HDG_ERR_STATE if not every element
+ * was condensed. */
+hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream);
+
+/* Preconditioner setup: block-Jacobi inverses of K_ff (Sec. 4.5, FP64 with
+ * partial pivoting), ASM element matrices and inverses (Sec. 4.6), and for a
+ * polynomial preconditioner one Arnoldi(P) cycle (MGS) with A = M^{-1} K from
+ * the start vector `v0` (device, n_dof doubles), harmonic Ritz values and
+ * Leja order (Sec. 4.7) or Chebyshev bounds.  v0 may be NULL when
+ * opts->poly == HDG_POLY_NONE.  Errors: HDG_ERR_SINGULAR, HDG_ERR_ARG. */
+hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* opts, const double* v0, void* stream);
+
+/* Restarted left-preconditioned GMRES(m) on K x = r for all R right-hand
+ * sides (Sec. 3.1, Sec. 4.4), x0 = 0.  The solution stays on the device; read
+ * it with hdg_get_trace.  `info` (host, may be NULL) receives the counts.
+ * Returns HDG_OK when every RHS met rtol, HDG_ERR_NOT_CONVERGED otherwise. */
+hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* opts, void* stream, hdg_solve_info* info);
+
+/* Full trace uhat (host or device): n_face x b x R, Dirichlet faces filled
+ * with u_D. */
+hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* stream);
+
+/* Element recovery (Eq. w19, Eq. w16): u^e = Ebar^{-1}(r_u - Fbar uhat^e),
+ * q^e_{a,d} = -(M^e)^{-1}(B_d u^e_a + C_d uhat^e_a).  Outputs host or device:
+ * u  n_elem x M*P_E x R,  q  n_elem x M*D*P_E x R. */
+hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void* stream);
+
+/* y = K x with K stored in `prec` (FP64, FP32 or BF16 blocks; products
+ * accumulated in FP64 for FP64 blocks, FP32 otherwise) (Sec. 4.3).  x, y:
+ * device, n_dof x R doubles.  For tests and benchmarks. */
+hdg_status hdg_apply_K(hdg_problem p, int prec, const double* x, double* y, void* stream);
+
+/* y = P^{-1} x for the preconditioner of the last hdg_setup_precond call,
+ * blocks in `prec` (Sec. 4.5-4.7).  x, y: device, n_dof x R doubles. */
+hdg_status hdg_apply_precond(hdg_problem p, const hdg_solver_opts* opts, int prec,
+                             const double* x, double* y, void* stream);
+
+/* Copy condensed element data to the host: Kbar (count x n x n, n =
+ * N_lfe*M*P_F) and rbar (count x n x R); either may be NULL. */
+hdg_status hdg_get_condensed(hdg_problem p, int64_t e0, int64_t count, double* Kbar, double* rbar);
+
+/* Copy the assembled right-hand side r (host, n_dof x R) and the FP64 face
+ * row blocks of free faces [f0, f0+count) (host, count x (2N_lfe-1) x b x b,
+ * slot s of face row f couples f with free face nbr[f][s]; zero blocks where
+ * nbr = -1) together with nbr (host, count x (2N_lfe-1) int32).  Any pointer
+ * may be NULL. */
+hdg_status hdg_get_face_rows(hdg_problem p, int64_t f0, int64_t count, double* blocks,
+                             int32_t* nbr, double* r);
+
+/* Polynomial coefficients of the last setup: theta (Leja order) as real and
+ * imaginary parts (host, capacity `cap`), or for Chebyshev (alpha, beta) in
+ * re[0], re[1].  *n receives the count. */
+hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n);
+
+/* Mean device time (ms) of the block-matvec launches of the last hdg_solve
+ * or hdg_apply_K calls with event timing enabled (enable = 1), and the launch
+ * count.  For benchmarks. */
+hdg_status hdg_set_timing(hdg_problem p, int enable);
+hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDG_H */

@@ -1,0 +1,189 @@
+"""ctypes binding of libhdg.so: one Python function per C entry point of
+include/hdg.h, with the same name and argument order.  Arguments are
+marshalled only: numpy arrays pass their host pointer, torch tensors their
+data pointer, ints are taken as raw addresses.  Functions return the integer
+hdg_status (0 = HDG_OK); hdg_problem_create returns (status, handle).
+
+Loading fails loudly (RuntimeError) when the compiled library is missing:
+there is no fallback implementation.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'libhdg.so')
+
+HDG_OK, HDG_ERR_ARG, HDG_ERR_OOM, HDG_ERR_BUDGET, HDG_ERR_SINGULAR, HDG_ERR_NOT_CONVERGED, HDG_ERR_BREAKDOWN, \
+    HDG_ERR_NAN, HDG_ERR_TIMEOUT, HDG_ERR_CUDA, HDG_ERR_STATE = range(11)
+HDG_FP64, HDG_FP32, HDG_BF16 = 0, 1, 2
+HDG_PC_NONE, HDG_PC_BJ, HDG_PC_ASM = 0, 1, 2
+HDG_POLY_NONE, HDG_POLY_GMRES, HDG_POLY_CHEBYSHEV = 0, 1, 2
+HDG_ORTH_CGS, HDG_ORTH_MGS, HDG_ORTH_CGS2 = 0, 1, 2
+
+
+class hdg_mesh(ctypes.Structure):
+    _fields_ = [('dim', ctypes.c_int), ('n_lfe', ctypes.c_int), ('M', ctypes.c_int), ('PE', ctypes.c_int),
+                ('PF', ctypes.c_int), ('n_elem', ctypes.c_int64), ('n_face', ctypes.c_int64),
+                ('elem_face', ctypes.c_void_p), ('face_elem', ctypes.c_void_p), ('face_dirichlet', ctypes.c_void_p)]
+
+
+class hdg_solver_opts(ctypes.Structure):
+    _fields_ = [('restart', ctypes.c_int), ('max_iters', ctypes.c_int), ('rtol', ctypes.c_double),
+                ('orth', ctypes.c_int), ('pc', ctypes.c_int), ('poly', ctypes.c_int), ('poly_degree', ctypes.c_int),
+                ('inner_prec', ctypes.c_int), ('poly_prec', ctypes.c_int), ('inner_rtol', ctypes.c_double),
+                ('max_outer', ctypes.c_int)]
+
+
+class hdg_solve_info(ctypes.Structure):
+    _fields_ = [('iters', ctypes.c_int), ('restarts', ctypes.c_int), ('outer', ctypes.c_int),
+                ('converged', ctypes.c_int), ('rel_resid', ctypes.c_double)]
+
+
+_V, _I, _I64, _D, _P = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+_SIGS = {
+    'hdg_status_str': (ctypes.c_char_p, [_I]),
+    'hdg_problem_create': (_I, [ctypes.POINTER(hdg_mesh), _I, _I, ctypes.POINTER(_V)]),
+    'hdg_problem_destroy': (_I, [_V]),
+    'hdg_problem_device_bytes': (ctypes.c_size_t, [_V]),
+    'hdg_workspace_bytes': (ctypes.c_size_t, [ctypes.POINTER(hdg_mesh), _I, ctypes.POINTER(hdg_solver_opts)]),
+    'hdg_condense': (_I, [_V, _I64, _I64] + [_P] * 11 + [_I, _V]),
+    'hdg_set_dirichlet': (_I, [_V, _P, _I, _V]),
+    'hdg_assemble': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _V]),
+    'hdg_setup_precond': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _P, _V]),
+    'hdg_solve': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _V, ctypes.POINTER(hdg_solve_info)]),
+    'hdg_get_trace': (_I, [_V, _P, _I, _V]),
+    'hdg_recover': (_I, [_V, _P, _P, _I, _V]),
+    'hdg_apply_K': (_I, [_V, _I, _P, _P, _V]),
+    'hdg_apply_precond': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _I, _P, _P, _V]),
+    'hdg_get_condensed': (_I, [_V, _I64, _I64, _P, _P]),
+    'hdg_get_face_rows': (_I, [_V, _I64, _I64, _P, _P, _P]),
+    'hdg_get_poly': (_I, [_V, _P, _P, _I, ctypes.POINTER(_I)]),
+    'hdg_set_timing': (_I, [_V, _I]),
+    'hdg_get_timing': (_I, [_V, _I, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libhdg.so (built by paper_2512_13619_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError('libhdg.so is not built (%s); run __graft_entry__.build()' % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def ptr(a):
+    """Address of a numpy array, a torch tensor, an int address or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, 'data_ptr'):
+        return a.data_ptr()
+    if hasattr(a, 'ctypes'):
+        return a.ctypes.data
+    raise TypeError('cannot take the address of %r' % type(a))
+
+
+def stream_ptr(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def hdg_status_str(st):
+    return load().hdg_status_str(st).decode()
+
+
+def hdg_problem_create(mesh, nrhs, device):
+    h = ctypes.c_void_p()
+    st = load().hdg_problem_create(ctypes.byref(mesh), nrhs, device, ctypes.byref(h))
+    return st, h.value
+
+
+def hdg_problem_destroy(p):
+    return load().hdg_problem_destroy(p)
+
+
+def hdg_problem_device_bytes(p):
+    return load().hdg_problem_device_bytes(p)
+
+
+def hdg_workspace_bytes(mesh, nrhs, opts):
+    return load().hdg_workspace_bytes(ctypes.byref(mesh), nrhs, ctypes.byref(opts) if opts is not None else None)
+
+
+def hdg_condense(p, e0, count, Me, Bd, Cd, D, E, F, G, H, J, ru, ruh, on_device, stream=None):
+    return load().hdg_condense(p, e0, count, *[ptr(a) for a in (Me, Bd, Cd, D, E, F, G, H, J, ru, ruh)],
+                               int(on_device), stream_ptr(stream))
+
+
+def hdg_set_dirichlet(p, uhat_dirichlet, on_device, stream=None):
+    return load().hdg_set_dirichlet(p, ptr(uhat_dirichlet), int(on_device), stream_ptr(stream))
+
+
+def hdg_assemble(p, opts, stream=None):
+    return load().hdg_assemble(p, ctypes.byref(opts), stream_ptr(stream))
+
+
+def hdg_setup_precond(p, opts, v0, stream=None):
+    return load().hdg_setup_precond(p, ctypes.byref(opts), ptr(v0), stream_ptr(stream))
+
+
+def hdg_solve(p, opts, stream=None, info=None):
+    return load().hdg_solve(p, ctypes.byref(opts), stream_ptr(stream), ctypes.byref(info) if info is not None else None)
+
+
+def hdg_get_trace(p, uhat, on_device, stream=None):
+    return load().hdg_get_trace(p, ptr(uhat), int(on_device), stream_ptr(stream))
+
+
+def hdg_recover(p, u, q, on_device, stream=None):
+    return load().hdg_recover(p, ptr(u), ptr(q), int(on_device), stream_ptr(stream))
+
+
+def hdg_apply_K(p, prec, x, y, stream=None):
+    return load().hdg_apply_K(p, prec, ptr(x), ptr(y), stream_ptr(stream))
+
+
+def hdg_apply_precond(p, opts, prec, x, y, stream=None):
+    return load().hdg_apply_precond(p, ctypes.byref(opts), prec, ptr(x), ptr(y), stream_ptr(stream))
+
+
+def hdg_get_condensed(p, e0, count, Kbar, rbar):
+    return load().hdg_get_condensed(p, e0, count, ptr(Kbar), ptr(rbar))
+
+
+def hdg_get_face_rows(p, f0, count, blocks, nbr, r):
+    return load().hdg_get_face_rows(p, f0, count, ptr(blocks), ptr(nbr), ptr(r))
+
+
+def hdg_get_poly(p, re, im, cap):
+    n = ctypes.c_int()
+    st = load().hdg_get_poly(p, ptr(re), ptr(im), cap, ctypes.byref(n))
+    return st, n.value
+
+
+def hdg_set_timing(p, enable):
+    return load().hdg_set_timing(p, int(enable))
+
+
+def hdg_get_timing(p, kind=0):
+    t = ctypes.c_double()
+    n = ctypes.c_int64()
+    st = load().hdg_get_timing(p, kind, ctypes.byref(t), ctypes.byref(n))
+    return st, t.value, n.value

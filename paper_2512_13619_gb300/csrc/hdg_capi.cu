@@ -1,0 +1,1379 @@
+// C ABI of the HDG trace-solver library: problem state, host-side mesh maps,
+// and the orchestration of the device kernels (condensation, assembly,
+// preconditioner setup, GMRES, recovery).  Every numerical step runs in the
+// library's CUDA kernels; the host only sequences launches and reads small
+// status words at synchronisation points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hdg_common.cuh"
+#include "hdg_gmres.h"
+#include "hdg_internal.h"
+
+using namespace hdg;
+
+namespace {
+
+struct CudaError {
+  cudaError_t e;
+};
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t _e = (x);                      \
+    if (_e != cudaSuccess) throw CudaError{_e}; \
+  } while (0)
+
+template <typename T>
+int64_t padded_stride(int64_t elems) {
+  int64_t bytes = elems * (int64_t)sizeof(T);
+  bytes = (bytes + 15) / 16 * 16;
+  return bytes / (int64_t)sizeof(T);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct hdg_problem_s {
+  int device = 0;
+  int dim = 0, nl = 0, M = 0, PE = 0, PF = 0, D = 0, R = 1, b = 0, nlb = 0, ms = 0, nlPF = 0, MPE = 0, MDPE = 0;
+  int64_t NE = 0, NF = 0, nfree = 0, ndof = 0;
+  std::vector<int32_t> h_elem_face, h_face_elem, h_free_of_face, h_nbr;
+  std::vector<uint8_t> h_face_dir;
+  std::vector<uint8_t> condensed;
+  int64_t n_condensed = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  // device tables
+  int32_t *d_elem_face = nullptr, *d_free_of_face = nullptr;
+  uint8_t* d_face_dir = nullptr;
+  int32_t *d_nbr = nullptr, *d_cnt = nullptr, *d_slot_e = nullptr, *d_slot_lr = nullptr, *d_slot_lc = nullptr;
+  int32_t *d_diag2 = nullptr, *d_rhs_src = nullptr, *d_bj_nbr = nullptr, *d_bj_cnt = nullptr;
+  int32_t *d_asm_lf = nullptr, *d_asm_cnt = nullptr, *d_asm_face_free = nullptr, *d_fsum = nullptr;
+
+  // condensation results
+  double *d_Kbar = nullptr, *d_rbar = nullptr, *d_MinvB = nullptr, *d_MinvC = nullptr, *d_XF = nullptr,
+         *d_Xr = nullptr;
+  double* d_uhatD = nullptr;
+  // staging / temporaries for condensation
+  int64_t chunk = 0;
+  double* d_stage = nullptr;
+  double* d_tmp = nullptr;
+
+  // assembled system
+  double* K64 = nullptr;
+  float* K32 = nullptr;
+  __nv_bfloat16* K16 = nullptr;
+  int64_t s64 = 0, s32 = 0, s16 = 0;
+  double* d_r = nullptr;
+  bool assembled = false;
+
+  // preconditioners
+  double* bj64 = nullptr;
+  float* bj32 = nullptr;
+  __nv_bfloat16* bj16 = nullptr;
+  int64_t bs64 = 0, bs32 = 0, bs16 = 0;
+  double* as64 = nullptr;
+  float* as32 = nullptr;
+  __nv_bfloat16* as16 = nullptr;
+  int64_t as_s64 = 0, as_s32 = 0, as_s16 = 0;
+  int pc_ready = -1;  // which base preconditioner is set up
+  int poly_kind = 0, poly_n = 0;
+  std::vector<double> th_re, th_im;
+  double* d_poly = nullptr;
+  double cheb_a = 0.0, cheb_b = 0.0;
+
+  // solve workspace
+  double* d_x = nullptr;
+  int ws_m = -1;
+  double *V = nullptr, *vscale = nullptr, *H = nullptr, *g = nullptr, *cs = nullptr, *sn = nullptr, *hcol = nullptr,
+         *htmp = nullptr, *ycoef = nullptr, *partial = nullptr, *tolabs = nullptr, *cfac = nullptr, *zb = nullptr,
+         *bnorm = nullptr, *rel = nullptr;
+  int *running = nullptr, *jend = nullptr, *on_estimate = nullptr, *done = nullptr, *iters = nullptr;
+  unsigned* counter = nullptr;
+  unsigned* d_err = nullptr;
+  double *t1 = nullptr, *res = nullptr, *pq = nullptr, *pw = nullptr, *ptmp = nullptr, *pAq = nullptr,
+         *pt = nullptr, *ze = nullptr, *xo = nullptr, *bo = nullptr;
+  // pinned host mirrors
+  double* h_dbl = nullptr;
+  int* h_int = nullptr;
+  unsigned* h_err = nullptr;
+
+  // timing of block-matvec launches
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double t_mv_ms = 0.0;
+  int64_t n_mv = 0;
+  int br_variant = 0;
+
+  void* dalloc(size_t nbytes) {
+    if (nbytes == 0) nbytes = 16;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, nbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    allocs.push_back(q);
+    bytes += nbytes;
+    return q;
+  }
+  void dfree(void* q, size_t nbytes) {
+    if (!q) return;
+    auto it = std::find(allocs.begin(), allocs.end(), q);
+    if (it != allocs.end()) allocs.erase(it);
+    cudaFree(q);
+    bytes -= std::min(bytes, nbytes);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* q = (T*)dalloc(v.size() * sizeof(T));
+    CK(cudaMemcpy(q, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return q;
+  }
+};
+
+namespace {
+
+hdg_status to_status(const CudaError& e) {
+  (void)e;
+  return HDG_ERR_CUDA;
+}
+
+// Reads and clears the device error word.
+hdg_status check_err(hdg_problem p, cudaStream_t s) {
+  CK(cudaMemcpyAsync(p->h_err, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  unsigned e = *p->h_err;
+  if (e) {
+    CK(cudaMemsetAsync(p->d_err, 0, sizeof(unsigned), s));
+    if (e & ERRBIT_TIMEOUT) return HDG_ERR_TIMEOUT;
+    if (e & ERRBIT_SINGULAR) return HDG_ERR_SINGULAR;
+    if (e & ERRBIT_NAN) return HDG_ERR_NAN;
+    if (e & ERRBIT_ARG) return HDG_ERR_ARG;
+  }
+  return HDG_OK;
+}
+
+struct DeviceGuard {
+  int prev = 0;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// ------------------------------------------------------------------ mesh maps
+// Face rows (Sec. 2.4, Sec. 4.2): slot 0 is the face itself; then the other
+// free faces of e1 in local order, then those of e2.  Dirichlet faces are
+// eliminated, so rows near the boundary hold fewer than 2N_lfe-1 blocks;
+// the real slots are packed first.
+hdg_status build_maps(hdg_problem p) {
+  const int nl = p->nl;
+  p->h_free_of_face.assign(p->NF, -1);
+  int64_t nf = 0;
+  for (int64_t f = 0; f < p->NF; ++f)
+    if (!p->h_face_dir[f]) p->h_free_of_face[f] = (int32_t)nf++;
+  p->nfree = nf;
+  p->ndof = nf * p->b;
+  const int ms = p->ms;
+  std::vector<int32_t> nbr(nf * ms, -1), cnt(nf, 0), se(nf * ms, -1), slr(nf * ms, 0), slc(nf * ms, 0),
+      diag2(nf * 2, -1), rsrc(nf * 4, -1);
+  for (int64_t f = 0; f < p->NF; ++f) {
+    const int32_t ff = p->h_free_of_face[f];
+    if (ff < 0) continue;
+    const int32_t e1 = p->h_face_elem[f * 4], l1 = p->h_face_elem[f * 4 + 1];
+    const int32_t e2 = p->h_face_elem[f * 4 + 2], l2 = p->h_face_elem[f * 4 + 3];
+    if (e1 < 0 || e1 >= p->NE || l1 < 0 || l1 >= nl) return HDG_ERR_ARG;
+    if (e2 >= p->NE || (e2 >= 0 && (l2 < 0 || l2 >= nl))) return HDG_ERR_ARG;
+    if (p->h_elem_face[(int64_t)e1 * nl + l1] != f) return HDG_ERR_ARG;
+    if (e2 >= 0 && p->h_elem_face[(int64_t)e2 * nl + l2] != f) return HDG_ERR_ARG;
+    int c = 0;
+    auto add = [&](int32_t e, int32_t lr, int32_t lc, int32_t g) {
+      nbr[ff * ms + c] = g;
+      se[ff * ms + c] = e;
+      slr[ff * ms + c] = lr;
+      slc[ff * ms + c] = lc;
+      ++c;
+    };
+    add(e1, l1, l1, ff);
+    diag2[ff * 2] = e2;
+    diag2[ff * 2 + 1] = l2;
+    for (int l = 0; l < nl; ++l) {
+      if (l == l1) continue;
+      int32_t g = p->h_elem_face[(int64_t)e1 * nl + l];
+      if (g < 0 || g >= p->NF) return HDG_ERR_ARG;
+      if (p->h_free_of_face[g] >= 0) add(e1, l1, l, p->h_free_of_face[g]);
+    }
+    if (e2 >= 0) {
+      for (int l = 0; l < nl; ++l) {
+        if (l == l2) continue;
+        int32_t g = p->h_elem_face[(int64_t)e2 * nl + l];
+        if (g < 0 || g >= p->NF) return HDG_ERR_ARG;
+        if (p->h_free_of_face[g] >= 0) add(e2, l2, l, p->h_free_of_face[g]);
+      }
+    }
+    cnt[ff] = c;
+    rsrc[ff * 4] = e1;
+    rsrc[ff * 4 + 1] = l1;
+    rsrc[ff * 4 + 2] = e2;
+    rsrc[ff * 4 + 3] = l2;
+  }
+  // ASM: per element, its free local faces (compacted); per free face the
+  // positions inside both elements.
+  std::vector<int32_t> alf(p->NE * nl, 0), acnt(p->NE, 0), aff(p->NE * nl, 0), fsum(nf * 4, -1);
+  std::vector<int32_t> pos(p->NE * nl, -1);
+  for (int64_t e = 0; e < p->NE; ++e) {
+    int c = 0;
+    for (int l = 0; l < nl; ++l) {
+      int32_t g = p->h_elem_face[e * nl + l];
+      if (g < 0 || g >= p->NF) return HDG_ERR_ARG;
+      int32_t ff = p->h_free_of_face[g];
+      if (ff >= 0) {
+        alf[e * nl + c] = l;
+        aff[e * nl + c] = ff;
+        pos[e * nl + l] = c;
+        ++c;
+      }
+    }
+    for (int s = c; s < nl; ++s) aff[e * nl + s] = 0;
+    acnt[e] = c;
+  }
+  for (int64_t f = 0; f < p->NF; ++f) {
+    const int32_t ff = p->h_free_of_face[f];
+    if (ff < 0) continue;
+    const int32_t e1 = p->h_face_elem[f * 4], l1 = p->h_face_elem[f * 4 + 1];
+    const int32_t e2 = p->h_face_elem[f * 4 + 2], l2 = p->h_face_elem[f * 4 + 3];
+    fsum[ff * 4] = e1;
+    fsum[ff * 4 + 1] = pos[(int64_t)e1 * nl + l1];
+    if (e2 >= 0) {
+      fsum[ff * 4 + 2] = e2;
+      fsum[ff * 4 + 3] = pos[(int64_t)e2 * nl + l2];
+    }
+  }
+  std::vector<int32_t> bjn(nf), bjc(nf, 1);
+  for (int64_t f = 0; f < nf; ++f) bjn[f] = (int32_t)f;
+  p->h_nbr = nbr;
+  p->d_nbr = p->upload(nbr);
+  p->d_cnt = p->upload(cnt);
+  p->d_slot_e = p->upload(se);
+  p->d_slot_lr = p->upload(slr);
+  p->d_slot_lc = p->upload(slc);
+  p->d_diag2 = p->upload(diag2);
+  p->d_rhs_src = p->upload(rsrc);
+  p->d_asm_lf = p->upload(alf);
+  p->d_asm_cnt = p->upload(acnt);
+  p->d_asm_face_free = p->upload(aff);
+  p->d_fsum = p->upload(fsum);
+  p->d_bj_nbr = p->upload(bjn);
+  p->d_bj_cnt = p->upload(bjc);
+  p->d_elem_face = p->upload(p->h_elem_face);
+  p->d_free_of_face = p->upload(p->h_free_of_face);
+  p->d_face_dir = p->upload(p->h_face_dir);
+  return HDG_OK;
+}
+
+// per-element input sizes (doubles)
+struct InSizes {
+  int64_t Me, Bd, Cd, D, E, F, G, H, J, ru, ruh, total;
+};
+InSizes in_sizes(hdg_problem p) {
+  InSizes s;
+  s.Me = (int64_t)p->PE * p->PE;
+  s.Bd = (int64_t)p->D * p->PE * p->PE;
+  s.Cd = (int64_t)p->D * p->PE * p->nlPF;
+  s.D = (int64_t)p->MPE * p->MDPE;
+  s.E = (int64_t)p->MPE * p->MPE;
+  s.F = (int64_t)p->MPE * p->nlb;
+  s.G = (int64_t)p->nlb * p->MDPE;
+  s.H = (int64_t)p->nlb * p->MPE;
+  s.J = (int64_t)p->nlb * p->nlb;
+  s.ru = (int64_t)p->MPE * p->R;
+  s.ruh = (int64_t)p->nlb * p->R;
+  s.total = s.Me + s.Bd + s.Cd + s.D + s.E + s.F + s.G + s.H + s.J + s.ru + s.ruh;
+  return s;
+}
+int64_t tmp_per_elem(hdg_problem p) {
+  return (int64_t)p->PE * p->PE + (int64_t)p->MPE * p->MPE + (int64_t)p->MPE * p->nlb + (int64_t)p->nlb * p->MPE;
+}
+
+GemmDesc gd(int M, int N, int K, const double* A, int64_t lda, int64_t sA0, int64_t sA1, const double* B,
+            int64_t ldb, int64_t sB0, int64_t sB1, double* C, int64_t ldc, int64_t sC0, int64_t sC1, double alpha,
+            double beta, int nb0, int nb1, int cg = 0, int64_t cgs = 0) {
+  GemmDesc d;
+  d.M = M; d.N = N; d.K = K;
+  d.A = A; d.lda = lda; d.sA0 = sA0; d.sA1 = sA1;
+  d.B = B; d.ldb = ldb; d.sB0 = sB0; d.sB1 = sB1;
+  d.C = C; d.ldc = ldc; d.sC0 = sC0; d.sC1 = sC1;
+  d.alpha = alpha; d.beta = beta; d.nb0 = nb0; d.nb1 = nb1;
+  d.cg = cg > 0 ? cg : N;
+  d.cgs = cg > 0 ? cgs : N;
+  return d;
+}
+
+// Condense elements [e0, e0+ec) whose inputs are device arrays laid out as in hdg.h.
+void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, const double* Bd, const double* Cd,
+                    const double* Dm, const double* Em, const double* Fm, const double* Gm, const double* Hm,
+                    const double* Jm, const double* ru, const double* ruh, cudaStream_t s) {
+  const int PE = p->PE, D = p->D, M = p->M, PF = p->PF, MPE = p->MPE, MDPE = p->MDPE, nlb = p->nlb,
+            nlPF = p->nlPF, R = p->R;
+  const int n = (int)ec;
+  double* Minv = p->d_tmp;
+  double* Eb = Minv + ec * PE * PE;
+  double* Fb = Eb + ec * MPE * MPE;
+  double* Hb = Fb + ec * MPE * nlb;
+  double* MinvB = p->d_MinvB + e0 * D * PE * PE;
+  double* MinvC = p->d_MinvC + e0 * D * PE * nlPF;
+  double* XF = p->d_XF + e0 * MPE * nlb;
+  double* Xr = p->d_Xr + e0 * MPE * R;
+  double* Kb = p->d_Kbar + e0 * nlb * nlb;
+  double* rb = p->d_rbar + e0 * nlb * R;
+  // (M^e)^{-1}                                                   (Eq. w16)
+  CK(cudaMemcpyAsync(Minv, Me, sizeof(double) * ec * PE * PE, cudaMemcpyDeviceToDevice, s));
+  inverse_f64(Minv, PE, (int64_t)PE * PE, ec, p->d_err, s);
+  // (M^e)^{-1} B_d, (M^e)^{-1} C_d
+  gemm_f64(gd(PE, PE, PE, Minv, PE, PE * PE, 0, Bd, PE, (int64_t)D * PE * PE, PE * PE, MinvB, PE,
+              (int64_t)D * PE * PE, PE * PE, 1.0, 0.0, n, D), s);
+  gemm_f64(gd(PE, nlPF, PE, Minv, PE, PE * PE, 0, Cd, nlPF, (int64_t)D * PE * nlPF, (int64_t)PE * nlPF, MinvC, nlPF,
+              (int64_t)D * PE * nlPF, (int64_t)PE * nlPF, 1.0, 0.0, n, D), s);
+  // Ebar = E - D A^{-1} B, per component block b: D[:, (b,.,.)] * stack_d (M^e)^{-1}B_d   (Eq. w19)
+  CK(cudaMemcpyAsync(Eb, Em, sizeof(double) * ec * MPE * MPE, cudaMemcpyDeviceToDevice, s));
+  gemm_f64(gd(MPE, PE, D * PE, Dm, MDPE, (int64_t)MPE * MDPE, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0,
+              Eb, MPE, (int64_t)MPE * MPE, PE, -1.0, 1.0, n, M), s);
+  // Fbar = F - D A^{-1} C, output columns (l, b, j)
+  CK(cudaMemcpyAsync(Fb, Fm, sizeof(double) * ec * MPE * nlb, cudaMemcpyDeviceToDevice, s));
+  gemm_f64(gd(MPE, nlPF, D * PE, Dm, MDPE, (int64_t)MPE * MDPE, (int64_t)D * PE, MinvC, nlPF,
+              (int64_t)D * PE * nlPF, 0, Fb, nlb, (int64_t)MPE * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF),
+           s);
+  // Hbar = H - G A^{-1} B                                       (Eq. w21)
+  CK(cudaMemcpyAsync(Hb, Hm, sizeof(double) * ec * nlb * MPE, cudaMemcpyDeviceToDevice, s));
+  gemm_f64(gd(nlb, PE, D * PE, Gm, MDPE, (int64_t)nlb * MDPE, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0,
+              Hb, MPE, (int64_t)nlb * MPE, PE, -1.0, 1.0, n, M), s);
+  // Jbar = J - G A^{-1} C  (written into Kbar)
+  CK(cudaMemcpyAsync(Kb, Jm, sizeof(double) * ec * nlb * nlb, cudaMemcpyDeviceToDevice, s));
+  gemm_f64(gd(nlb, nlPF, D * PE, Gm, MDPE, (int64_t)nlb * MDPE, (int64_t)D * PE, MinvC, nlPF,
+              (int64_t)D * PE * nlPF, 0, Kb, nlb, (int64_t)nlb * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF),
+           s);
+  // Ebar^{-1}; X_F = Ebar^{-1} Fbar; X_r = Ebar^{-1} r_u
+  inverse_f64(Eb, MPE, (int64_t)MPE * MPE, ec, p->d_err, s);
+  gemm_f64(gd(MPE, nlb, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlb, (int64_t)MPE * nlb, 0, XF, nlb,
+              (int64_t)MPE * nlb, 0, 1.0, 0.0, n, 1), s);
+  gemm_f64(gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, (int64_t)MPE * R, 0, Xr, R, (int64_t)MPE * R, 0, 1.0,
+              0.0, n, 1), s);
+  // Kbar = Jbar - Hbar X_F ; rbar = r_uh - Hbar X_r              (Eq. w22)
+  gemm_f64(gd(nlb, nlb, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, XF, nlb, (int64_t)MPE * nlb, 0, Kb, nlb,
+              (int64_t)nlb * nlb, 0, -1.0, 1.0, n, 1), s);
+  CK(cudaMemcpyAsync(rb, ruh, sizeof(double) * ec * nlb * R, cudaMemcpyDeviceToDevice, s));
+  gemm_f64(gd(nlb, R, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, Xr, R, (int64_t)MPE * R, 0, rb, R, (int64_t)nlb * R, 0,
+              -1.0, 1.0, n, 1), s);
+}
+
+// ------------------------------------------------------------------ operators
+struct Ops {
+  hdg_problem p;
+  cudaStream_t s;
+  int R;
+
+  void mv_timed_begin(cudaEvent_t* a) {
+    if (!p->timing) return;
+    if (p->ev_used + 2 > p->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        p->ev_pool.push_back(e);
+      }
+    }
+    *a = p->ev_pool[p->ev_used];
+    CK(cudaEventRecord(*a, s));
+  }
+  void mv_timed_end() {
+    if (!p->timing) return;
+    CK(cudaEventRecord(p->ev_pool[p->ev_used + 1], s));
+    p->ev_used += 2;
+  }
+
+  // y = K x (prec storage), epilogue
+  void K(int prec, const double* x, double* y, int epi, const double* rhs, const double* scale, const int* active) {
+    BlockRowDesc d{};
+    d.prec = prec;
+    d.blk = prec == HDG_FP64 ? (const void*)p->K64 : prec == HDG_FP32 ? (const void*)p->K32 : (const void*)p->K16;
+    d.blk_stride = prec == HDG_FP64 ? p->s64 : prec == HDG_FP32 ? p->s32 : p->s16;
+    d.nbr = p->d_nbr;
+    d.cnt = p->d_cnt;
+    d.n_units = p->nfree;
+    d.b_rows = p->b;
+    d.bc = p->b;
+    d.max_slots = p->ms;
+    d.R = R;
+    d.in = x;
+    d.out = y;
+    d.epi = epi;
+    d.rhs = rhs;
+    d.scale = scale;
+    d.active = active;
+    d.err = p->d_err;
+    cudaEvent_t a;
+    mv_timed_begin(&a);
+    blockrow(d, p->br_variant, s);
+    mv_timed_end();
+  }
+  // y = M^{-1} x for the base preconditioner
+  void Minv(int pc, int prec, const double* x, double* y, const int* active) {
+    if (pc == HDG_PC_NONE) {
+      launch_axpby(y, x, 1.0, 0.0, p->ndof * R, active, R, s);
+      return;
+    }
+    BlockRowDesc d{};
+    d.prec = prec;
+    d.R = R;
+    d.in = x;
+    d.epi = EPI_STORE;
+    d.active = active;
+    d.err = p->d_err;
+    d.bc = p->b;
+    if (pc == HDG_PC_BJ) {
+      d.blk = prec == HDG_FP64 ? (const void*)p->bj64 : prec == HDG_FP32 ? (const void*)p->bj32 : (const void*)p->bj16;
+      d.blk_stride = prec == HDG_FP64 ? p->bs64 : prec == HDG_FP32 ? p->bs32 : p->bs16;
+      d.nbr = p->d_bj_nbr;
+      d.cnt = p->d_bj_cnt;
+      d.n_units = p->nfree;
+      d.b_rows = p->b;
+      d.max_slots = 1;
+      d.out = y;
+      blockrow(d, p->br_variant, s);
+    } else {
+      d.blk = prec == HDG_FP64 ? (const void*)p->as64 : prec == HDG_FP32 ? (const void*)p->as32 : (const void*)p->as16;
+      d.blk_stride = prec == HDG_FP64 ? p->as_s64 : prec == HDG_FP32 ? p->as_s32 : p->as_s16;
+      d.nbr = p->d_asm_face_free;
+      d.cnt = p->d_asm_cnt;
+      d.n_units = p->NE;
+      d.b_rows = p->nlb;
+      d.max_slots = p->nl;
+      d.out = p->ze;
+      blockrow(d, p->br_variant, s);
+      asm_face_sum(p->ze, p->nlb, p->b, R, p->nfree, p->d_fsum, y, s);
+    }
+  }
+  // y = A x with A = M^{-1} K
+  void A(int pc, int kprec, int mprec, const double* x, double* y, const int* active) {
+    if (pc == HDG_PC_NONE) {
+      K(kprec, x, y, EPI_STORE, nullptr, nullptr, active);
+    } else {
+      K(kprec, x, p->ptmp, EPI_STORE, nullptr, nullptr, active);
+      Minv(pc, mprec, p->ptmp, y, active);
+    }
+  }
+  // y = P^{-1} x : polynomial p(M^{-1}K) applied to M^{-1} x, or M^{-1} x.
+  void Pinv(const hdg_solver_opts& o, int mprec, int kpoly, const double* x, double* y, const int* active) {
+    const int64_t len = p->ndof * R;
+    if (o.poly == HDG_POLY_NONE || p->poly_n == 0) {
+      Minv(o.pc, mprec, x, y, active);
+      return;
+    }
+    double* q = p->pq;
+    Minv(o.pc, mprec, x, q, active);
+    if (o.poly == HDG_POLY_GMRES) {
+      // Sec. 4.7 recurrence, real values and conjugate pairs
+      const int P = p->poly_n;
+      int i = 0;
+      bool first = true;
+      while (i < P) {
+        const double a = p->th_re[i], bi = p->th_im[i];
+        if (bi == 0.0) {
+          const bool last = (i == P - 1);
+          if (!last) A(o.pc, kpoly, mprec, q, p->pAq, active);
+          launch_pp_real(y, q, p->pAq, 1.0 / a, len, last ? 0 : 1, active, R, first ? 1 : 0, s);
+          i += 1;
+        } else {
+          const double mod2 = a * a + bi * bi;
+          const bool last = (i + 1 >= P - 1);
+          A(o.pc, kpoly, mprec, q, p->pAq, active);
+          launch_pp_pair_t(p->pt, y, q, p->pAq, 2.0 * a, 1.0 / mod2, len, active, R, first ? 1 : 0, s);
+          if (!last) {
+            A(o.pc, kpoly, mprec, p->pt, p->pAq, active);
+            launch_pp_pair_q(q, p->pAq, 1.0 / mod2, len, active, R, s);
+          }
+          i += 2;
+        }
+        first = false;
+      }
+    } else {
+      // Chebyshev iteration (Saad, Alg. 12.1) with degree+1 steps from z = 0
+      const double theta = 0.5 * (p->cheb_b + p->cheb_a), delta = 0.5 * (p->cheb_b - p->cheb_a);
+      const double sigma = theta / delta;
+      double rho = 1.0 / sigma;
+      double* r = q;          // residual, starts at M^{-1} x
+      double* d = p->pt;
+      launch_axpby(d, r, 1.0 / theta, 0.0, len, active, R, s);
+      for (int kq = 0; kq <= p->poly_n; ++kq) {
+        launch_cheb(y, d, r, nullptr, 0, 0, len, kq == 0 ? 0 : 1, active, R, s);
+        if (kq == p->poly_n) break;
+        A(o.pc, kpoly, mprec, d, p->pAq, active);
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        launch_cheb(y, d, r, p->pAq, rho_new * rho, 2.0 * rho_new / delta, len, 2, active, R, s);
+        rho = rho_new;
+      }
+    }
+  }
+};
+
+void ensure_workspace(hdg_problem p, int m) {
+  if (p->ws_m >= m) return;
+  const int64_t len = p->ndof * p->R;
+  const int R = p->R;
+  auto A = [&](size_t nb) { return p->dalloc(nb); };
+  if (p->ws_m < 0) {
+    p->d_x = (double*)A(sizeof(double) * len);
+    p->t1 = (double*)A(sizeof(double) * len);
+    p->res = (double*)A(sizeof(double) * len);
+    p->pq = (double*)A(sizeof(double) * len);
+    p->pw = (double*)A(sizeof(double) * len);
+    p->ptmp = (double*)A(sizeof(double) * len);
+    p->pAq = (double*)A(sizeof(double) * len);
+    p->pt = (double*)A(sizeof(double) * len);
+    p->xo = (double*)A(sizeof(double) * len);
+    p->bo = (double*)A(sizeof(double) * len);
+    p->ze = (double*)A(sizeof(double) * p->NE * p->nlb * R);
+    p->tolabs = (double*)A(sizeof(double) * kMaxR);
+    p->cfac = (double*)A(sizeof(double) * kMaxR);
+    p->zb = (double*)A(sizeof(double) * kMaxR);
+    p->bnorm = (double*)A(sizeof(double) * kMaxR);
+    p->rel = (double*)A(sizeof(double) * kMaxR);
+    p->running = (int*)A(sizeof(int) * kMaxR);
+    p->jend = (int*)A(sizeof(int) * kMaxR);
+    p->on_estimate = (int*)A(sizeof(int) * kMaxR);
+    p->done = (int*)A(sizeof(int) * kMaxR);
+    p->iters = (int*)A(sizeof(int) * kMaxR);
+    p->counter = (unsigned*)A(sizeof(unsigned) * 4);
+    CK(cudaMemset(p->counter, 0, sizeof(unsigned) * 4));
+    CK(cudaMemset(p->d_x, 0, sizeof(double) * len));
+  } else {
+    p->dfree(p->V, 0);
+    p->dfree(p->vscale, 0);
+    p->dfree(p->H, 0);
+    p->dfree(p->g, 0);
+    p->dfree(p->cs, 0);
+    p->dfree(p->sn, 0);
+    p->dfree(p->hcol, 0);
+    p->dfree(p->htmp, 0);
+    p->dfree(p->ycoef, 0);
+    p->dfree(p->partial, 0);
+  }
+  p->V = (double*)A(sizeof(double) * (m + 1) * len);
+  p->vscale = (double*)A(sizeof(double) * (m + 1) * R);
+  p->H = (double*)A(sizeof(double) * R * (m + 1) * m);
+  p->g = (double*)A(sizeof(double) * R * (m + 1));
+  p->cs = (double*)A(sizeof(double) * R * m);
+  p->sn = (double*)A(sizeof(double) * R * m);
+  p->hcol = (double*)A(sizeof(double) * R * (m + 2));
+  p->htmp = (double*)A(sizeof(double) * R * (m + 2));
+  p->ycoef = (double*)A(sizeof(double) * R * (m + 1));
+  // reductions use at most 1024 blocks (see gmres_chunk)
+  p->partial = (double*)A(sizeof(double) * (int64_t)(m + 2) * 1024 * R);
+  p->ws_m = m;
+}
+
+GmresView make_view(hdg_problem p, int R, int m, double rtol, int maxit) {
+  GmresView k{};
+  k.n = p->ndof;
+  k.R = R;
+  k.m = m;
+  k.chunk = gmres_chunk(p->ndof * R);
+  k.V = p->V;
+  k.vscale = p->vscale;
+  k.H = p->H;
+  k.g = p->g;
+  k.cs = p->cs;
+  k.sn = p->sn;
+  k.hcol = p->hcol;
+  k.htmp = p->htmp;
+  k.ycoef = p->ycoef;
+  k.partial = p->partial;
+  k.tolabs = p->tolabs;
+  k.cfac = p->cfac;
+  k.zb = p->zb;
+  k.rtol = rtol;
+  k.running = p->running;
+  k.jend = p->jend;
+  k.on_estimate = p->on_estimate;
+  k.done = p->done;
+  k.iters = p->iters;
+  k.maxit = maxit;
+  k.counter = p->counter;
+  k.err = p->d_err;
+  return k;
+}
+
+// One Arnoldi orthogonalisation of V_{j+1} against V_0..V_j.
+void orthogonalize(const GmresView& k, int orth, int j, cudaStream_t s) {
+  double* w = k.V + (int64_t)(j + 1) * k.n * k.R;
+  if (orth == HDG_ORTH_MGS) {
+    for (int i = 0; i <= j; ++i) {
+      launch_dots(k, w, i, i + 1, s);
+      launch_update(k, w, i, i + 1, j, 0, i == j ? 1 : 0, s);
+    }
+  } else {
+    launch_dots(k, w, 0, j + 1, s);
+    launch_update(k, w, 0, j + 1, j, 0, orth == HDG_ORTH_CGS2 ? 0 : 1, s);
+    if (orth == HDG_ORTH_CGS2) {
+      launch_dots(k, w, 0, j + 1, s);
+      launch_update(k, w, 0, j + 1, j, 1, 1, s);
+    }
+  }
+}
+
+void set_ints(hdg_problem p, int* dptr, int v, int R, cudaStream_t s) {
+  for (int r = 0; r < R; ++r) p->h_int[r] = v;
+  CK(cudaMemcpyAsync(dptr, p->h_int, sizeof(int) * R, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+}
+void set_dbls(hdg_problem p, double* dptr, double v, int R, cudaStream_t s) {
+  for (int r = 0; r < R; ++r) p->h_dbl[r] = v;
+  CK(cudaMemcpyAsync(dptr, p->h_dbl, sizeof(double) * R, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+struct GmresResult {
+  int iters = 0, restarts = 0;
+  bool converged = false;
+  double rel = 0.0;
+  hdg_status st = HDG_OK;
+};
+
+// Restarted left-preconditioned GMRES(m) for the R right-hand sides b
+// (device, n x R); x (device) receives the solution, starting from 0.
+//  true_check = 1: accept on the true residual ||b - K64 x|| <= rtol ||b||
+//                  (FP64), dividing the cycle tolerance by 10 after a false
+//                  stop on the least-squares estimate.
+//  true_check = 0: (inner solve) stop when a cycle ends on the estimate.
+GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec, int kpoly, const double* b,
+                  double* x, double rtol, int maxit, int true_check, cudaStream_t s) {
+  GmresResult out;
+  const int R = p->R, m = o.restart;
+  const int64_t len = p->ndof * R;
+  Ops ops{p, s, R};
+  GmresView k = make_view(p, R, m, rtol, maxit);
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * len, s));
+  CK(cudaMemsetAsync(p->iters, 0, sizeof(int) * R, s));
+  CK(cudaMemsetAsync(p->done, 0, sizeof(int) * R, s));
+  set_ints(p, p->running, 1, R, s);
+  set_dbls(p, p->cfac, 1.0, R, s);
+  // ||b|| and ||P^{-1} b||
+  launch_norms(k, b, p->bnorm, 0, nullptr, s);
+  ops.Pinv(o, mprec, kpoly, b, p->t1, p->running);
+  launch_norms(k, p->t1, p->zb, 0, nullptr, s);
+  CK(cudaMemcpyAsync(p->res, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> cf(R, 1.0);
+  std::vector<int> done(R, 0);
+  int total_iters = 0;
+  while (true) {
+    // true relative residual of the current iterate
+    launch_norms(k, p->res, p->rel, 0, p->bnorm, s);
+    CK(cudaMemcpyAsync(p->h_dbl, p->rel, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->h_int, p->on_estimate, sizeof(int) * R, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->h_int + kMaxR, p->iters, sizeof(int) * R, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    hdg_status est = check_err(p, s);
+    if (est != HDG_OK) {
+      out.st = est;
+      break;
+    }
+    double worst = 0.0;
+    bool all_done = true;
+    int mx_it = 0;
+    for (int r = 0; r < R; ++r) {
+      const double rel = p->h_dbl[r];
+      worst = std::max(worst, rel);
+      mx_it = std::max(mx_it, p->h_int[kMaxR + r]);
+      if (true_check) {
+        if (out.restarts > 0 && p->h_int[r] && rel > rtol) cf[r] *= 0.1;
+        done[r] = rel <= rtol ? 1 : 0;
+      } else {
+        done[r] = (out.restarts > 0 && p->h_int[r]) || rel == 0.0 ? 1 : 0;
+      }
+      if (!done[r]) all_done = false;
+    }
+    out.rel = worst;
+    total_iters = mx_it;
+    if (all_done) {
+      out.converged = true;
+      break;
+    }
+    if (total_iters >= maxit) break;
+    for (int r = 0; r < R; ++r) {
+      p->h_int[r] = done[r];
+      p->h_dbl[r] = cf[r];
+    }
+    CK(cudaMemcpyAsync(p->done, p->h_int, sizeof(int) * R, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->cfac, p->h_dbl, sizeof(double) * R, cudaMemcpyHostToDevice, s));
+    // start a cycle: V_0 = P^{-1} res, beta = ||V_0||
+    set_ints(p, p->running, 1, R, s);
+    ops.Pinv(o, mprec, kpoly, p->res, p->V, nullptr);
+    launch_norms(k, p->V, nullptr, 1, nullptr, s);
+    for (int j = 0; j < m; ++j) {
+      double* vj = p->V + (int64_t)j * len;
+      double* vn = p->V + (int64_t)(j + 1) * len;
+      ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running);
+      ops.Pinv(o, mprec, kpoly, p->t1, vn, p->running);
+      orthogonalize(k, o.orth, j, s);
+    }
+    launch_backsolve(k, s);
+    launch_xupdate(k, x, s);
+    // true residual with the FP64 matrix (outer) or the solve's own matrix (inner)
+    ops.K(true_check ? HDG_FP64 : kprec, x, p->res, EPI_RESID, b, nullptr, nullptr);
+    out.restarts += 1;
+  }
+  out.iters = total_iters;
+  return out;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* hdg_status_str(hdg_status s) {
+  switch (s) {
+    case HDG_OK: return "ok";
+    case HDG_ERR_ARG: return "invalid argument";
+    case HDG_ERR_OOM: return "out of device memory";
+    case HDG_ERR_BUDGET: return "memory budget exceeded";
+    case HDG_ERR_SINGULAR: return "singular block";
+    case HDG_ERR_NOT_CONVERGED: return "not converged";
+    case HDG_ERR_BREAKDOWN: return "breakdown";
+    case HDG_ERR_NAN: return "NaN or Inf";
+    case HDG_ERR_TIMEOUT: return "device wait timed out";
+    case HDG_ERR_CUDA: return "CUDA error";
+    case HDG_ERR_STATE: return "call out of order";
+  }
+  return "unknown";
+}
+
+hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_problem* out) {
+  if (!mesh || !out) return HDG_ERR_ARG;
+  *out = nullptr;
+  if (mesh->dim < 2 || mesh->dim > 3 || mesh->n_lfe < 3 || mesh->n_lfe > 8 || mesh->M < 1 || mesh->PE < 1 ||
+      mesh->PF < 1 || mesh->n_elem < 1 || mesh->n_face < 1 || !mesh->elem_face || !mesh->face_elem ||
+      !mesh->face_dirichlet)
+    return HDG_ERR_ARG;
+  if (!(nrhs == 1 || nrhs == 2 || nrhs == 4 || nrhs == 8)) return HDG_ERR_ARG;
+  hdg_problem p = new (std::nothrow) hdg_problem_s();
+  if (!p) return HDG_ERR_OOM;
+  try {
+    DeviceGuard dg(device);
+    p->device = device;
+    p->dim = mesh->dim;
+    p->D = mesh->dim;
+    p->nl = mesh->n_lfe;
+    p->M = mesh->M;
+    p->PE = mesh->PE;
+    p->PF = mesh->PF;
+    p->NE = mesh->n_elem;
+    p->NF = mesh->n_face;
+    p->R = nrhs;
+    p->b = p->M * p->PF;
+    p->nlb = p->nl * p->b;
+    p->ms = 2 * p->nl - 1;
+    p->nlPF = p->nl * p->PF;
+    p->MPE = p->M * p->PE;
+    p->MDPE = p->M * p->D * p->PE;
+    if (p->b > 512 || p->nlb > 512) {
+      delete p;
+      return HDG_ERR_ARG;
+    }
+    p->h_elem_face.assign(mesh->elem_face, mesh->elem_face + p->NE * p->nl);
+    p->h_face_elem.assign(mesh->face_elem, mesh->face_elem + p->NF * 4);
+    p->h_face_dir.assign(mesh->face_dirichlet, mesh->face_dirichlet + p->NF);
+    for (auto& v : p->h_face_dir) v = v ? 1 : 0;
+    CK(cudaMallocHost(&p->h_dbl, sizeof(double) * 4 * kMaxR + 64));
+    CK(cudaMallocHost(&p->h_int, sizeof(int) * 4 * kMaxR + 64));
+    CK(cudaMallocHost(&p->h_err, sizeof(unsigned) * 4));
+    p->d_err = (unsigned*)p->dalloc(sizeof(unsigned) * 4);
+    CK(cudaMemset(p->d_err, 0, sizeof(unsigned) * 4));
+    hdg_status st = build_maps(p);
+    if (st != HDG_OK) {
+      hdg_problem_destroy(p);
+      return st;
+    }
+    const int R = p->R, D = p->D, PE = p->PE, MPE = p->MPE, nlb = p->nlb, nlPF = p->nlPF;
+    p->d_Kbar = (double*)p->dalloc(sizeof(double) * p->NE * nlb * nlb);
+    p->d_rbar = (double*)p->dalloc(sizeof(double) * p->NE * nlb * R);
+    p->d_MinvB = (double*)p->dalloc(sizeof(double) * p->NE * D * PE * PE);
+    p->d_MinvC = (double*)p->dalloc(sizeof(double) * p->NE * D * PE * nlPF);
+    p->d_XF = (double*)p->dalloc(sizeof(double) * p->NE * MPE * nlb);
+    p->d_Xr = (double*)p->dalloc(sizeof(double) * p->NE * MPE * R);
+    p->d_uhatD = (double*)p->dalloc(sizeof(double) * p->NF * p->b * R);
+    CK(cudaMemset(p->d_uhatD, 0, sizeof(double) * p->NF * p->b * R));
+    p->condensed.assign(p->NE, 0);
+    // condensation chunk: inputs + temporaries of ~1 GiB
+    const int64_t per = in_sizes(p).total + tmp_per_elem(p);
+    int64_t ch = (int64_t)((1ll << 30) / (per * 8));
+    ch = std::max<int64_t>(1, std::min<int64_t>(ch, p->NE));
+    p->chunk = ch;
+    p->d_stage = (double*)p->dalloc(sizeof(double) * ch * in_sizes(p).total);
+    p->d_tmp = (double*)p->dalloc(sizeof(double) * ch * tmp_per_elem(p));
+    p->s64 = padded_stride<double>((int64_t)p->b * p->b);
+    p->s32 = padded_stride<float>((int64_t)p->b * p->b);
+    p->s16 = padded_stride<__nv_bfloat16>((int64_t)p->b * p->b);
+    *out = p;
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    hdg_problem_destroy(p);
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    hdg_problem_destroy(p);
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_problem_destroy(hdg_problem p) {
+  if (!p) return HDG_OK;
+  DeviceGuard dg(p->device);
+  for (void* q : p->allocs) cudaFree(q);
+  p->allocs.clear();
+  for (auto e : p->ev_pool) cudaEventDestroy(e);
+  if (p->h_dbl) cudaFreeHost(p->h_dbl);
+  if (p->h_int) cudaFreeHost(p->h_int);
+  if (p->h_err) cudaFreeHost(p->h_err);
+  delete p;
+  return HDG_OK;
+}
+
+size_t hdg_problem_device_bytes(hdg_problem p) { return p ? p->bytes : 0; }
+
+size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts* opts) {
+  if (!mesh) return 0;
+  const int64_t NE = mesh->n_elem, NF = mesh->n_face;
+  const int64_t b = (int64_t)mesh->M * mesh->PF, nl = mesh->n_lfe, nlb = nl * b, PE = mesh->PE,
+                D = mesh->dim, MPE = (int64_t)mesh->M * PE, R = nrhs;
+  int64_t nfree = 0;
+  for (int64_t f = 0; f < NF; ++f) nfree += mesh->face_dirichlet[f] ? 0 : 1;
+  const int64_t ms = 2 * nl - 1;
+  int64_t by = 0;
+  by += NE * (nlb * nlb + nlb * R + D * PE * PE + D * PE * nl * mesh->PF + MPE * nlb + MPE * R) * 8;
+  by += NF * b * R * 8;
+  by += (int64_t)(1ll << 30) + (1ll << 28);                     // staging + temporaries (upper bound)
+  by += nfree * ms * b * b * (8 + 4);                             // K in FP64 + FP32
+  if (opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16)) by += nfree * ms * b * b * 2;
+  by += nfree * b * b * (8 + 4 + 8);                              // BJ
+  if (opts && opts->pc == HDG_PC_ASM) by += NE * nlb * nlb * (8 + 8 + 4);
+  const int m = opts ? opts->restart : 50;
+  by += (int64_t)(m + 12) * nfree * b * R * 8;
+  by += NE * nlb * R * 8;
+  return (size_t)by;
+}
+
+hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count, const double* Me, const double* Bd,
+                        const double* Cd, const double* Dm, const double* Em, const double* Fm, const double* Gm,
+                        const double* Hm, const double* Jm, const double* ru, const double* ruh, int on_device,
+                        void* stream) {
+  if (!p) return HDG_ERR_ARG;
+  if (e0 < 0 || count < 0 || e0 + count > p->NE) return HDG_ERR_ARG;
+  if (!Me || !Bd || !Cd || !Dm || !Em || !Fm || !Gm || !Hm || !Jm || !ru || !ruh) return HDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    const InSizes z = in_sizes(p);
+    const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int64_t c0 = 0; c0 < count; c0 += p->chunk) {
+      const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
+      const double* src[11] = {Me, Bd, Cd, Dm, Em, Fm, Gm, Hm, Jm, ru, ruh};
+      const int64_t sz[11] = {z.Me, z.Bd, z.Cd, z.D, z.E, z.F, z.G, z.H, z.J, z.ru, z.ruh};
+      const double* dev[11];
+      double* st = p->d_stage;
+      for (int i = 0; i < 11; ++i) {
+        const double* base = src[i] + c0 * sz[i];
+        if (on_device) {
+          dev[i] = base;
+        } else {
+          CK(cudaMemcpyAsync(st, base, sizeof(double) * ec * sz[i], kind, s));
+          dev[i] = st;
+          st += ec * sz[i];
+        }
+      }
+      condense_chunk(p, e0 + c0, ec, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], dev[7], dev[8], dev[9],
+                     dev[10], s);
+      CK(cudaGetLastError());
+      for (int64_t e = e0 + c0; e < e0 + c0 + ec; ++e) {
+        if (!p->condensed[e]) {
+          p->condensed[e] = 1;
+          p->n_condensed++;
+        }
+      }
+    }
+    p->assembled = false;
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
+}
+
+hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhatD, int on_device, void* stream) {
+  if (!p || !uhatD) return HDG_ERR_ARG;
+  try {
+    DeviceGuard dg(p->device);
+    CK(cudaMemcpyAsync(p->d_uhatD, uhatD, sizeof(double) * p->NF * p->b * p->R,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    if (!on_device) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    p->assembled = false;
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
+}
+
+hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream) {
+  if (!p) return HDG_ERR_ARG;
+  if (p->n_condensed != p->NE) return HDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    const int64_t rows = p->nfree * p->ms;
+    if (!p->K64) p->K64 = (double*)p->dalloc(sizeof(double) * rows * p->s64);
+    if (!p->K32) p->K32 = (float*)p->dalloc(sizeof(float) * rows * p->s32);
+    const bool need16 = opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16);
+    if (need16 && !p->K16) p->K16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * rows * p->s16);
+    if (!p->d_r) p->d_r = (double*)p->dalloc(sizeof(double) * p->ndof * p->R);
+    AssembleDesc d{};
+    d.Kbar = p->d_Kbar;
+    d.rbar = p->d_rbar;
+    d.uhatD = p->d_uhatD;
+    d.nlb = p->nlb;
+    d.b = p->b;
+    d.nl = p->nl;
+    d.R = p->R;
+    d.max_slots = p->ms;
+    d.n_free = p->nfree;
+    d.slot_e = p->d_slot_e;
+    d.slot_lr = p->d_slot_lr;
+    d.slot_lc = p->d_slot_lc;
+    d.diag2 = p->d_diag2;
+    d.rhs_src = p->d_rhs_src;
+    d.elem_face = p->d_elem_face;
+    d.face_dir = p->d_face_dir;
+    d.K64 = p->K64;
+    d.s64 = p->s64;
+    d.K32 = p->K32;
+    d.s32 = p->s32;
+    d.K16 = p->K16;
+    d.s16 = p->s16;
+    d.r = p->d_r;
+    assemble(d, s);
+    CK(cudaGetLastError());
+    hdg_status st = check_err(p, s);
+    if (st != HDG_OK) return st;
+    p->assembled = true;
+    p->pc_ready = -1;
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const double* v0, void* stream) {
+  if (!p || !o) return HDG_ERR_ARG;
+  if (!p->assembled) return HDG_ERR_STATE;
+  if (o->pc < HDG_PC_NONE || o->pc > HDG_PC_ASM || o->poly < 0 || o->poly > 2) return HDG_ERR_ARG;
+  if (o->poly != HDG_POLY_NONE && (o->poly_degree < 1 || o->poly_degree > kMaxPoly || !v0)) return HDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    const int b = p->b;
+    const bool need16 = (o->poly_prec == HDG_BF16 || o->inner_prec == HDG_BF16);
+    if (o->pc == HDG_PC_BJ) {
+      double* tmp = (double*)p->dalloc(sizeof(double) * p->nfree * b * b);
+      extract_diag(p->K64, p->s64, p->ms, b, p->nfree, tmp, s);
+      inverse_f64(tmp, b, (int64_t)b * b, p->nfree, p->d_err, s);
+      p->bs64 = padded_stride<double>((int64_t)b * b);
+      p->bs32 = padded_stride<float>((int64_t)b * b);
+      p->bs16 = padded_stride<__nv_bfloat16>((int64_t)b * b);
+      if (!p->bj64) p->bj64 = (double*)p->dalloc(sizeof(double) * p->nfree * p->bs64);
+      if (!p->bj32) p->bj32 = (float*)p->dalloc(sizeof(float) * p->nfree * p->bs32);
+      if (need16 && !p->bj16) p->bj16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * p->nfree * p->bs16);
+      pack_blocks(tmp, b, p->nfree, p->bj64, p->bs64, p->bj32, p->bs32, p->bj16, p->bs16, s);
+      hdg_status st = check_err(p, s);
+      p->dfree(tmp, sizeof(double) * p->nfree * b * b);
+      if (st != HDG_OK) return st;
+    } else if (o->pc == HDG_PC_ASM) {
+      const int nlb = p->nlb;
+      if (nlb > inverse_max_n()) return HDG_ERR_ARG;
+      double* P = (double*)p->dalloc(sizeof(double) * p->NE * nlb * nlb);
+      asm_build(p->d_Kbar, nlb, b, p->nl, p->NE, p->d_asm_lf, p->d_asm_cnt, p->d_asm_face_free, p->K64, p->s64, p->ms,
+                P, s);
+      inverse_f64(P, nlb, (int64_t)nlb * nlb, p->NE, p->d_err, s);
+      p->as_s64 = padded_stride<double>((int64_t)nlb * b);
+      p->as_s32 = padded_stride<float>((int64_t)nlb * b);
+      p->as_s16 = padded_stride<__nv_bfloat16>((int64_t)nlb * b);
+      if (!p->as64) p->as64 = (double*)p->dalloc(sizeof(double) * p->NE * p->nl * p->as_s64);
+      if (!p->as32) p->as32 = (float*)p->dalloc(sizeof(float) * p->NE * p->nl * p->as_s32);
+      if (need16 && !p->as16)
+        p->as16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * p->NE * p->nl * p->as_s16);
+      asm_pack(P, nlb, b, p->nl, p->NE, p->as64, p->as_s64, p->as32, p->as_s32, p->as16, p->as_s16, s);
+      hdg_status st = check_err(p, s);
+      p->dfree(P, sizeof(double) * p->NE * nlb * nlb);
+      if (st != HDG_OK) return st;
+    }
+    p->pc_ready = o->pc;
+    p->poly_n = 0;
+    p->poly_kind = o->poly;
+    if (o->poly != HDG_POLY_NONE) {
+      // one Arnoldi(P) cycle with MGS on A = M^{-1} K (FP64) from v0   (Sec. 4.7)
+      const int P = o->poly_degree;
+      const int Pa = (o->poly == HDG_POLY_CHEBYSHEV) ? std::max(P, 10) : P;
+      ensure_workspace(p, std::max(Pa, o->restart));
+      Ops ops{p, s, 1};
+      GmresView k = make_view(p, 1, Pa, 0.0, 1 << 30);
+      k.chunk = gmres_chunk(p->ndof);
+      // Arnoldi variant of the finalize step: the H column is stored unrotated
+      CK(cudaMemcpyAsync(p->V, v0, sizeof(double) * p->ndof, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemsetAsync(p->iters, 0, sizeof(int), s));
+      CK(cudaMemsetAsync(p->done, 0, sizeof(int), s));
+      CK(cudaMemsetAsync(p->H, 0, sizeof(double) * (Pa + 1) * Pa, s));
+      set_dbls(p, p->cfac, 1.0, 1, s);
+      set_dbls(p, p->zb, 0.0, 1, s);
+      launch_norms(k, p->V, nullptr, 1, nullptr, s);   // vscale_0 = 1/||v0||, running = 1
+      int Peff = Pa;
+      for (int j = 0; j < Pa; ++j) {
+        double* vj = p->V + (int64_t)j * p->ndof;
+        double* vn = p->V + (int64_t)(j + 1) * p->ndof;
+        ops.K(HDG_FP64, vj, p->t1, EPI_SCALE, nullptr, p->vscale + j, nullptr);
+        ops.Minv(o->pc, HDG_FP64, p->t1, vn, nullptr);
+        for (int i = 0; i <= j; ++i) {
+          launch_dots(k, vn, i, i + 1, s);
+          launch_update(k, vn, i, i + 1, j, 0, i == j ? 2 : 0, s);
+        }
+        CK(cudaMemcpyAsync(p->h_int, p->running, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!p->h_int[0]) {
+          Peff = j + 1;
+          break;
+        }
+      }
+      if (!p->d_poly) p->d_poly = (double*)p->dalloc(sizeof(double) * (2 * kMaxPoly + 2));
+      double* d_re = p->d_poly;
+      double* d_im = p->d_poly + kMaxPoly;
+      int* d_n = (int*)(p->d_poly + 2 * kMaxPoly);
+      launch_ritz_leja(p->H, Pa, Peff, o->poly == HDG_POLY_GMRES ? 1 : 0, d_re, d_im, d_n, p->d_err, s);
+      std::vector<double> hb(2 * kMaxPoly + 1);
+      CK(cudaMemcpyAsync(hb.data(), d_re, sizeof(double) * (2 * kMaxPoly + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      hdg_status st = check_err(p, s);
+      if (st != HDG_OK) return st;
+      int nth = 0;
+      std::memcpy(&nth, &hb[2 * kMaxPoly], sizeof(int));
+      if (o->poly == HDG_POLY_GMRES) {
+        p->th_re.assign(hb.begin(), hb.begin() + nth);
+        p->th_im.assign(hb.begin() + kMaxPoly, hb.begin() + kMaxPoly + nth);
+        p->poly_n = nth;
+      } else {
+        double lo = 1e300, hi = -1e300;
+        for (int i = 0; i < nth; ++i) {
+          lo = std::min(lo, hb[i]);
+          hi = std::max(hi, hb[i]);
+        }
+        p->cheb_a = 0.9 * lo;
+        p->cheb_b = 1.1 * hi;
+        p->poly_n = P;
+      }
+    }
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* o, void* stream, hdg_solve_info* info) {
+  if (!p || !o) return HDG_ERR_ARG;
+  if (!p->assembled || p->pc_ready != o->pc) return HDG_ERR_STATE;
+  if (o->restart < 1 || o->restart + 1 > kMaxBasis || o->max_iters < 1 || !(o->rtol > 0.0)) return HDG_ERR_ARG;
+  if (o->poly != HDG_POLY_NONE && (p->poly_n == 0 || p->poly_kind != o->poly)) return HDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    ensure_workspace(p, o->restart);
+    p->ev_used = 0;
+    hdg_solve_info inf{};
+    hdg_status st = HDG_OK;
+    if (o->inner_prec == HDG_FP64) {
+      GmresResult g = gmres(p, *o, HDG_FP64, HDG_FP64, HDG_FP64, p->d_r, p->d_x, o->rtol, o->max_iters, 1, s);
+      inf.iters = g.iters;
+      inf.restarts = g.restarts;
+      inf.converged = g.converged ? 1 : 0;
+      inf.rel_resid = g.rel;
+      st = g.st != HDG_OK ? g.st : (g.converged ? HDG_OK : HDG_ERR_NOT_CONVERGED);
+    } else {
+      // FP64 iterative refinement around a low-precision inner GMRES
+      const int64_t len = p->ndof * p->R;
+      const int kp = o->inner_prec, pp = (o->poly_prec == HDG_BF16) ? HDG_BF16 : kp;
+      Ops ops{p, s, p->R};
+      GmresView k = make_view(p, p->R, o->restart, o->rtol, o->max_iters);
+      CK(cudaMemsetAsync(p->d_x, 0, sizeof(double) * len, s));
+      CK(cudaMemcpyAsync(p->bo, p->d_r, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+      double* bnorm0 = p->pw;   // keep ||b|| of the original system
+      launch_norms(k, p->d_r, bnorm0, 0, nullptr, s);
+      int total = 0, outer = 0;
+      double rel = 1.0;
+      bool conv = false;
+      const int max_outer = o->max_outer > 0 ? o->max_outer : 20;
+      while (outer < max_outer) {
+        launch_norms(k, p->bo, p->rel, 0, bnorm0, s);
+        CK(cudaMemcpyAsync(p->h_dbl, p->rel, sizeof(double) * p->R, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rel = 0.0;
+        for (int r = 0; r < p->R; ++r) rel = std::max(rel, p->h_dbl[r]);
+        if (rel <= o->rtol) {
+          conv = true;
+          break;
+        }
+        if (total >= o->max_iters) break;
+        const double itol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-4;
+        GmresResult g = gmres(p, *o, kp, kp, pp, p->bo, p->xo, itol, o->max_iters - total, 0, s);
+        total += g.iters;
+        if (g.st != HDG_OK) {
+          st = g.st;
+          break;
+        }
+        launch_axpby(p->d_x, p->xo, 1.0, 1.0, len, nullptr, p->R, s);          // x += d
+        ops.K(HDG_FP64, p->d_x, p->bo, EPI_RESID, p->d_r, nullptr, nullptr);  // r = b - K x (FP64)
+        ++outer;
+      }
+      inf.iters = total;
+      inf.outer = outer;
+      inf.converged = conv ? 1 : 0;
+      inf.rel_resid = rel;
+      if (st == HDG_OK) st = conv ? HDG_OK : HDG_ERR_NOT_CONVERGED;
+    }
+    // matvec timing
+    if (p->timing && p->ev_used > 0) {
+      CK(cudaStreamSynchronize(s));
+      for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
+        p->t_mv_ms += ms;
+        p->n_mv += 1;
+      }
+      p->ev_used = 0;
+    }
+    if (info) *info = inf;
+    return st;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* stream) {
+  if (!p || !uhat) return HDG_ERR_ARG;
+  if (!p->d_x) return HDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    const int64_t n = p->NF * p->b * p->R;
+    double* full = on_device ? uhat : (double*)p->dalloc(sizeof(double) * n);
+    expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
+    if (!on_device) {
+      CK(cudaMemcpyAsync(uhat, full, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      p->dfree(full, sizeof(double) * n);
+    }
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void* stream) {
+  if (!p || !u || !q) return HDG_ERR_ARG;
+  if (!p->d_x) return HDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    const int64_t nu = p->NE * p->MPE * p->R, nq = p->NE * p->MDPE * p->R, nt = p->NF * p->b * p->R;
+    double* full = (double*)p->dalloc(sizeof(double) * nt);
+    double* du = on_device ? u : (double*)p->dalloc(sizeof(double) * nu);
+    double* dq = on_device ? q : (double*)p->dalloc(sizeof(double) * nq);
+    expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
+    RecoverDesc d{};
+    d.XF = p->d_XF;
+    d.Xr = p->d_Xr;
+    d.MinvB = p->d_MinvB;
+    d.MinvC = p->d_MinvC;
+    d.uhat_full = full;
+    d.elem_face = p->d_elem_face;
+    d.M = p->M;
+    d.D = p->D;
+    d.PE = p->PE;
+    d.PF = p->PF;
+    d.nl = p->nl;
+    d.R = p->R;
+    d.n_elem = p->NE;
+    d.u = du;
+    d.q = dq;
+    recover(d, s);
+    CK(cudaGetLastError());
+    if (!on_device) {
+      CK(cudaMemcpyAsync(u, du, sizeof(double) * nu, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(q, dq, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    p->dfree(full, sizeof(double) * nt);
+    if (!on_device) {
+      p->dfree(du, sizeof(double) * nu);
+      p->dfree(dq, sizeof(double) * nq);
+    }
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_apply_K(hdg_problem p, int prec, const double* x, double* y, void* stream) {
+  if (!p || !x || !y || prec < 0 || prec > 2) return HDG_ERR_ARG;
+  if (!p->assembled) return HDG_ERR_STATE;
+  if (prec == HDG_BF16 && !p->K16) return HDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    Ops ops{p, s, p->R};
+    ops.K(prec, x, y, EPI_STORE, nullptr, nullptr, nullptr);
+    CK(cudaGetLastError());
+    if (p->timing && p->ev_used > 0) {
+      CK(cudaStreamSynchronize(s));
+      for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
+        p->t_mv_ms += ms;
+        p->n_mv += 1;
+      }
+      p->ev_used = 0;
+    }
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
+}
+
+hdg_status hdg_apply_precond(hdg_problem p, const hdg_solver_opts* o, int prec, const double* x, double* y,
+                             void* stream) {
+  if (!p || !o || !x || !y || prec < 0 || prec > 2) return HDG_ERR_ARG;
+  if (!p->assembled || p->pc_ready != o->pc) return HDG_ERR_STATE;
+  if (o->poly != HDG_POLY_NONE && (p->poly_n == 0 || p->poly_kind != o->poly)) return HDG_ERR_STATE;
+  if (prec == HDG_BF16 && ((o->pc == HDG_PC_BJ && !p->bj16) || (o->pc == HDG_PC_ASM && !p->as16) || !p->K16))
+    return HDG_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    ensure_workspace(p, std::max(o->restart, 1));
+    Ops ops{p, s, p->R};
+    const int pp = (o->poly_prec == HDG_BF16) ? HDG_BF16 : prec;
+    ops.Pinv(*o, prec, pp, x, y, nullptr);
+    CK(cudaGetLastError());
+    return check_err(p, s);
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_get_condensed(hdg_problem p, int64_t e0, int64_t count, double* Kbar, double* rbar) {
+  if (!p || e0 < 0 || count < 0 || e0 + count > p->NE) return HDG_ERR_ARG;
+  try {
+    DeviceGuard dg(p->device);
+    CK(cudaDeviceSynchronize());
+    if (Kbar)
+      CK(cudaMemcpy(Kbar, p->d_Kbar + e0 * p->nlb * p->nlb, sizeof(double) * count * p->nlb * p->nlb,
+                    cudaMemcpyDeviceToHost));
+    if (rbar)
+      CK(cudaMemcpy(rbar, p->d_rbar + e0 * p->nlb * p->R, sizeof(double) * count * p->nlb * p->R,
+                    cudaMemcpyDeviceToHost));
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
+}
+
+hdg_status hdg_get_face_rows(hdg_problem p, int64_t f0, int64_t count, double* blocks, int32_t* nbr, double* r) {
+  if (!p || f0 < 0 || count < 0 || f0 + count > p->nfree) return HDG_ERR_ARG;
+  if (!p->assembled) return HDG_ERR_STATE;
+  try {
+    DeviceGuard dg(p->device);
+    CK(cudaDeviceSynchronize());
+    const int b = p->b, ms = p->ms;
+    if (blocks) {
+      std::vector<double> tmp((size_t)count * ms * p->s64);
+      CK(cudaMemcpy(tmp.data(), p->K64 + f0 * ms * p->s64, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost));
+      for (int64_t f = 0; f < count; ++f)
+        for (int s = 0; s < ms; ++s)
+          for (int i = 0; i < b; ++i)
+            for (int j = 0; j < b; ++j)
+              blocks[((f * ms + s) * b + i) * b + j] = tmp[(f * ms + s) * p->s64 + (int64_t)j * b + i];
+    }
+    if (nbr) std::memcpy(nbr, p->h_nbr.data() + f0 * ms, sizeof(int32_t) * count * ms);
+    if (r) CK(cudaMemcpy(r, p->d_r, sizeof(double) * p->ndof * p->R, cudaMemcpyDeviceToHost));
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
+}
+
+hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n) {
+  if (!p || !n) return HDG_ERR_ARG;
+  if (p->poly_kind == HDG_POLY_CHEBYSHEV) {
+    if (re && cap >= 2) {
+      re[0] = p->cheb_a;
+      re[1] = p->cheb_b;
+    }
+    *n = 2;
+    return HDG_OK;
+  }
+  *n = p->poly_n;
+  for (int i = 0; i < p->poly_n && i < cap; ++i) {
+    if (re) re[i] = p->th_re[i];
+    if (im) im[i] = p->th_im[i];
+  }
+  return HDG_OK;
+}
+
+hdg_status hdg_set_timing(hdg_problem p, int enable) {
+  if (!p) return HDG_ERR_ARG;
+  p->timing = enable != 0;
+  p->t_mv_ms = 0.0;
+  p->n_mv = 0;
+  p->ev_used = 0;
+  return HDG_OK;
+}
+
+hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches) {
+  if (!p || kind != 0) return HDG_ERR_ARG;
+  if (total_ms) *total_ms = p->t_mv_ms;
+  if (launches) *launches = p->n_mv;
+  return HDG_OK;
+}
+
+}  // extern "C"

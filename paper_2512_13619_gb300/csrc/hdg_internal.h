@@ -1,0 +1,111 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/hdg.h"
+
+namespace hdg {
+
+// --------------------------------------------------------------- batched GEMM
+// C[b] = beta*C[b] + alpha*A[b]*B[b] for a two-level batch (b0 < nb0, b1 < nb1),
+// row-major FP64.  The output column c is stored at (c / cg)*cgs + (c % cg),
+// which lets one product write a strided set of column groups.
+struct GemmDesc {
+  int M, N, K;
+  const double* A; int64_t lda, sA0, sA1;
+  const double* B; int64_t ldb, sB0, sB1;
+  double* C; int64_t ldc, sC0, sC1;
+  int cg; int64_t cgs;
+  double alpha, beta;
+  int nb0, nb1;
+};
+void gemm_f64(const GemmDesc& d, cudaStream_t s);
+
+// Batched in-place inverse (Gauss-Jordan, partial pivoting) of `count`
+// n x n FP64 matrices with batch stride `stride`.  Sets ERRBIT_SINGULAR in
+// *err on a zero pivot.  Returns false if n is too large for one CTA.
+bool inverse_f64(double* A, int n, int64_t stride, int64_t count, unsigned* err, cudaStream_t s);
+int inverse_max_n();
+
+// --------------------------------------------------------------- block rows
+// out[u][row][r] = epilogue( sum_{s < cnt[u]} sum_{c < bc}
+//                   blk[u][s](row, c) * in[(nbr[u][s]*bc + c)*R + r] )
+// blk[u][s] is a column-major b_rows x bc block at blk + (u*max_slots + s)*
+// blk_stride elements.  Slots of a unit are packed first (cnt[u] of them).
+enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_SCALE = 2 };
+struct BlockRowDesc {
+  int prec;               // HDG_FP64 / HDG_FP32 / HDG_BF16 storage of blk
+  const void* blk;
+  int64_t blk_stride;     // elements per slot block (padded to 16 bytes)
+  const int32_t* nbr;     // n_units * max_slots
+  const int32_t* cnt;     // n_units
+  int64_t n_units;
+  int b_rows, bc, max_slots, R;
+  const double* in;
+  double* out;
+  int epi;
+  const double* rhs;      // EPI_RESID: out = rhs - acc
+  const double* scale;    // EPI_SCALE: out = scale[r] * acc (per RHS)
+  const int* active;      // optional: skip the launch work when all R entries are 0
+  unsigned* err;
+};
+void blockrow(const BlockRowDesc& d, int variant, cudaStream_t s);
+int blockrow_variants();
+
+// --------------------------------------------------------------- assembly etc.
+struct AssembleDesc {
+  const double* Kbar; const double* rbar; const double* uhatD;
+  int nlb;                       // n_lfe*b: side of Kbar
+  int b, nl, R, max_slots;
+  int64_t n_free;
+  const int32_t* slot_e;         // n_free*max_slots element of the block (-1 pad)
+  const int32_t* slot_lr;        // row local face
+  const int32_t* slot_lc;        // column local face
+  const int32_t* diag2;          // n_free*2: (e2, l2) second element of the diagonal (-1)
+  const int32_t* rhs_src;        // n_free*4: (e1,l1,e2,l2)
+  const int32_t* elem_face;      // n_elem*nl
+  const uint8_t* face_dir;       // n_face
+  double* K64; int64_t s64;
+  float* K32; int64_t s32;
+  __nv_bfloat16* K16; int64_t s16;
+  double* r;
+};
+void assemble(const AssembleDesc& d, cudaStream_t s);
+
+// copy diagonal blocks (slot 0, column-major) into dense row-major blocks
+void extract_diag(const double* K64, int64_t s64, int max_slots, int b, int64_t n_free, double* out,
+                  cudaStream_t s);
+// dense row-major FP64 n x n blocks -> column-major padded blocks in the three precisions
+void pack_blocks(const double* in, int n, int64_t count, double* o64, int64_t s64, float* o32, int64_t s32,
+                 __nv_bfloat16* o16, int64_t s16, cudaStream_t s);
+// ASM element matrices from Kbar: rows/cols restricted to free faces in local order
+// (compacted), diagonal blocks of interior faces replaced by K_ff, padding = identity.
+void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const int32_t* asm_lf,
+               const int32_t* asm_cnt, const int32_t* asm_face_free, const double* K64, int64_t s64,
+               int max_slots, double* P, cudaStream_t s);
+// ASM panels: column-major (nl*b) x b panels for the free local faces of each element
+void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, double* o64, int64_t s64, float* o32,
+              int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s);
+// z_f = z^{e1}[slot s1] + z^{e2}[slot s2] (face-parallel, no atomics)
+void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum, double* z,
+                  cudaStream_t s);
+
+// --------------------------------------------------------------- recovery
+struct RecoverDesc {
+  const double* XF; const double* Xr; const double* MinvB; const double* MinvC;
+  const double* uhat_full;   // n_face*b*R
+  const int32_t* elem_face;
+  int M, D, PE, PF, nl, R;
+  int64_t n_elem;
+  double* u; double* q;
+  double* uhe;               // scratch n_elem * nl*b * R
+};
+void recover(const RecoverDesc& d, cudaStream_t s);
+// free-vector -> full trace (Dirichlet faces from uhatD)
+void expand_trace(const double* x, const double* uhatD, const int32_t* free_of_face, int64_t n_face, int b, int R,
+                  double* full, cudaStream_t s);
+
+}  // namespace hdg

@@ -1,0 +1,202 @@
+// Dense FP64 building blocks of the batched static condensation (Sec. 4.1,
+// Eqs. w16-w22) and of the block-Jacobi / ASM factorizations (Sec. 4.5, 4.6):
+// a batched GEMM and a batched Gauss-Jordan inverse with partial pivoting.
+//
+// FP64 on this GPU runs on the CUDA-core FP64 pipes (about 1.2 TFLOP/s
+// measured), so both kernels are ALU-bound; they keep operands in shared
+// memory and each thread owns a 4x4 register tile.
+#include "hdg_common.cuh"
+#include "hdg_internal.h"
+
+namespace hdg {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int b0 = blockIdx.z / d.nb1, b1 = blockIdx.z % d.nb1;
+  const double* A = d.A + b0 * d.sA0 + b1 * d.sA1;
+  const double* B = d.B + b0 * d.sB0 + b1 * d.sB1;
+  double* C = d.C + b0 * d.sC0 + b1 * d.sC1;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < d.K; k0 += BK) {
+    // A tile: BM x BK, B tile: BK x BN (256 threads, 4 loads each)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      int idx = threadIdx.x + t * 256;
+      int r = idx / BK, c = idx % BK;
+      int gr = row0 + r, gc = k0 + c;
+      As[c][r] = (gr < d.M && gc < d.K) ? A[(int64_t)gr * d.lda + gc] : 0.0;
+      int br = idx / BN, bcol = idx % BN;
+      int gbr = k0 + br, gbc = col0 + bcol;
+      Bs[br][bcol] = (gbr < d.K && gbc < d.N) ? B[(int64_t)gbr * d.ldb + gbc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gr = row0 + ty + 16 * i;
+    if (gr >= d.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gc = col0 + tx + 16 * j;
+      if (gc >= d.N) continue;
+      int64_t cc = (int64_t)(gc / d.cg) * d.cgs + (gc % d.cg);
+      double* p = C + (int64_t)gr * d.ldc + cc;
+      *p = (d.beta == 0.0 ? 0.0 : d.beta * *p) + d.alpha * acc[i][j];
+    }
+  }
+}
+
+// ----------------------------------------------------------------- inverse
+constexpr int kInvThreads = 256;
+constexpr size_t kInvSmemMax = 227 * 1024;
+
+__global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int n, int64_t stride, unsigned* err) {
+  extern __shared__ double sm[];
+  double* a = sm;                 // n x n row-major
+  double* col = sm + n * n;       // n multipliers
+  int* piv = reinterpret_cast<int*>(col + n);
+  __shared__ int s_p;
+  __shared__ double s_pv;
+  double* A = Aall + blockIdx.x * stride;
+  const int nn = n * n;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) a[i] = A[i];
+  __syncthreads();
+  bool singular = false;
+  for (int k = 0; k < n; ++k) {
+    // pivot search (warp 0): largest |a[i][k]|, i >= k, lowest index on ties
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = n;
+      for (int i = k + threadIdx.x; i < n; i += 32) {
+        double v = fabs(a[i * n + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (threadIdx.x == 0) { s_p = bi; }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != k) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = a[k * n + j];
+        a[k * n + j] = a[p * n + j];
+        a[p * n + j] = t;
+      }
+    }
+    if (threadIdx.x == 0) piv[k] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) s_pv = a[k * n + k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = a[i * n + k];
+    __syncthreads();
+    const double pv = s_pv;
+    if (pv == 0.0 || !isfinite(pv)) { singular = true; break; }
+    const double inv = 1.0 / pv;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * inv;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      int i = idx / n, j = idx - i * n;
+      if (i == k) continue;
+      double v = (j == k) ? 0.0 : a[idx];
+      a[idx] = fma(-col[i], a[k * n + j], v);
+    }
+    __syncthreads();
+  }
+  if (singular) {
+    if (threadIdx.x == 0) atomicOr(err, ERRBIT_SINGULAR);
+    return;
+  }
+  // undo the row interchanges as column interchanges, in reverse order
+  for (int k = n - 1; k >= 0; --k) {
+    int p = piv[k];
+    if (p != k) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double t = a[i * n + k];
+        a[i * n + k] = a[i * n + p];
+        a[i * n + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) A[i] = a[i];
+}
+
+size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)n * 4 + 16; }
+
+}  // namespace
+
+void gemm_f64(const GemmDesc& d, cudaStream_t s) {
+  if (d.M <= 0 || d.N <= 0 || d.nb0 <= 0 || d.nb1 <= 0) return;
+  int64_t nb = (int64_t)d.nb0 * d.nb1;
+  // grid.z is limited to 65535: split the outer batch if needed
+  const int64_t zmax = 65535;
+  if (nb <= zmax) {
+    dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, (unsigned)nb);
+    gemm_f64_kernel<<<grid, 256, 0, s>>>(d);
+    return;
+  }
+  int per = (int)(zmax / d.nb1);
+  for (int b0 = 0; b0 < d.nb0; b0 += per) {
+    GemmDesc e = d;
+    e.nb0 = (d.nb0 - b0 < per) ? d.nb0 - b0 : per;
+    e.A = d.A + b0 * d.sA0;
+    e.B = d.B + b0 * d.sB0;
+    e.C = d.C + b0 * d.sC0;
+    dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, (unsigned)((int64_t)e.nb0 * d.nb1));
+    gemm_f64_kernel<<<grid, 256, 0, s>>>(e);
+  }
+}
+
+int inverse_max_n() {
+  int n = 1;
+  while (inverse_smem(n + 1) <= kInvSmemMax - 1024) ++n;
+  return n;
+}
+
+bool inverse_f64(double* A, int n, int64_t stride, int64_t count, unsigned* err, cudaStream_t s) {
+  if (n <= 0 || count <= 0) return true;
+  size_t smem = inverse_smem(n);
+  if (smem > kInvSmemMax - 1024) return false;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kInvSmemMax - 1024));
+    attr_set = true;
+  }
+  const int64_t gmax = 2147483647;
+  for (int64_t c0 = 0; c0 < count; c0 += gmax) {
+    int64_t c = count - c0 < gmax ? count - c0 : gmax;
+    inverse_kernel<<<(unsigned)c, kInvThreads, smem, s>>>(A + c0 * stride, n, stride, err);
+  }
+  return true;
+}
+
+}  // namespace hdg

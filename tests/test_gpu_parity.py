@@ -1,0 +1,254 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on seeded inputs (Welter & Nguyen, Sec. 4.1-4.7)."""
+import numpy as np
+import pytest
+
+from hdg_inputs import workloads as W
+from oracle import krylov, precond
+from oracle.condense import condense_local
+from tests.gpu_helpers import need_gpu, rel, sparse_mv
+from tests.oracle_helpers import OracleSystem
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+U16 = 2.0 ** -8
+
+SMALL = {
+    'tri_k2': lambda: W.tri_poisson(n=3, k=2),
+    'hex_k2': lambda: W.hex_poisson(n=3, k=2),
+    'elast_R2': lambda: W.hex_elasticity(n=2, k=1, R=2),
+    'cdr_M5_R4': lambda: W.hex_cdr(n=2, k=1, R=4),
+    'elast_pert_k2_R8': lambda: W.hex_elasticity(n=2, k=2, R=8),
+}
+
+
+def _problem(w, o=None, chunks=1):
+    from paper_2512_13619_gb300 import driver
+    o = o or driver.opts()
+    p = driver.Problem.from_workload(w)
+    bounds = np.linspace(0, w.n_elem, chunks + 1).astype(int)
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        p.condense(w.blocks(a, b), a)
+    p.set_dirichlet(w.uhat_dirichlet())
+    return p
+
+
+@pytest.mark.parametrize('name', sorted(SMALL))
+def test_condensation_matches_oracle(name):
+    """Kbar^e and rbar^e (Eq. w22) per element, FP64, to 1e-12."""
+    need_gpu()
+    w = SMALL[name]()
+    p = _problem(w, chunks=2)
+    Kg, rg = p.condensed()
+    Ko, ro, _ = condense_local(w.blocks(), w.M, w.n_lfe)
+    assert rel(Kg, Ko) < 1e-12
+    assert rel(rg, ro) < 1e-12
+    p.close()
+
+
+@pytest.mark.parametrize('name', sorted(SMALL))
+def test_assembly_matches_oracle(name):
+    """Face rows of K (Sec. 4.2) equal the blocks of the oracle's
+    K = sum_e R_e^T Kbar^e R_e; padding slots are zero; r equals."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = SMALL[name]()
+    s = OracleSystem(w)
+    p = _problem(w)
+    p.assemble(driver.opts())
+    blocks, nbr, r = p.face_rows()
+    b = s.bsz
+    K = s.K.toarray()
+    seen = np.zeros_like(K, dtype=bool)
+    scale = np.abs(K).max()
+    for f in range(p.n_free):
+        for sl in range(nbr.shape[1]):
+            g = nbr[f, sl]
+            if g < 0:
+                assert np.all(blocks[f, sl] == 0.0)
+                continue
+            ref = K[f * b:(f + 1) * b, g * b:(g + 1) * b]
+            assert np.abs(blocks[f, sl] - ref).max() <= 1e-12 * scale
+            seen[f * b:(f + 1) * b, g * b:(g + 1) * b] = True
+    assert np.all(K[~seen] == 0.0)          # every nonzero block is in some slot
+    assert rel(r, s.r) < 1e-12
+    p.close()
+
+
+@pytest.mark.parametrize('name', sorted(SMALL))
+def test_matvec_fp64_fp32_bf16(name):
+    """y = K x (Sec. 4.3).  FP64: normwise 1e-13.  FP32/BF16 storage with FP32
+    accumulation: |y - Kx| <= (u_store + (n+1) u_32) |K||x| elementwise,
+    n = terms per row (the rounding bound of a dot product)."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = SMALL[name]()
+    s = OracleSystem(w)
+    p = _problem(w)
+    p.assemble(driver.opts(poly_prec='bf16'))
+    x = np.random.default_rng(7).standard_normal((p.n_dof, w.R))
+    y_ref = sparse_mv(s.K, x)
+    bound = sparse_mv(abs(s.K), np.abs(x))
+    nterm = (2 * w.n_lfe - 1) * s.bsz
+    y64 = p.apply_K(x, 'fp64')
+    assert np.abs(y64 - y_ref).max() <= 1e-13 * np.abs(bound).max()
+    y32 = p.apply_K(x, 'fp32')
+    assert np.all(np.abs(y32 - y_ref) <= (U32 + (nterm + 1) * U32) * bound + 1e-300)
+    y16 = p.apply_K(x, 'bf16')
+    assert np.all(np.abs(y16 - y_ref) <= (U16 + (nterm + 1) * U32) * bound + 1e-300)
+    p.close()
+
+
+@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'elast_pert_k2_R8'])
+@pytest.mark.parametrize('pc', ['bj', 'asm'])
+def test_bj_asm_apply(name, pc):
+    """Block-Jacobi (Sec. 4.5) and ASM (Sec. 4.6) applies in FP64 against the
+    oracle's inverses of K_ff and of R_e K R_e^T."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = SMALL[name]()
+    s = OracleSystem(w)
+    o = driver.opts(pc=pc)
+    p = _problem(w)
+    p.assemble(o)
+    p.setup_precond(o)
+    x = np.random.default_rng(8).standard_normal((p.n_dof, w.R))
+    if pc == 'bj':
+        Binv = precond.bj_setup(s.K, s.bsz)
+        z_ref = np.column_stack([precond.bj_apply(Binv, x[:, r]) for r in range(w.R)])
+    else:
+        subs = precond.asm_setup(s.K, s.elem_dofs)
+        z_ref = np.column_stack([precond.asm_apply(subs, x[:, r]) for r in range(w.R)])
+    z = p.apply_precond(o, x, 'fp64')
+    assert rel(z, z_ref) < 1e-10
+    z32 = p.apply_precond(o, x, 'fp32')
+    assert rel(z32, z_ref) < 1e-3
+    p.close()
+
+
+def test_gmres_bj_tri_poisson_to_1e10():
+    """Unit square, 128 P^2 triangles (528 unknowns), BJ-GMRES(30) to 1e-10:
+    the true relative residual of the GPU solution is <= 1e-10 and it equals
+    the sparse direct solution within cond(K) * 1e-10; the iteration count is
+    within 2 of the oracle's GMRES with the same rule."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.tri_poisson(8, 2)
+    s = OracleSystem(w)
+    o = driver.opts(restart=30, rtol=1e-10, pc='bj')
+    p = _problem(w)
+    p.assemble(o)
+    p.setup_precond(o)
+    st, info = p.solve(o)
+    assert st == 0 and info.converged == 1
+    x = p.free_trace()
+    b = s.r[:, 0]
+    assert np.linalg.norm(b - s.K @ x[:, 0]) / np.linalg.norm(b) <= 1e-10
+    xd = s.direct()
+    cond = np.linalg.cond(s.K.toarray())
+    assert np.linalg.norm(x[:, 0] - xd) / np.linalg.norm(xd) <= cond * 1e-10
+    Binv = precond.bj_setup(s.K, s.bsz)
+    _, oi = krylov.gmres(lambda v: s.K @ v, lambda v: precond.bj_apply(Binv, v), b, m=30, rtol=1e-10)
+    assert abs(info.iters - oi['iters']) <= 2
+    # recovery (Eq. w19, w16) against the oracle's recovery of its own solution
+    u, q = p.recover()
+    uo, qo = s.recover(xd)
+    assert rel(u, uo) < cond * 1e-9
+    assert rel(q, qo) < cond * 1e-9
+    p.close()
+
+
+@pytest.mark.parametrize('orth', ['mgs', 'cgs2'])
+@pytest.mark.parametrize('pc', ['asm', 'none'])
+def test_gmres_variants_multi_rhs(orth, pc):
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.hex_elasticity(n=2, k=1, R=4)
+    s = OracleSystem(w)
+    o = driver.opts(restart=20, rtol=1e-9, pc=pc, orth=orth, max_iters=2000)
+    p = _problem(w)
+    p.assemble(o)
+    p.setup_precond(o)
+    st, info = p.solve(o)
+    assert st == 0, info.rel_resid
+    x = p.free_trace()
+    for r in range(w.R):
+        b = s.r[:, r]
+        assert np.linalg.norm(b - s.K @ x[:, r]) / np.linalg.norm(b) <= 1e-9
+    p.close()
+
+
+def test_polynomial_setup_and_apply():
+    """Harmonic Ritz values of Arnoldi(P) on M^{-1} K from the same seeded v0
+    agree with the oracle's, and the GPU's polynomial apply agrees with the
+    oracle's apply of its own values (p does not depend on the order)."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.hex_elasticity(n=2, k=1, R=2)
+    s = OracleSystem(w)
+    o = driver.opts(pc='bj', poly='gmres', degree=6)
+    p = _problem(w)
+    p.assemble(o)
+    v0 = w.random_vector(31)
+    p.setup_precond(o, v0)
+    th = p.poly()
+    Binv = precond.bj_setup(s.K, s.bsz)
+    M = lambda v: precond.bj_apply(Binv, v)
+    A = lambda v: M(s.K @ v)
+    tho = precond.pp_setup(A, v0, 6)
+    key = lambda t: (round(t.real, 6), round(t.imag, 6))
+    assert np.allclose(sorted(th, key=key), sorted(tho, key=key), rtol=1e-8, atol=1e-10)
+    x = np.random.default_rng(9).standard_normal((p.n_dof, w.R))
+    z = p.apply_precond(o, x, 'fp64')
+    zo = np.column_stack([precond.pp_apply(A, tho, M(x[:, r])) for r in range(w.R)])
+    assert rel(z, zo) < 1e-7
+    p.close()
+
+
+def test_chebyshev_setup_and_apply():
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.hex_elasticity(n=2, k=1, R=2)
+    s = OracleSystem(w)
+    o = driver.opts(pc='asm', poly='chebyshev', degree=4)
+    p = _problem(w)
+    p.assemble(o)
+    v0 = w.random_vector(31)
+    p.setup_precond(o, v0)
+    ab = p.poly().real
+    subs = precond.asm_setup(s.K, s.elem_dofs)
+    M = lambda v: precond.asm_apply(subs, v)
+    A = lambda v: M(s.K @ v)
+    a, b = precond.chebyshev_bounds(A, v0, 10)
+    assert abs(ab[0] - a) < 1e-8 * abs(b) and abs(ab[1] - b) < 1e-8 * abs(b)
+    x = np.random.default_rng(10).standard_normal((p.n_dof, w.R))
+    z = p.apply_precond(o, x, 'fp64')
+    zo = np.column_stack([precond.chebyshev_apply(A, a, b, 4, M(x[:, r])) for r in range(w.R)])
+    assert rel(z, zo) < 1e-8
+    p.close()
+
+
+@pytest.mark.parametrize('pc,poly,deg', [('asm', 'chebyshev', 4), ('bj', 'gmres', 6), ('bj', None, 0)])
+def test_mixed_precision_reaches_1e8(pc, poly, deg):
+    """FP32 blocks + FP64 refinement reach a true FP64 relative residual of
+    1e-8; the error against the oracle's direct solution is <= cond * 1e-8."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.hex_elasticity(n=3, k=1, R=8)
+    s = OracleSystem(w)
+    o = driver.opts(restart=30, rtol=1e-8, pc=pc, poly=poly, degree=deg, inner='fp32', inner_rtol=1e-4,
+                    max_iters=3000)
+    p = _problem(w)
+    p.assemble(o)
+    p.setup_precond(o, w.random_vector(31) if poly else None)
+    st, info = p.solve(o)
+    assert st == 0 and info.outer >= 1
+    x = p.free_trace()
+    xd = np.column_stack([s.direct()[:, r] for r in range(w.R)]) if s.direct().ndim == 2 else s.direct()[:, None]
+    cond = np.linalg.cond(s.K.toarray())
+    for r in range(w.R):
+        b = s.r[:, r]
+        assert np.linalg.norm(b - s.K @ x[:, r]) / np.linalg.norm(b) <= 1e-8
+        assert np.linalg.norm(x[:, r] - xd[:, r]) / np.linalg.norm(xd[:, r]) <= cond * 1e-8
+    p.close()
