@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the HDG trace-solver hot path (one GB300 per rank).
+
+Workload (default): HDG Poisson on the unit cube, 16^3 hexahedra, Q3 tensor
+basis (16 trace dofs per face, 96 x 96 condensed element blocks), manufactured
+sin-product solution, 184,320 trace unknowns, one right-hand side,
+block-Jacobi GMRES(50).
+
+One step = one pass of the whole hot path over the element blocks already
+resident in HBM: batched static condensation -> face-based assembly ->
+block-Jacobi factorization -> GMRES to a true FP64 relative residual of 1e-8
+(FP32 blocks + FP64 iterative refinement, the "mixed" path) -> element
+recovery.  The same step with the plain FP64 solve is timed beside it.
+
+Prints ONE JSON line (rank 0).  Several ranks run independent replicas (the
+path is not sharded in this build); timings are the max over ranks.
+`--impl reference` times the FP64 CPU oracle (test infrastructure) on the
+same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = 'time to 1e-8 rel. residual (mixed vs FP64); block-matvec GB/s; p99 latency'
+WORKLOAD = 'HDG Poisson, unit cube, 16^3 hex, Q3 (16 dofs/face, 96x96 element blocks), sin-product MMS, 1 RHS'
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--n', type=int, default=16)
+    ap.add_argument('--k', type=int, default=3)
+    ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--no-cpu', action='store_true')
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
+    except Exception:
+        return {'hbm_gbs': 6800.0, 'bf16_tflops': 1900.0, '_fallback': True}
+
+
+# FP64 ALU peak: 152 SMs x 2.07 GHz x 4 FP64 FLOP/clk/SM (nominal 1.25 TFLOP/s)
+FP64_ALU_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    FIELDS = 'index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,' \
+             'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,' \
+             'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap'
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.gpu), '--query-gpu=' + self.FIELDS,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(',')]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == 'active':
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {'sm_mhz': sm[len(sm) // 2], 'sm_max_mhz': max(mx), 'samples': len(sm), 'reasons': sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+def condense_flops(w):
+    """Algorithmic FP64 flops of the batched condensation per element
+    (Eqs. w16-w22 as implemented: inverses by Gauss-Jordan, 2n^3)."""
+    PE, D, M, PF, nl, R = w.PE, w.D, w.M, w.PF, w.n_lfe, w.R
+    MPE, nlPF, nlb = M * PE, nl * PF, nl * M * PF
+    f = 2 * PE ** 3 + D * 2 * PE ** 3 + D * 2 * PE ** 2 * nlPF
+    f += 2 * MPE * MPE * D * PE + 2 * MPE * nlb * D * PE + 2 * nlb * MPE * D * PE + 2 * nlb * nlb * D * PE
+    f += 2 * MPE ** 3 + 2 * MPE ** 2 * (nlb + R) + 2 * nlb * MPE * (nlb + R)
+    return f
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=dev)
+
+    w = W.hex_poisson(n=args.n, k=args.k)
+    blk = w.blocks()
+    names = driver.BLOCK_NAMES
+    host = {k: torch.from_numpy(np.ascontiguousarray(blk[k])).pin_memory() for k in names}
+    dblk = {k: host[k].to(dev) for k in names}
+    uD_host = torch.from_numpy(w.uhat_dirichlet()).pin_memory()
+    uD_dev = uD_host.to(dev)
+    in_bytes = sum(v.numel() * 8 for v in host.values()) + uD_host.numel() * 8
+    R = w.R
+    o_mixed = driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp32', inner_rtol=1e-4, max_iters=5000)
+    o_fp64 = driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp64', max_iters=5000)
+    p = driver.Problem.from_workload(w, local)
+    u_dev = torch.empty((w.n_elem, w.M * w.PE, R), dtype=torch.float64, device=dev)
+    q_dev = torch.empty((w.n_elem, w.M * w.D * w.PE, R), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    infos = {}
+
+    def step(o, tag, phases=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if phases is not None else None
+        if ev: ev[0].record()
+        driver.check(L.hdg_condense(p.h, 0, w.n_elem, *[dblk[k] for k in names], 1, st), 'condense')
+        driver.check(L.hdg_set_dirichlet(p.h, uD_dev, 1, st), 'dirichlet')
+        driver.check(L.hdg_assemble(p.h, o, st), 'assemble')
+        driver.check(L.hdg_setup_precond(p.h, o, None, st), 'setup')
+        if ev: ev[1].record()
+        info = L.hdg_solve_info()
+        s = L.hdg_solve(p.h, o, st, info)
+        if s != 0:
+            raise RuntimeError('%s solve: %s rel=%g' % (tag, L.hdg_status_str(s), info.rel_resid))
+        if ev: ev[2].record()
+        driver.check(L.hdg_recover(p.h, u_dev, q_dev, 1, st), 'recover')
+        if ev:
+            ev[3].record()
+            phases.append(ev)
+        infos[tag] = (info.iters, info.outer, info.rel_resid)
+
+    def timed(o, tag, K, timing=False):
+        for _ in range(args.warmup):
+            step(o, tag)
+        torch.cuda.synchronize(dev)
+        if dist: dist.barrier()
+        torch.cuda.synchronize(dev)
+        L.hdg_set_timing(p.h, 1 if timing else 0)
+        phases = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = L.hdg_launch_count()
+        e0.record()
+        for _ in range(K):
+            step(o, tag, phases)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        n1 = L.hdg_launch_count()
+        ms = e0.elapsed_time(e1) / K
+        ph = {'setup': 0.0, 'solve': 0.0, 'recover': 0.0}
+        for ev in phases:
+            ph['setup'] += ev[0].elapsed_time(ev[1]) / K
+            ph['solve'] += ev[1].elapsed_time(ev[2]) / K
+            ph['recover'] += ev[2].elapsed_time(ev[3]) / K
+        tm = [L.hdg_get_timing(p.h, kind) for kind in range(3)]
+        L.hdg_set_timing(p.h, 0)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, ph, (n1 - n0) / K, tm
+
+    clk = Clocks(local)
+    clk.start()
+    ms_mixed, ph_mixed, launches, tm_mixed = timed(o_mixed, 'mixed', args.steps, timing=True)
+    ms_fp64, ph_fp64, launches64, tm_fp64 = timed(o_fp64, 'fp64', args.steps, timing=True)
+    clocks = clk.stop()
+
+    # condensation alone (the dominant kernels: batched FP64 GEMMs + inverses)
+    torch.cuda.synchronize(dev)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record()
+    for _ in range(args.steps):
+        driver.check(L.hdg_condense(p.h, 0, w.n_elem, *[dblk[k] for k in names], 1, st), 'condense')
+    c1.record()
+    torch.cuda.synchronize(dev)
+    ms_cond = c0.elapsed_time(c1) / args.steps
+    cflops = condense_flops(w) * w.n_elem
+
+    # end to end through the C ABI from pinned host buffers (inputs in, trace + u + q out)
+    e2e = None
+    if not args.no_e2e:
+        uh_host = torch.empty((w.n_face, w.M * w.PF, R), dtype=torch.float64).pin_memory()
+        u_host = torch.empty((w.n_elem, w.M * w.PE, R), dtype=torch.float64).pin_memory()
+        q_host = torch.empty((w.n_elem, w.M * w.D * w.PE, R), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            driver.check(L.hdg_condense(p.h, 0, w.n_elem, *[host[k] for k in names], 0, st), 'condense')
+            driver.check(L.hdg_set_dirichlet(p.h, uD_host, 0, st), 'dirichlet')
+            driver.check(L.hdg_assemble(p.h, o_mixed, st), 'assemble')
+            driver.check(L.hdg_setup_precond(p.h, o_mixed, None, st), 'setup')
+            info = L.hdg_solve_info()
+            s = L.hdg_solve(p.h, o_mixed, st, info)
+            if s != 0:
+                raise RuntimeError('e2e solve: ' + L.hdg_status_str(s))
+            driver.check(L.hdg_get_trace(p.h, uh_host, 0, st), 'trace')
+            driver.check(L.hdg_recover(p.h, u_host, q_host, 0, st), 'recover')
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        if dist: dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        out_bytes = (uh_host.numel() + u_host.numel() + q_host.numel()) * 8
+        e2e = {'value': round(e_ms, 3), 'unit': 'ms', 'h2d_bytes_per_step': int(in_bytes),
+               'd2h_bytes_per_step': int(out_bytes)}
+
+    pk = peaks()
+    fd = w.face_dirichlet
+    nfree_e = (fd[w.mesh.elem_face] == 0).sum(axis=1)
+    nnzb = int((nfree_e ** 2).sum() - w.n_free)      # nonzero b x b blocks of K
+    b = w.M * w.PF
+    mv = {}
+    for prec, name, sz in ((0, 'fp64', 8), (1, 'fp32', 4)):
+        tot = tm_mixed[prec][1] + tm_fp64[prec][1]
+        n = tm_mixed[prec][2] + tm_fp64[prec][2]
+        if n:
+            avg = tot / n
+            by = nnzb * b * b * sz + p.n_dof * R * (8 + 8)
+            gbs = by / avg / 1e6
+            mv[name] = {'avg_ms': round(avg, 5), 'launches': int(n), 'bytes_per_launch': int(by),
+                        'gbs': round(gbs, 1), 'frac_hbm': round(gbs / pk['hbm_gbs'], 3),
+                        'tflops': round(2 * nnzb * b * b * R / avg / 1e9, 3)}
+    achieved = cflops / ms_cond / 1e9
+    roof = {'kernel': 'gemm_f64_kernel + inverse_kernel (batched static condensation, FP64)',
+            'bound': 'alu', 'achieved': round(achieved, 4), 'peak': round(FP64_ALU_PEAK_TFLOPS, 4),
+            'unit': 'TFLOP/s', 'frac': round(achieved / FP64_ALU_PEAK_TFLOPS, 3), 'traffic': None,
+            'flops_per_step': int(cflops), 'ms_per_step': round(ms_cond, 3),
+            'peak_source': 'FP64 ALU: 152 SMs x 2.07 GHz x 4 FLOP/clk (nominal 1.25 TFLOP/s)'}
+    out = {
+        'metric': METRIC, 'value': round(ms_mixed, 3), 'unit': 'ms', 'n_gpus': ws, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': round(ms_mixed, 3), 'higher_is_better': False, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64+f32', 'data': 'synthetic',
+        'config': {'workload': WORKLOAD, 'n_elem': w.n_elem, 'n_dof': p.n_dof, 'precond': 'block-Jacobi',
+                   'restart': 50, 'rtol': 1e-8, 'rhs': R, 'solve': 'FP32 blocks + FP64 iterative refinement',
+                   'l2': 'inputs larger than L2 (%.2f GB element blocks read per step)' % (in_bytes / 1e9),
+                   'parallelism': 'replicas' if ws > 1 else 'single GPU'},
+        'fp64_ms_per_step': round(ms_fp64, 3),
+        'speedup_mixed_vs_fp64': round(ms_fp64 / ms_mixed, 3),
+        'phases_ms': {'mixed': {k: round(v, 3) for k, v in ph_mixed.items()},
+                      'fp64': {k: round(v, 3) for k, v in ph_fp64.items()}, 'condense': round(ms_cond, 3)},
+        'iterations': {k: {'gmres': v[0], 'refinement': v[1], 'rel_resid': v[2]} for k, v in infos.items()},
+        'aggregate_solves_per_s': round(ws * 1000.0 / ms_mixed, 3),
+        'block_matvec': mv,
+        'roofline': roof,
+        'gpu_launches': int(round(launches)),
+        'clocks': clocks,
+    }
+    if e2e:
+        out['e2e'] = e2e
+    if rank == 0 and not args.no_cpu:
+        out['cpu_baseline'] = cpu_baseline(args, w, blk)
+    p.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def oracle_step(w, blk):
+    """One step of the workload with the FP64 oracle (condense, assemble,
+    block-Jacobi, GMRES(50) to 1e-8, recover).  Returns (ms, iterations)."""
+    from oracle.condense import condense_local
+    from oracle.assemble import assemble, element_traces, recover
+    from oracle import krylov, precond
+    t0 = time.perf_counter()
+    uD = w.uhat_dirichlet()
+    Kb, rb, rec = condense_local(blk, w.M, w.n_lfe)
+    K, r = assemble(Kb, rb, w.mesh.elem_face, w.face_dirichlet, uD, w.M, w.PF)
+    Binv = precond.bj_setup(K, w.M * w.PF)
+    x, info = krylov.gmres(lambda v: K @ v, lambda v: precond.bj_apply(Binv, v), r[:, 0], m=50, rtol=1e-8)
+    ue = element_traces(x[:, None], w.mesh.elem_face, w.face_dirichlet, uD, w.M, w.PF)
+    recover(rec, ue, w.M, w.n_lfe)
+    return (time.perf_counter() - t0) * 1e3, info['iters']
+
+
+def cpu_cores():
+    try:
+        import numpy  # noqa: F401
+        from threadpoolctl import threadpool_info
+        n = max([i.get('num_threads', 1) for i in threadpool_info()] + [1])
+        return n
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(args, w, blk):
+    ms, it = oracle_step(w, blk)
+    return {'value': round(ms, 1), 'unit': 'ms', 'cores': cpu_cores(), 'kind': 'oracle',
+            'sample': 'one full step of the same workload (condense all %d elements, assemble, BJ setup, '
+                      'BJ-GMRES(50) to 1e-8 in FP64: %d iterations, recover) on the host cores' % (w.n_elem, it)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    from hdg_inputs import workloads as W
+    w = W.hex_poisson(n=args.n, k=args.k)
+    blk = w.blocks()
+    for _ in range(args.warmup):
+        oracle_step(w, blk)
+    ts = []
+    for _ in range(args.steps):
+        ts.append(oracle_step(w, blk)[0])
+    ms = sum(ts) / len(ts)
+    cores = cpu_cores()
+    return {'impl': 'reference', 'metric': METRIC, 'value': round(ms, 1), 'unit': 'ms', 'n_gpus': ws,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': round(ms, 1), 'higher_is_better': False,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': WORKLOAD, 'n_elem': w.n_elem, 'n_dof': w.n_dof, 'precond': 'block-Jacobi',
+                       'restart': 50, 'rtol': 1e-8, 'rhs': w.R, 'solve': 'FP64 oracle (CPU)',
+                       'parallelism': 'rank 0 only'},
+            'cpu_baseline': {'value': round(ms, 1), 'unit': 'ms', 'cores': cores, 'kind': 'oracle',
+                             'sample': 'full steps of the workload with the FP64 CPU oracle'},
+            'e2e': {'value': round(ms, 1), 'unit': 'ms', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == 'reference':
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == '__main__':
+    main()

@@ -234,11 +234,22 @@ hdg_status hdg_get_face_rows(hdg_problem p, int64_t f0, int64_t count, double* b
  * re[0], re[1].  *n receives the count. */
 hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n);
 
-/* Mean device time (ms) of the block-matvec launches of the last hdg_solve
- * or hdg_apply_K calls with event timing enabled (enable = 1), and the launch
- * count.  For benchmarks. */
+/* Event timing of the block-matvec launches (hdg_solve, hdg_apply_K and the
+ * polynomial steps) while enabled: hdg_set_timing(p, 1) clears and enables,
+ * hdg_get_timing returns the summed device time (ms) and launch count of the
+ * matvecs with blocks in precision `kind` (HDG_FP64, HDG_FP32, HDG_BF16).
+ * The events are recorded on the caller's stream around each launch. */
 hdg_status hdg_set_timing(hdg_problem p, int enable);
 hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches);
+
+/* Number of CUDA kernels the library has launched in this process. */
+long long hdg_launch_count(void);
+
+/* Kernel variant of the block-row products (matvec, BJ and ASM applies):
+ * 0 = one thread per output row with direct global loads (default),
+ * 1 = shared-memory staging with bulk copies.  Used by the autotuner;
+ * results agree to rounding. */
+hdg_status hdg_set_kernel_variant(hdg_problem p, int variant);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,8 @@ _SIGS = {
     'hdg_get_poly': (_I, [_V, _P, _P, _I, ctypes.POINTER(_I)]),
     'hdg_set_timing': (_I, [_V, _I]),
     'hdg_get_timing': (_I, [_V, _I, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    'hdg_set_kernel_variant': (_I, [_V, _I]),
+    'hdg_launch_count': (ctypes.c_longlong, []),
 }
 
 _lib = None
@@ -187,3 +189,11 @@ def hdg_get_timing(p, kind=0):
     n = ctypes.c_int64()
     st = load().hdg_get_timing(p, kind, ctypes.byref(t), ctypes.byref(n))
     return st, t.value, n.value
+
+
+def hdg_set_kernel_variant(p, variant):
+    return load().hdg_set_kernel_variant(p, variant)
+
+
+def hdg_launch_count():
+    return load().hdg_launch_count()

@@ -17,6 +17,12 @@
 
 using namespace hdg;
 
+#include <atomic>
+namespace hdg {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace hdg
+
 namespace {
 
 struct CudaError {
@@ -48,6 +54,8 @@ struct hdg_problem_s {
   int dim = 0, nl = 0, M = 0, PE = 0, PF = 0, D = 0, R = 1, b = 0, nlb = 0, ms = 0, nlPF = 0, MPE = 0, MDPE = 0;
   int64_t NE = 0, NF = 0, nfree = 0, ndof = 0;
   std::vector<int32_t> h_elem_face, h_face_elem, h_free_of_face, h_nbr;
+  std::vector<int64_t> h_rowptr;
+  int64_t nnzb = 0, asm_nblk = 0;
   std::vector<uint8_t> h_face_dir;
   std::vector<uint8_t> condensed;
   int64_t n_condensed = 0;
@@ -60,6 +68,7 @@ struct hdg_problem_s {
   int32_t *d_nbr = nullptr, *d_cnt = nullptr, *d_slot_e = nullptr, *d_slot_lr = nullptr, *d_slot_lc = nullptr;
   int32_t *d_diag2 = nullptr, *d_rhs_src = nullptr, *d_bj_nbr = nullptr, *d_bj_cnt = nullptr;
   int32_t *d_asm_lf = nullptr, *d_asm_cnt = nullptr, *d_asm_face_free = nullptr, *d_fsum = nullptr;
+  int64_t *d_rowptr = nullptr, *d_bj_rowptr = nullptr, *d_asm_rowptr = nullptr;
 
   // condensation results
   double *d_Kbar = nullptr, *d_rbar = nullptr, *d_MinvB = nullptr, *d_MinvC = nullptr, *d_XF = nullptr,
@@ -102,9 +111,13 @@ struct hdg_problem_s {
   int *running = nullptr, *jend = nullptr, *on_estimate = nullptr, *done = nullptr, *iters = nullptr;
   unsigned* counter = nullptr;
   unsigned* d_err = nullptr;
+  float* x32 = nullptr;
   double *t1 = nullptr, *res = nullptr, *pq = nullptr, *pw = nullptr, *ptmp = nullptr, *pAq = nullptr,
          *pt = nullptr, *ze = nullptr, *xo = nullptr, *bo = nullptr;
   // pinned host mirrors
+  int* h_flag = nullptr;      // host-mapped progress flags of the current cycle
+  int* d_flag = nullptr;      // device alias of h_flag
+  std::vector<cudaEvent_t> ev_iter;
   double* h_dbl = nullptr;
   int* h_int = nullptr;
   unsigned* h_err = nullptr;
@@ -113,8 +126,9 @@ struct hdg_problem_s {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  double t_mv_ms = 0.0;
-  int64_t n_mv = 0;
+  double t_mv_ms[3] = {0.0, 0.0, 0.0};
+  int64_t n_mv[3] = {0, 0, 0};
+  std::vector<int> ev_prec;
   int br_variant = 0;
 
   void* dalloc(size_t nbytes) {
@@ -269,6 +283,19 @@ hdg_status build_maps(hdg_problem p) {
   }
   std::vector<int32_t> bjn(nf), bjc(nf, 1);
   for (int64_t f = 0; f < nf; ++f) bjn[f] = (int32_t)f;
+  // compact block offsets of the face rows, the BJ blocks and the ASM panels
+  std::vector<int64_t> rp(nf + 1, 0), bjrp(nf + 1, 0), arp(p->NE + 1, 0);
+  for (int64_t f = 0; f < nf; ++f) {
+    rp[f + 1] = rp[f] + cnt[f];
+    bjrp[f + 1] = f + 1;
+  }
+  for (int64_t e = 0; e < p->NE; ++e) arp[e + 1] = arp[e] + acnt[e];
+  p->nnzb = rp[nf];
+  p->asm_nblk = arp[p->NE];
+  p->h_rowptr = rp;
+  p->d_rowptr = p->upload(rp);
+  p->d_bj_rowptr = p->upload(bjrp);
+  p->d_asm_rowptr = p->upload(arp);
   p->h_nbr = nbr;
   p->d_nbr = p->upload(nbr);
   p->d_cnt = p->upload(cnt);
@@ -402,10 +429,11 @@ struct Ops {
     *a = p->ev_pool[p->ev_used];
     CK(cudaEventRecord(*a, s));
   }
-  void mv_timed_end() {
+  void mv_timed_end(int prec) {
     if (!p->timing) return;
     CK(cudaEventRecord(p->ev_pool[p->ev_used + 1], s));
     p->ev_used += 2;
+    p->ev_prec.push_back(prec);
   }
 
   // y = K x (prec storage), epilogue
@@ -414,6 +442,7 @@ struct Ops {
     d.prec = prec;
     d.blk = prec == HDG_FP64 ? (const void*)p->K64 : prec == HDG_FP32 ? (const void*)p->K32 : (const void*)p->K16;
     d.blk_stride = prec == HDG_FP64 ? p->s64 : prec == HDG_FP32 ? p->s32 : p->s16;
+    d.rowptr = p->d_rowptr;
     d.nbr = p->d_nbr;
     d.cnt = p->d_cnt;
     d.n_units = p->nfree;
@@ -422,6 +451,11 @@ struct Ops {
     d.max_slots = p->ms;
     d.R = R;
     d.in = x;
+    d.in32 = nullptr;
+    if (prec != HDG_FP64) {
+      to_f32(x, p->x32, p->ndof * R, s);
+      d.in32 = p->x32;
+    }
     d.out = y;
     d.epi = epi;
     d.rhs = rhs;
@@ -431,7 +465,7 @@ struct Ops {
     cudaEvent_t a;
     mv_timed_begin(&a);
     blockrow(d, p->br_variant, s);
-    mv_timed_end();
+    mv_timed_end(prec);
   }
   // y = M^{-1} x for the base preconditioner
   void Minv(int pc, int prec, const double* x, double* y, const int* active) {
@@ -443,6 +477,11 @@ struct Ops {
     d.prec = prec;
     d.R = R;
     d.in = x;
+    d.in32 = nullptr;
+    if (prec != HDG_FP64) {
+      to_f32(x, p->x32, p->ndof * R, s);
+      d.in32 = p->x32;
+    }
     d.epi = EPI_STORE;
     d.active = active;
     d.err = p->d_err;
@@ -450,6 +489,7 @@ struct Ops {
     if (pc == HDG_PC_BJ) {
       d.blk = prec == HDG_FP64 ? (const void*)p->bj64 : prec == HDG_FP32 ? (const void*)p->bj32 : (const void*)p->bj16;
       d.blk_stride = prec == HDG_FP64 ? p->bs64 : prec == HDG_FP32 ? p->bs32 : p->bs16;
+      d.rowptr = p->d_bj_rowptr;
       d.nbr = p->d_bj_nbr;
       d.cnt = p->d_bj_cnt;
       d.n_units = p->nfree;
@@ -460,6 +500,7 @@ struct Ops {
     } else {
       d.blk = prec == HDG_FP64 ? (const void*)p->as64 : prec == HDG_FP32 ? (const void*)p->as32 : (const void*)p->as16;
       d.blk_stride = prec == HDG_FP64 ? p->as_s64 : prec == HDG_FP32 ? p->as_s32 : p->as_s16;
+      d.rowptr = p->d_asm_rowptr;
       d.nbr = p->d_asm_face_free;
       d.cnt = p->d_asm_cnt;
       d.n_units = p->NE;
@@ -533,6 +574,21 @@ struct Ops {
   }
 };
 
+// Adds the durations of the recorded block-matvec launches to the per-precision totals.
+void collect_timing(hdg_problem p, cudaStream_t s) {
+  if (!p->timing || p->ev_used == 0) return;
+  CK(cudaStreamSynchronize(s));
+  for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
+    const int pr = p->ev_prec[i / 2];
+    p->t_mv_ms[pr] += ms;
+    p->n_mv[pr] += 1;
+  }
+  p->ev_used = 0;
+  p->ev_prec.clear();
+}
+
 void ensure_workspace(hdg_problem p, int m) {
   if (p->ws_m >= m) return;
   const int64_t len = p->ndof * p->R;
@@ -548,6 +604,7 @@ void ensure_workspace(hdg_problem p, int m) {
     p->pAq = (double*)A(sizeof(double) * len);
     p->pt = (double*)A(sizeof(double) * len);
     p->xo = (double*)A(sizeof(double) * len);
+    p->x32 = (float*)A(sizeof(float) * len);
     p->bo = (double*)A(sizeof(double) * len);
     p->ze = (double*)A(sizeof(double) * p->NE * p->nlb * R);
     p->tolabs = (double*)A(sizeof(double) * kMaxR);
@@ -615,6 +672,7 @@ GmresView make_view(hdg_problem p, int R, int m, double rtol, int maxit) {
   k.done = p->done;
   k.iters = p->iters;
   k.maxit = maxit;
+  k.hflag = p->d_flag;
   k.counter = p->counter;
   k.err = p->d_err;
   return k;
@@ -726,12 +784,22 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
     set_ints(p, p->running, 1, R, s);
     ops.Pinv(o, mprec, kpoly, p->res, p->V, nullptr);
     launch_norms(k, p->V, nullptr, 1, nullptr, s);
+    // Iterations are enqueued at most kLag steps ahead of the device: before
+    // step j the host waits for step j-kLag and stops once its flag says that
+    // no right-hand side is still running (no empty launches after convergence).
+    constexpr int kLag = 2;
+    for (int j = 0; j <= m; ++j) p->h_flag[j] = 1;
     for (int j = 0; j < m; ++j) {
+      if (j >= kLag) {
+        CK(cudaEventSynchronize(p->ev_iter[j - kLag]));
+        if (!((volatile int*)p->h_flag)[j - kLag]) break;
+      }
       double* vj = p->V + (int64_t)j * len;
       double* vn = p->V + (int64_t)(j + 1) * len;
       ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running);
       ops.Pinv(o, mprec, kpoly, p->t1, vn, p->running);
       orthogonalize(k, o.orth, j, s);
+      CK(cudaEventRecord(p->ev_iter[j], s));
     }
     launch_backsolve(k, s);
     launch_xupdate(k, x, s);
@@ -804,6 +872,13 @@ hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_pr
     CK(cudaMallocHost(&p->h_dbl, sizeof(double) * 4 * kMaxR + 64));
     CK(cudaMallocHost(&p->h_int, sizeof(int) * 4 * kMaxR + 64));
     CK(cudaMallocHost(&p->h_err, sizeof(unsigned) * 4));
+    CK(cudaHostAlloc(&p->h_flag, sizeof(int) * (kMaxBasis + 8), cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer((void**)&p->d_flag, p->h_flag, 0));
+    for (int i = 0; i < kMaxBasis + 8; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      p->ev_iter.push_back(e);
+    }
     p->d_err = (unsigned*)p->dalloc(sizeof(unsigned) * 4);
     CK(cudaMemset(p->d_err, 0, sizeof(unsigned) * 4));
     hdg_status st = build_maps(p);
@@ -848,6 +923,8 @@ hdg_status hdg_problem_destroy(hdg_problem p) {
   for (void* q : p->allocs) cudaFree(q);
   p->allocs.clear();
   for (auto e : p->ev_pool) cudaEventDestroy(e);
+  for (auto e : p->ev_iter) cudaEventDestroy(e);
+  if (p->h_flag) cudaFreeHost(p->h_flag);
   if (p->h_dbl) cudaFreeHost(p->h_dbl);
   if (p->h_int) cudaFreeHost(p->h_int);
   if (p->h_err) cudaFreeHost(p->h_err);
@@ -944,7 +1021,7 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   try {
     DeviceGuard dg(p->device);
-    const int64_t rows = p->nfree * p->ms;
+    const int64_t rows = std::max<int64_t>(p->nnzb, 1);
     if (!p->K64) p->K64 = (double*)p->dalloc(sizeof(double) * rows * p->s64);
     if (!p->K32) p->K32 = (float*)p->dalloc(sizeof(float) * rows * p->s32);
     const bool need16 = opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16);
@@ -967,6 +1044,7 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
     d.rhs_src = p->d_rhs_src;
     d.elem_face = p->d_elem_face;
     d.face_dir = p->d_face_dir;
+    d.rowptr = p->d_rowptr;
     d.K64 = p->K64;
     d.s64 = p->s64;
     d.K32 = p->K32;
@@ -1000,7 +1078,7 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
     const bool need16 = (o->poly_prec == HDG_BF16 || o->inner_prec == HDG_BF16);
     if (o->pc == HDG_PC_BJ) {
       double* tmp = (double*)p->dalloc(sizeof(double) * p->nfree * b * b);
-      extract_diag(p->K64, p->s64, p->ms, b, p->nfree, tmp, s);
+      extract_diag(p->K64, p->s64, p->d_rowptr, b, p->nfree, tmp, s);
       inverse_f64(tmp, b, (int64_t)b * b, p->nfree, p->d_err, s);
       p->bs64 = padded_stride<double>((int64_t)b * b);
       p->bs32 = padded_stride<float>((int64_t)b * b);
@@ -1016,17 +1094,18 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       const int nlb = p->nlb;
       if (nlb > inverse_max_n()) return HDG_ERR_ARG;
       double* P = (double*)p->dalloc(sizeof(double) * p->NE * nlb * nlb);
-      asm_build(p->d_Kbar, nlb, b, p->nl, p->NE, p->d_asm_lf, p->d_asm_cnt, p->d_asm_face_free, p->K64, p->s64, p->ms,
-                P, s);
+      asm_build(p->d_Kbar, nlb, b, p->nl, p->NE, p->d_asm_lf, p->d_asm_cnt, p->d_asm_face_free, p->K64, p->s64,
+                p->d_rowptr, P, s);
       inverse_f64(P, nlb, (int64_t)nlb * nlb, p->NE, p->d_err, s);
       p->as_s64 = padded_stride<double>((int64_t)nlb * b);
       p->as_s32 = padded_stride<float>((int64_t)nlb * b);
       p->as_s16 = padded_stride<__nv_bfloat16>((int64_t)nlb * b);
-      if (!p->as64) p->as64 = (double*)p->dalloc(sizeof(double) * p->NE * p->nl * p->as_s64);
-      if (!p->as32) p->as32 = (float*)p->dalloc(sizeof(float) * p->NE * p->nl * p->as_s32);
-      if (need16 && !p->as16)
-        p->as16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * p->NE * p->nl * p->as_s16);
-      asm_pack(P, nlb, b, p->nl, p->NE, p->as64, p->as_s64, p->as32, p->as_s32, p->as16, p->as_s16, s);
+      const int64_t npan = std::max<int64_t>(p->asm_nblk, 1);
+      if (!p->as64) p->as64 = (double*)p->dalloc(sizeof(double) * npan * p->as_s64);
+      if (!p->as32) p->as32 = (float*)p->dalloc(sizeof(float) * npan * p->as_s32);
+      if (need16 && !p->as16) p->as16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * npan * p->as_s16);
+      asm_pack(P, nlb, b, p->nl, p->NE, p->d_asm_rowptr, p->as64, p->as_s64, p->as32, p->as_s32, p->as16, p->as_s16,
+               s);
       hdg_status st = check_err(p, s);
       p->dfree(P, sizeof(double) * p->NE * nlb * nlb);
       if (st != HDG_OK) return st;
@@ -1163,17 +1242,7 @@ hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* o, void* stream, hdg_
       inf.rel_resid = rel;
       if (st == HDG_OK) st = conv ? HDG_OK : HDG_ERR_NOT_CONVERGED;
     }
-    // matvec timing
-    if (p->timing && p->ev_used > 0) {
-      CK(cudaStreamSynchronize(s));
-      for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
-        p->t_mv_ms += ms;
-        p->n_mv += 1;
-      }
-      p->ev_used = 0;
-    }
+        collect_timing(p, s);
     if (info) *info = inf;
     return st;
   } catch (const CudaError& e) {
@@ -1259,19 +1328,11 @@ hdg_status hdg_apply_K(hdg_problem p, int prec, const double* x, double* y, void
   cudaStream_t s = (cudaStream_t)stream;
   try {
     DeviceGuard dg(p->device);
+    ensure_workspace(p, std::max(p->ws_m, 1));
     Ops ops{p, s, p->R};
     ops.K(prec, x, y, EPI_STORE, nullptr, nullptr, nullptr);
     CK(cudaGetLastError());
-    if (p->timing && p->ev_used > 0) {
-      CK(cudaStreamSynchronize(s));
-      for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
-        p->t_mv_ms += ms;
-        p->n_mv += 1;
-      }
-      p->ev_used = 0;
-    }
+    collect_timing(p, s);
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
@@ -1326,13 +1387,18 @@ hdg_status hdg_get_face_rows(hdg_problem p, int64_t f0, int64_t count, double* b
     CK(cudaDeviceSynchronize());
     const int b = p->b, ms = p->ms;
     if (blocks) {
-      std::vector<double> tmp((size_t)count * ms * p->s64);
-      CK(cudaMemcpy(tmp.data(), p->K64 + f0 * ms * p->s64, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost));
-      for (int64_t f = 0; f < count; ++f)
-        for (int s = 0; s < ms; ++s)
+      const int64_t b0 = p->h_rowptr[f0], b1 = p->h_rowptr[f0 + count];
+      std::vector<double> tmp((size_t)std::max<int64_t>(b1 - b0, 1) * p->s64);
+      if (b1 > b0)
+        CK(cudaMemcpy(tmp.data(), p->K64 + b0 * p->s64, sizeof(double) * (b1 - b0) * p->s64, cudaMemcpyDeviceToHost));
+      std::fill(blocks, blocks + count * ms * b * b, 0.0);
+      for (int64_t f = 0; f < count; ++f) {
+        const int64_t rb = p->h_rowptr[f0 + f] - b0, ns = p->h_rowptr[f0 + f + 1] - p->h_rowptr[f0 + f];
+        for (int64_t s = 0; s < ns; ++s)
           for (int i = 0; i < b; ++i)
             for (int j = 0; j < b; ++j)
-              blocks[((f * ms + s) * b + i) * b + j] = tmp[(f * ms + s) * p->s64 + (int64_t)j * b + i];
+              blocks[((f * ms + s) * b + i) * b + j] = tmp[(rb + s) * p->s64 + (int64_t)j * b + i];
+      }
     }
     if (nbr) std::memcpy(nbr, p->h_nbr.data() + f0 * ms, sizeof(int32_t) * count * ms);
     if (r) CK(cudaMemcpy(r, p->d_r, sizeof(double) * p->ndof * p->R, cudaMemcpyDeviceToHost));
@@ -1363,16 +1429,27 @@ hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n) 
 hdg_status hdg_set_timing(hdg_problem p, int enable) {
   if (!p) return HDG_ERR_ARG;
   p->timing = enable != 0;
-  p->t_mv_ms = 0.0;
-  p->n_mv = 0;
+  for (int i = 0; i < 3; ++i) {
+    p->t_mv_ms[i] = 0.0;
+    p->n_mv[i] = 0;
+  }
   p->ev_used = 0;
+  p->ev_prec.clear();
   return HDG_OK;
 }
 
 hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches) {
-  if (!p || kind != 0) return HDG_ERR_ARG;
-  if (total_ms) *total_ms = p->t_mv_ms;
-  if (launches) *launches = p->n_mv;
+  if (!p || kind < 0 || kind > 2) return HDG_ERR_ARG;
+  if (total_ms) *total_ms = p->t_mv_ms[kind];
+  if (launches) *launches = p->n_mv[kind];
+  return HDG_OK;
+}
+
+long long hdg_launch_count(void) { return hdg::g_launches.load(); }
+
+hdg_status hdg_set_kernel_variant(hdg_problem p, int variant) {
+  if (!p || variant < 0 || variant >= blockrow_variants()) return HDG_ERR_ARG;
+  p->br_variant = variant;
   return HDG_OK;
 }
 

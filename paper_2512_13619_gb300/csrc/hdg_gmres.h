@@ -34,6 +34,7 @@ struct GmresView {
   int* done;          // R
   int* iters;         // R
   int maxit;
+  int* hflag;         // host-mapped: hflag[j] = 1 while any RHS is running after step j
   unsigned* counter;
   unsigned* err;
 };

@@ -33,18 +33,20 @@ int inverse_max_n();
 // --------------------------------------------------------------- block rows
 // out[u][row][r] = epilogue( sum_{s < cnt[u]} sum_{c < bc}
 //                   blk[u][s](row, c) * in[(nbr[u][s]*bc + c)*R + r] )
-// blk[u][s] is a column-major b_rows x bc block at blk + (u*max_slots + s)*
-// blk_stride elements.  Slots of a unit are packed first (cnt[u] of them).
+// blk[u][s] is a column-major b_rows x bc block at blk + (rowptr[u] + s)*
+// blk_stride elements (compact storage: cnt[u] = rowptr[u+1] - rowptr[u]).
 enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_SCALE = 2 };
 struct BlockRowDesc {
   int prec;               // HDG_FP64 / HDG_FP32 / HDG_BF16 storage of blk
   const void* blk;
   int64_t blk_stride;     // elements per slot block (padded to 16 bytes)
+  const int64_t* rowptr;  // n_units + 1 block offsets
   const int32_t* nbr;     // n_units * max_slots
   const int32_t* cnt;     // n_units
   int64_t n_units;
   int b_rows, bc, max_slots, R;
   const double* in;
+  const float* in32;      // FP32 copy of `in` (required for FP32/BF16 blocks)
   double* out;
   int epi;
   const double* rhs;      // EPI_RESID: out = rhs - acc
@@ -54,6 +56,8 @@ struct BlockRowDesc {
 };
 void blockrow(const BlockRowDesc& d, int variant, cudaStream_t s);
 int blockrow_variants();
+// FP64 -> FP32 copy of a vector (rounding to nearest)
+void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 
 // --------------------------------------------------------------- assembly etc.
 struct AssembleDesc {
@@ -68,6 +72,7 @@ struct AssembleDesc {
   const int32_t* rhs_src;        // n_free*4: (e1,l1,e2,l2)
   const int32_t* elem_face;      // n_elem*nl
   const uint8_t* face_dir;       // n_face
+  const int64_t* rowptr;         // n_free + 1 compact block offsets of the face rows
   double* K64; int64_t s64;
   float* K32; int64_t s32;
   __nv_bfloat16* K16; int64_t s16;
@@ -76,7 +81,7 @@ struct AssembleDesc {
 void assemble(const AssembleDesc& d, cudaStream_t s);
 
 // copy diagonal blocks (slot 0, column-major) into dense row-major blocks
-void extract_diag(const double* K64, int64_t s64, int max_slots, int b, int64_t n_free, double* out,
+void extract_diag(const double* K64, int64_t s64, const int64_t* rowptr, int b, int64_t n_free, double* out,
                   cudaStream_t s);
 // dense row-major FP64 n x n blocks -> column-major padded blocks in the three precisions
 void pack_blocks(const double* in, int n, int64_t count, double* o64, int64_t s64, float* o32, int64_t s32,
@@ -85,10 +90,10 @@ void pack_blocks(const double* in, int n, int64_t count, double* o64, int64_t s6
 // (compacted), diagonal blocks of interior faces replaced by K_ff, padding = identity.
 void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const int32_t* asm_lf,
                const int32_t* asm_cnt, const int32_t* asm_face_free, const double* K64, int64_t s64,
-               int max_slots, double* P, cudaStream_t s);
+               const int64_t* rowptr, double* P, cudaStream_t s);
 // ASM panels: column-major (nl*b) x b panels for the free local faces of each element
-void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, double* o64, int64_t s64, float* o32,
-              int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s);
+void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, const int64_t* arowptr, double* o64,
+              int64_t s64, float* o32, int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s);
 // z_f = z^{e1}[slot s1] + z^{e2}[slot s2] (face-parallel, no atomics)
 void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum, double* z,
                   cudaStream_t s);

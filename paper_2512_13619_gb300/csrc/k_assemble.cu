@@ -15,8 +15,11 @@ namespace {
 __global__ void assemble_kernel(AssembleDesc d) {
   const int64_t f = blockIdx.x;
   const int b = d.b, bb = b * b, nlb = d.nlb;
-  for (int s = 0; s < d.max_slots; ++s) {
+  const int64_t r0 = d.rowptr[f];
+  const int ns = (int)(d.rowptr[f + 1] - r0);
+  for (int s = 0; s < ns; ++s) {
     const int64_t slot = f * d.max_slots + s;
+    const int64_t dst = r0 + s;
     const int e = d.slot_e[slot];
     const int lr = d.slot_lr[slot], lc = d.slot_lc[slot];
     const int e2 = (s == 0) ? d.diag2[f * 2] : -1;
@@ -28,9 +31,9 @@ __global__ void assemble_kernel(AssembleDesc d) {
         v = d.Kbar[(int64_t)e * nlb * nlb + (int64_t)(lr * b + i) * nlb + lc * b + j];
         if (e2 >= 0) v += d.Kbar[(int64_t)e2 * nlb * nlb + (int64_t)(l2 * b + i) * nlb + l2 * b + j];
       }
-      if (d.K64) d.K64[slot * d.s64 + idx] = v;
-      if (d.K32) d.K32[slot * d.s32 + idx] = (float)v;
-      if (d.K16) d.K16[slot * d.s16 + idx] = __float2bfloat16_rn((float)v);
+      if (d.K64) d.K64[dst * d.s64 + idx] = v;
+      if (d.K32) d.K32[dst * d.s32 + idx] = (float)v;
+      if (d.K16) d.K16[dst * d.s16 + idx] = __float2bfloat16_rn((float)v);
     }
   }
   // right-hand side: r_f = sum over the face's elements of rbar^e_l minus the
@@ -56,12 +59,12 @@ __global__ void assemble_kernel(AssembleDesc d) {
   }
 }
 
-__global__ void extract_diag_kernel(const double* K64, int64_t s64, int max_slots, int b, int64_t n_free,
+__global__ void extract_diag_kernel(const double* K64, int64_t s64, const int64_t* rowptr, int b, int64_t n_free,
                                     double* out) {
   const int64_t f = blockIdx.x;
   for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
     const int j = idx / b, i = idx - j * b;
-    out[f * b * b + i * b + j] = K64[f * max_slots * s64 + idx];
+    out[f * b * b + i * b + j] = K64[rowptr[f] * s64 + idx];
   }
 }
 
@@ -82,7 +85,7 @@ __global__ void pack_blocks_kernel(const double* in, int n, double* o64, int64_t
 // padding rows/columns = identity.
 __global__ void asm_build_kernel(const double* Kbar, int nlb, int b, int nl, const int32_t* asm_lf,
                                  const int32_t* asm_cnt, const int32_t* asm_face_free, const double* K64,
-                                 int64_t s64, int max_slots, double* P) {
+                                 int64_t s64, const int64_t* rowptr, double* P) {
   const int64_t e = blockIdx.x;
   const int cnt = asm_cnt[e];
   const int n = nlb;
@@ -95,7 +98,7 @@ __global__ void asm_build_kernel(const double* Kbar, int nlb, int b, int nl, con
       v = (rr == cc) ? 1.0 : 0.0;
     } else if (s == t) {
       const int64_t f = asm_face_free[e * nl + s];
-      v = K64[f * max_slots * s64 + (int64_t)j * b + i];
+      v = K64[rowptr[f] * s64 + (int64_t)j * b + i];
     } else {
       const int ls = asm_lf[e * nl + s], lt = asm_lf[e * nl + t];
       v = Kbar[e * (int64_t)n * n + (int64_t)(ls * b + i) * n + lt * b + j];
@@ -104,12 +107,13 @@ __global__ void asm_build_kernel(const double* Kbar, int nlb, int b, int nl, con
   }
 }
 
-__global__ void asm_pack_kernel(const double* Pinv, int nlb, int b, int nl, double* o64, int64_t s64, float* o32,
-                                int64_t s32, __nv_bfloat16* o16, int64_t s16) {
+__global__ void asm_pack_kernel(const double* Pinv, int nlb, int b, int nl, const int64_t* arowptr, double* o64,
+                                int64_t s64, float* o32, int64_t s32, __nv_bfloat16* o16, int64_t s16) {
   const int64_t e = blockIdx.x;
   const int n = nlb;
-  for (int s = 0; s < nl; ++s) {
-    const int64_t panel = e * nl + s;
+  const int ns = (int)(arowptr[e + 1] - arowptr[e]);
+  for (int s = 0; s < ns; ++s) {
+    const int64_t panel = arowptr[e] + s;
     for (int idx = threadIdx.x; idx < n * b; idx += blockDim.x) {
       const int c = idx / n, row = idx - c * n;
       const double v = Pinv[e * (int64_t)n * n + (int64_t)row * n + s * b + c];
@@ -200,47 +204,47 @@ inline unsigned grid_for(int64_t total, int threads) {
 
 void assemble(const AssembleDesc& d, cudaStream_t s) {
   if (d.n_free <= 0) return;
-  assemble_kernel<<<(unsigned)d.n_free, 256, 0, s>>>(d);
+  count_launch(); assemble_kernel<<<(unsigned)d.n_free, 256, 0, s>>>(d);
 }
 
-void extract_diag(const double* K64, int64_t s64, int max_slots, int b, int64_t n_free, double* out,
+void extract_diag(const double* K64, int64_t s64, const int64_t* rowptr, int b, int64_t n_free, double* out,
                   cudaStream_t s) {
   if (n_free <= 0) return;
-  extract_diag_kernel<<<(unsigned)n_free, 256, 0, s>>>(K64, s64, max_slots, b, n_free, out);
+  count_launch(); extract_diag_kernel<<<(unsigned)n_free, 256, 0, s>>>(K64, s64, rowptr, b, n_free, out);
 }
 
 void pack_blocks(const double* in, int n, int64_t count, double* o64, int64_t s64, float* o32, int64_t s32,
                  __nv_bfloat16* o16, int64_t s16, cudaStream_t s) {
   if (count <= 0) return;
-  pack_blocks_kernel<<<(unsigned)count, 256, 0, s>>>(in, n, o64, s64, o32, s32, o16, s16);
+  count_launch(); pack_blocks_kernel<<<(unsigned)count, 256, 0, s>>>(in, n, o64, s64, o32, s32, o16, s16);
 }
 
 void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const int32_t* asm_lf,
                const int32_t* asm_cnt, const int32_t* asm_face_free, const double* K64, int64_t s64,
-               int max_slots, double* P, cudaStream_t s) {
+               const int64_t* rowptr, double* P, cudaStream_t s) {
   if (n_elem <= 0) return;
-  asm_build_kernel<<<(unsigned)n_elem, 256, 0, s>>>(Kbar, nlb, b, nl, asm_lf, asm_cnt, asm_face_free, K64, s64,
-                                                     max_slots, P);
+  count_launch(); asm_build_kernel<<<(unsigned)n_elem, 256, 0, s>>>(Kbar, nlb, b, nl, asm_lf, asm_cnt, asm_face_free, K64, s64,
+                                                     rowptr, P);
 }
 
-void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, double* o64, int64_t s64, float* o32,
-              int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s) {
+void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, const int64_t* arowptr, double* o64,
+              int64_t s64, float* o32, int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s) {
   if (n_elem <= 0) return;
-  asm_pack_kernel<<<(unsigned)n_elem, 256, 0, s>>>(Pinv, nlb, b, nl, o64, s64, o32, s32, o16, s16);
+  count_launch(); asm_pack_kernel<<<(unsigned)n_elem, 256, 0, s>>>(Pinv, nlb, b, nl, arowptr, o64, s64, o32, s32, o16, s16);
 }
 
 void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum, double* z,
                   cudaStream_t s) {
   int64_t total = n_free * b * R;
   if (total <= 0) return;
-  asm_face_sum_kernel<<<grid_for(total, 256), 256, 0, s>>>(ze, nlb, b, R, n_free, fsum, z);
+  count_launch(); asm_face_sum_kernel<<<grid_for(total, 256), 256, 0, s>>>(ze, nlb, b, R, n_free, fsum, z);
 }
 
 void expand_trace(const double* x, const double* uhatD, const int32_t* free_of_face, int64_t n_face, int b, int R,
                   double* full, cudaStream_t s) {
   int64_t total = n_face * b * R;
   if (total <= 0) return;
-  expand_trace_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, uhatD, free_of_face, n_face, b, R, full);
+  count_launch(); expand_trace_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, uhatD, free_of_face, n_face, b, R, full);
 }
 
 void recover(const RecoverDesc& d, cudaStream_t s) {
@@ -248,7 +252,7 @@ void recover(const RecoverDesc& d, cudaStream_t s) {
   const int b = d.M * d.PF;
   size_t smem = (size_t)(d.nl * b + d.M * d.PE) * d.R * sizeof(double);
   cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  recover_kernel<<<(unsigned)d.n_elem, 256, smem, s>>>(d);
+  count_launch(); recover_kernel<<<(unsigned)d.n_elem, 256, smem, s>>>(d);
 }
 
 }  // namespace hdg

@@ -4,16 +4,21 @@
 // element solves z^e = (Pbar^e)^{-1} y^e of the ASM apply (Sec. 4.6) all have
 // the form
 //     out[u][row] = sum_{s < cnt[u]} sum_c blk[u][s](row, c) * in[nbr[u][s]][c]
-// with dense column-major slot blocks.  Instead of materialising the paper's
-// extended x vector, the gather goes through the neighbour table.
+// with dense column-major slot blocks stored compactly (unit u's blocks at
+// rowptr[u] .. rowptr[u+1]-1).  Instead of materialising the paper's extended
+// x vector, the gather goes through the neighbour table.
 //
-// Kernel "tma": a persistent CTA streams the slot blocks of a group of units
-// through a ring of shared-memory stages with 1D bulk copies
-// (cp.async.bulk, completion tracked by mbarrier transaction counts); one
-// producer warp issues the copies, the consumer warps read each block with
-// one thread per output row (column-major blocks make those reads
-// conflict-free) and gather x through L1/L2.  HBM sees each block once.
-// Kernel "direct": the same mapping with plain coalesced global loads.
+// Kernel "tma": a persistent CTA takes tasks (a group of G consecutive units,
+// or one unit split into slot ranges when a row is long); each task's blocks
+// are contiguous in HBM and arrive with ONE 1D bulk copy (cp.async.bulk,
+// completion by mbarrier transaction count) into a ring of shared-memory
+// stages filled by a producer warp.  Consumer thread (unit g, row, part p)
+// accumulates columns c = p, p+P, ... of every slot (column-major blocks make
+// the shared-memory reads conflict-free), gathers x through L1/L2, and the P
+// partial sums meet in shared memory before the epilogue.
+// Kernel "direct": one thread per output row with plain global loads.
+// FP32/BF16 blocks multiply an FP32 copy of x (converting each gathered FP64
+// value per product would run on the FP64 pipe, 1/57 of the FP32 rate here).
 #include <algorithm>
 #include "hdg_common.cuh"
 #include "hdg_internal.h"
@@ -25,16 +30,11 @@ namespace {
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
-template <int R, typename A>
-__device__ __forceinline__ void epilogue(const BlockRowDesc& d, int64_t u, int row, const A (&acc)[R]) {
-  int64_t o = (u * d.b_rows + row) * R;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    double v = (double)acc[r];
-    if (d.epi == EPI_RESID) v = d.rhs[o + r] - v;
-    else if (d.epi == EPI_SCALE) v = d.scale[r] * v;
-    d.out[o + r] = v;
-  }
+__device__ __forceinline__ void epi_store(const BlockRowDesc& d, int64_t u, int row, int r, double v) {
+  const int64_t o = (u * d.b_rows + row) * d.R + r;
+  if (d.epi == EPI_RESID) v = d.rhs[o] - v;
+  else if (d.epi == EPI_SCALE) v = d.scale[r] * v;
+  d.out[o] = v;
 }
 
 __device__ __forceinline__ bool any_active(const int* active, int R) {
@@ -44,151 +44,257 @@ __device__ __forceinline__ bool any_active(const int* active, int R) {
   return false;
 }
 
+// x in the accumulation precision: FP64 from `in`, FP32 from the FP32 copy
+template <typename A> __device__ __forceinline__ A load_x(const BlockRowDesc& d, int64_t i);
+template <> __device__ __forceinline__ double load_x<double>(const BlockRowDesc& d, int64_t i) { return __ldg(d.in + i); }
+template <> __device__ __forceinline__ float load_x<float>(const BlockRowDesc& d, int64_t i) { return __ldg(d.in32 + i); }
+
+__device__ __forceinline__ void consumer_bar(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
+
+struct Plan {
+  int G, P, S, nch, nstage, NT, NPW;   // units/task, column parts, slots/chunk, chunks/task, stages, consumers, producer warps
+  int stage_bytes;                    // bytes of one stage (blocks + gathered x + metadata)
+  int kbytes;                         // block area of a stage
+  int xoff, moff;                     // offsets of the x area and the metadata area inside a stage
+  int64_t ntasks;
+};
+
+// Stage layout: [blocks: kbytes][x: G*S*bc*R doubles][meta: G ints cnt, G ints block offset, G*S ints unused]
 template <typename T, int R>
-__global__ void __launch_bounds__(544) blockrow_tma_kernel(BlockRowDesc d, int S, int nstage, int stage_bytes) {
+__global__ void __launch_bounds__(640) blockrow_tma_kernel(BlockRowDesc d, Plan pl) {
   using A = typename Acc<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* empty = full + nstage;
-  unsigned char* stages = smem + 128;
+  uint64_t* empty = full + pl.nstage;
+  unsigned char* stages = smem + 256;
+  A* red = reinterpret_cast<A*>(stages + (size_t)pl.nstage * pl.stage_bytes);
   __shared__ volatile int s_abort;
+  __shared__ long long s_issued[8];   // last iteration issued on each stage (drain after an abort)
 
-  const int NT = blockDim.x - 32;          // consumer threads
-  const int nwc = NT / 32;
+  const int NT = pl.NT;
   const int tid = threadIdx.x;
-  const bool producer = tid >= NT;
   if (!any_active(d.active, R)) return;
   if (tid == 0) {
     s_abort = 0;
-    for (int i = 0; i < nstage; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], nwc);
+    for (int i = 0; i < pl.nstage; ++i) {
+      s_issued[i] = -1;
+      mbar_init(&full[i], 32);
+      mbar_init(&empty[i], NT / 32);
     }
     fence_mbar_init();
   }
   __syncthreads();
 
-  const int G = NT / d.b_rows;
-  const int64_t ngroups = (d.n_units + G - 1) / G;
-  const int nchunks = (d.max_slots + S - 1) / S;
   const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
   const T* blk = static_cast<const T*>(d.blk);
-  int64_t issued = 0;
+  const int G = pl.G, P = pl.P, S = pl.S, bc = d.bc;
+  const bool whole = (pl.nch == 1);
 
-  if (producer) {
-    if ((tid & 31) == 0) {
-      int64_t it = 0;
-      for (int64_t g = blockIdx.x; g < ngroups && !s_abort; g += gridDim.x) {
-        for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int st = (int)(it % nstage);
-          const unsigned ph = (unsigned)((it / nstage) & 1);
-          if (!mbar_wait_bounded(&empty[st], ph ^ 1u)) {
-            atomicOr(d.err, ERRBIT_TIMEOUT);
-            s_abort = 1;
-            break;
-          }
-          const int s0 = ch * S;
-          unsigned bytes = 0;
-          for (int gu = 0; gu < G; ++gu) {
-            int64_t u = g * G + gu;
-            if (u >= d.n_units) break;
-            int ns = min(S, d.cnt[u] - s0);
-            if (ns > 0) bytes += (unsigned)(ns * blk_bytes);
-          }
-          mbar_arrive_expect_tx(&full[st], bytes);
-          unsigned char* dst = stages + (size_t)st * stage_bytes;
-          for (int gu = 0; gu < G; ++gu) {
-            int64_t u = g * G + gu;
-            if (u >= d.n_units) break;
-            int ns = min(S, d.cnt[u] - s0);
-            if (ns > 0)
-              bulk_g2s(dst + (size_t)gu * S * blk_bytes, blk + (u * d.max_slots + s0) * d.blk_stride,
-                       (unsigned)(ns * blk_bytes), &full[st]);
-          }
-          issued = it + 1;
-        }
-      }
-      // drain: every issued copy must land before the CTA can exit
-      int64_t first = issued > nstage ? issued - nstage : 0;
-      for (int64_t t = first; t < issued; ++t)
-        if (!mbar_wait_bounded(&full[t % nstage], (unsigned)((t / nstage) & 1))) atomicOr(d.err, ERRBIT_TIMEOUT);
-    }
-  } else {
-    const int gu = tid / d.b_rows;
-    const int row = tid - gu * d.b_rows;
-    const int lane = tid & 31;
-    int64_t it = 0;
+  if (tid >= NT) {
+    // ------------------------------------------------------------ producers
+    // Warp w of NPW takes the CTA's tasks k = w, w+NPW, ...  For each chunk it
+    // loads the metadata and gathers x for the chunk into the stage with plain
+    // loads, lane 0 issues one bulk copy for the blocks, and all 32 lanes
+    // arrive on the stage's full barrier (lane 0 with the byte count).
+    const int w = (tid - NT) >> 5, lane = tid & 31;
     bool abort = false;
-    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-      const int64_t u = g * G + gu;
-      const bool act = (gu < G) && (u < d.n_units);
-      A acc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = (A)0;
-      for (int ch = 0; ch < nchunks; ++ch, ++it) {
-        const int st = (int)(it % nstage);
-        const unsigned ph = (unsigned)((it / nstage) & 1);
-        if (!abort && !mbar_wait_bounded(&full[st], ph)) {
-          atomicOr(d.err, ERRBIT_TIMEOUT);
-          abort = true;
+    for (int64_t k = w, t = blockIdx.x + (int64_t)w * gridDim.x; t < pl.ntasks;
+         k += pl.NPW, t += (int64_t)pl.NPW * gridDim.x) {
+      const int64_t u0 = t * G;
+      const int64_t u1 = min(u0 + G, d.n_units);
+      for (int ch = 0; ch < pl.nch; ++ch) {
+        const int64_t it = k * pl.nch + ch;
+        const int st = (int)(it % pl.nstage);
+        const unsigned ph = (unsigned)((it / pl.nstage) & 1);
+        if (s_abort || !mbar_wait_bounded(&empty[st], ph ^ 1u)) {
+          if (!s_abort) atomicOr(d.err, ERRBIT_TIMEOUT);
           s_abort = 1;
+          abort = true;
+          break;
         }
-        if (!abort && act) {
-          const int s0 = ch * S;
-          const int ns = min(S, d.cnt[u] - s0);
-          const T* sb = reinterpret_cast<const T*>(stages + (size_t)st * stage_bytes + (size_t)gu * S * blk_bytes);
-          for (int s = 0; s < ns; ++s) {
-            const int32_t nb = d.nbr[u * d.max_slots + s0 + s];
-            const double* xin = d.in + (int64_t)nb * d.bc * R;
-            const T* bs = sb + (size_t)s * d.blk_stride + row;
-#pragma unroll 4
-            for (int c = 0; c < d.bc; ++c) {
-              const A kv = cvt<A>(bs[c * d.b_rows]);
-#pragma unroll
-              for (int r = 0; r < R; ++r) acc[r] = fma(kv, (A)__ldg(xin + c * R + r), acc[r]);
-            }
+        unsigned char* sbase = stages + (size_t)st * pl.stage_bytes;
+        A* xs = reinterpret_cast<A*>(sbase + pl.xoff);
+        int* meta = reinterpret_cast<int*>(sbase + pl.moff);
+        const int s0 = whole ? 0 : ch * S;
+        int64_t b0, nb;
+        if (whole) {
+          b0 = d.rowptr[u0];
+          nb = d.rowptr[u1] - b0;
+        } else {
+          b0 = d.rowptr[u0] + s0;
+          nb = max(0, min(S, d.cnt[u0] - s0));
+        }
+        if (lane == 0) {
+          // register the bytes first (no arrival), then start the copy; the
+          // 32 arrivals of the warp come after the x stores below
+          const unsigned bytes = (unsigned)(nb * blk_bytes);
+          s_issued[st] = it;
+          if (bytes) {
+            mbar_expect_tx(&full[st], bytes);
+            bulk_g2s(sbase, blk + b0 * d.blk_stride, bytes, &full[st]);
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);
+        // per-unit metadata: number of slots in this chunk and block offset in the stage
+        for (int g = lane; g < G; g += 32) {
+          const int64_t u = u0 + g;
+          int ns = 0, off = 0;
+          if (u < d.n_units) {
+            ns = whole ? d.cnt[u] : max(0, min(S, d.cnt[u] - s0));
+            off = whole ? (int)(d.rowptr[u] - b0) : 0;
+          }
+          meta[g] = ns;
+          meta[G + g] = off;
+        }
+        // gathered x of every (unit, slot in chunk, column)
+        const int per_unit = S * bc * R;
+        for (int idx = lane; idx < G * per_unit; idx += 32) {
+          const int g = idx / per_unit;
+          const int rem = idx - g * per_unit;
+          const int sl = rem / (bc * R);
+          const int cr = rem - sl * bc * R;
+          const int64_t u = u0 + g;
+          A v = (A)0;
+          if (u < d.n_units) {
+            const int ns = whole ? d.cnt[u] : min(S, d.cnt[u] - s0);
+            if (sl < ns) v = load_x<A>(d, (int64_t)d.nbr[u * d.max_slots + s0 + sl] * bc * R + cr);
+          }
+          xs[idx] = v;
+        }
+        mbar_arrive(&full[st]);  // one arrival per lane (count 32); release orders the x stores
       }
-      if (act && !abort) epilogue<R, A>(d, u, row, acc);
       if (abort) break;
     }
+  } else {
+  // -------------------------------------------------------------- consumers
+  const int rows = G * d.b_rows;
+  const int lr = tid % rows;
+  const int part = tid / rows;
+  const int g = lr / d.b_rows;
+  const int row = lr - g * d.b_rows;
+  const int lane = tid & 31;
+  const bool in_part = part < P;
+  bool abort = false;
+  int64_t k = 0;
+  for (int64_t t = blockIdx.x; t < pl.ntasks; t += gridDim.x, ++k) {
+    const int64_t u = t * G + g;
+    A acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = (A)0;
+    for (int ch = 0; ch < pl.nch; ++ch) {
+      const int64_t it = k * pl.nch + ch;
+      const int st = (int)(it % pl.nstage);
+      const unsigned ph = (unsigned)((it / pl.nstage) & 1);
+      if (!abort && !mbar_wait_bounded(&full[st], ph)) {
+        atomicOr(d.err, ERRBIT_TIMEOUT);
+        abort = true;
+        s_abort = 1;
+      }
+      if (!abort && in_part) {
+        const unsigned char* sbase = stages + (size_t)st * pl.stage_bytes;
+        const int* meta = reinterpret_cast<const int*>(sbase + pl.moff);
+        const int ns = meta[g];
+        const T* sb = reinterpret_cast<const T*>(sbase) + (int64_t)meta[G + g] * d.blk_stride + row;
+        const A* xs = reinterpret_cast<const A*>(sbase + pl.xoff) + (int64_t)g * S * bc * R;
+        for (int sl = 0; sl < ns; ++sl) {
+          const T* bs = sb + (int64_t)sl * d.blk_stride;
+          const A* xv = xs + sl * bc * R;
+#pragma unroll 4
+          for (int c = part; c < bc; c += P) {
+            const A kv = cvt<A>(bs[c * d.b_rows]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(kv, xv[c * R + r], acc[r]);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    if (abort) break;
+    // reduce the P column parts of each output row
+    if (P == 1) {
+      if (in_part && u < d.n_units) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) epi_store(d, u, row, r, (double)acc[r]);
+      }
+    } else {
+      if (in_part) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) red[((int64_t)part * rows + lr) * R + r] = acc[r];
+      }
+      consumer_bar(NT);
+      if (part == 0 && u < d.n_units) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          A sum = red[(int64_t)lr * R + r];
+          for (int q = 1; q < P; ++q) sum += red[((int64_t)q * rows + lr) * R + r];
+          epi_store(d, u, row, r, (double)sum);
+        }
+      }
+      consumer_bar(NT);
+    }
   }
+  }
+  // After an abort, bulk copies may still be in flight on stages nobody
+  // consumed: wait (bounded) for them before the CTA's shared memory goes away.
   __syncthreads();
+  if (tid == 0 && s_abort) {
+    for (int i = 0; i < pl.nstage; ++i) {
+      const long long q = s_issued[i];
+      if (q >= 0 && !mbar_wait_bounded(&full[i], (unsigned)((q / pl.nstage) & 1))) atomicOr(d.err, ERRBIT_TIMEOUT);
+    }
+  }
 }
 
-template <typename T, int R>
+// One thread per output row; BC > 0 fixes the column count at compile time so
+// the loads of a whole slot block are in flight together.
+template <typename T, int R, int BC>
 __global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
   using A = typename Acc<T>::type;
   if (!any_active(d.active, R)) return;
+  const int bc = BC > 0 ? BC : d.bc;
   const int G = blockDim.x / d.b_rows;
   const int gu = threadIdx.x / d.b_rows;
   const int row = threadIdx.x - gu * d.b_rows;
   if (gu >= G) return;
   const T* blk = static_cast<const T*>(d.blk);
   const int64_t ngroups = (d.n_units + G - 1) / G;
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const int64_t u = g * G + gu;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int64_t u = grp * G + gu;
     if (u >= d.n_units) continue;
     A acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = (A)0;
     const int n = d.cnt[u];
+    const int64_t rp = d.rowptr[u];
+    const int32_t* nbr = d.nbr + u * d.max_slots;
     for (int s = 0; s < n; ++s) {
-      const int32_t nb = d.nbr[u * d.max_slots + s];
-      const double* xin = d.in + (int64_t)nb * d.bc * R;
-      const T* bs = blk + (u * d.max_slots + s) * d.blk_stride + row;
-#pragma unroll 4
-      for (int c = 0; c < d.bc; ++c) {
-        const A kv = cvt<A>(__ldg(bs + (size_t)c * d.b_rows));
+      const int64_t xb = (int64_t)nbr[s] * bc * R;
+      const T* bs = blk + (rp + s) * d.blk_stride + row;
+      if (BC > 0) {
+        T kv[BC > 0 ? BC : 1];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = fma(kv, (A)__ldg(xin + c * R + r), acc[r]);
+        for (int c = 0; c < (BC > 0 ? BC : 1); ++c) kv[c] = __ldg(bs + (size_t)c * d.b_rows);
+#pragma unroll
+        for (int c = 0; c < (BC > 0 ? BC : 1); ++c)
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] = fma(cvt<A>(kv[c]), load_x<A>(d, xb + c * R + r), acc[r]);
+      } else {
+#pragma unroll 4
+        for (int c = 0; c < bc; ++c) {
+          const A kv = cvt<A>(__ldg(bs + (size_t)c * d.b_rows));
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] = fma(kv, load_x<A>(d, xb + c * R + r), acc[r]);
+        }
       }
     }
-    epilogue<R, A>(d, u, row, acc);
+#pragma unroll
+    for (int r = 0; r < R; ++r) epi_store(d, u, row, r, (double)acc[r]);
   }
+}
+
+__global__ void to_f32_kernel(const double* x, float* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 int g_num_sms = 0;
@@ -202,58 +308,105 @@ int num_sms() {
   return g_num_sms;
 }
 
-// consumer thread count giving the best row utilisation (<= 512)
-int pick_nt(int b_rows) {
+constexpr size_t kStageTarget = 40 * 1024;
+constexpr size_t kSmemCap = 200 * 1024;
+
+int largest_divisor_leq(int n, int cap) {
+  for (int p = std::min(n, cap); p >= 1; --p)
+    if (n % p == 0) return p;
+  return 1;
+}
+
+template <typename T, int R>
+Plan make_plan(const BlockRowDesc& d) {
+  Plan pl{};
+  const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
+  const size_t row_bytes = (size_t)d.max_slots * blk_bytes;
+  const int nt_max = 512;
+  if (row_bytes <= kStageTarget) {
+    pl.G = (int)std::max<size_t>(1, std::min<size_t>(kStageTarget / row_bytes, (size_t)(nt_max / d.b_rows)));
+    pl.S = d.max_slots;
+    pl.nch = 1;
+    pl.kbytes = (int)(pl.G * row_bytes);
+  } else {
+    pl.G = 1;
+    pl.S = (int)std::max<size_t>(1, kStageTarget / blk_bytes);
+    if (pl.S > d.max_slots) pl.S = d.max_slots;
+    pl.nch = (d.max_slots + pl.S - 1) / pl.S;
+    pl.kbytes = (int)(pl.S * blk_bytes);
+  }
+  pl.P = largest_divisor_leq(d.bc, std::max(1, nt_max / (pl.G * d.b_rows)));
+  pl.NT = ((pl.G * d.b_rows * pl.P + 31) / 32) * 32;
+  pl.NPW = 4;
+  const size_t xbytes = (size_t)pl.G * pl.S * d.bc * R * sizeof(typename Acc<T>::type);
+  pl.xoff = (pl.kbytes + 15) / 16 * 16;
+  pl.moff = (int)((pl.xoff + xbytes + 15) / 16 * 16);
+  pl.stage_bytes = (int)((pl.moff + 2 * pl.G * sizeof(int) + 127) / 128 * 128);
+  const size_t red = (pl.P > 1) ? (size_t)pl.P * pl.G * d.b_rows * R * sizeof(typename Acc<T>::type) : 0;
+  pl.nstage = (int)std::min<size_t>(8, (kSmemCap - red) / pl.stage_bytes);
+  if (pl.nstage < 2) pl.nstage = 2;
+  pl.ntasks = (d.n_units + pl.G - 1) / pl.G;
+  return pl;
+}
+
+template <typename T, int R>
+void launch_tma(const BlockRowDesc& d, cudaStream_t s) {
+  const Plan pl = make_plan<T, R>(d);
+  const size_t red = (pl.P > 1) ? (size_t)pl.P * pl.G * d.b_rows * R * sizeof(typename Acc<T>::type) : 0;
+  const size_t smem = 256 + (size_t)pl.nstage * pl.stage_bytes + red;
+  auto kern = blockrow_tma_kernel<T, R>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  const int threads = pl.NT + 32 * pl.NPW;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = std::min<int64_t>(pl.ntasks, (int64_t)num_sms() * per_sm);
+  if (grid < 1) grid = 1;
+  count_launch(); kern<<<(unsigned)grid, threads, smem, s>>>(d, pl);
+}
+
+int pick_nt_direct(int b_rows) {
   int best = 32 * ((b_rows + 31) / 32), bestu = -1;
-  for (int nt = 32 * ((b_rows + 31) / 32); nt <= 512; nt += 32) {
-    int g = nt / b_rows;
-    int used = g * b_rows;
-    // utilisation in 1/1000, prefer larger CTAs on ties up to 256 threads
-    int util = used * 1000 / nt;
+  for (int nt = best; nt <= 512; nt += 32) {
+    int util = (nt / b_rows) * b_rows * 1000 / nt;
     if (util > bestu || (util == bestu && nt <= 256)) { bestu = util; best = nt; }
   }
   return best;
 }
 
-template <typename T, int R>
-void launch_tma(const BlockRowDesc& d, cudaStream_t s) {
-  const int NT = pick_nt(d.b_rows);
-  const int G = NT / d.b_rows;
-  const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
-  const size_t smem_cap = 200 * 1024;
-  const size_t stage_target = 32 * 1024;
-  int S = (int)std::max<size_t>(1, stage_target / (G * blk_bytes));
-  S = std::min(S, d.max_slots);
-  size_t stage_bytes = (size_t)G * S * blk_bytes;
-  int nstage = (int)std::min<size_t>(8, smem_cap / stage_bytes);
-  if (nstage < 2) nstage = 2;
-  size_t smem = 128 + (size_t)nstage * stage_bytes;
-  auto kern = blockrow_tma_kernel<T, R>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, smem);
-  if (per_sm < 1) per_sm = 1;
-  int64_t ngroups = (d.n_units + G - 1) / G;
-  int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * per_sm);
-  if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, NT + 32, smem, s>>>(d, S, nstage, (int)stage_bytes);
-}
-
-template <typename T, int R>
-void launch_direct(const BlockRowDesc& d, cudaStream_t s) {
-  const int NT = pick_nt(d.b_rows);
+template <typename T, int R, int BC>
+void launch_direct_bc(const BlockRowDesc& d, cudaStream_t s) {
+  const int NT = pick_nt_direct(d.b_rows);
   const int G = NT / d.b_rows;
   int64_t ngroups = (d.n_units + G - 1) / G;
   int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * 8);
   if (grid < 1) grid = 1;
-  blockrow_direct_kernel<T, R><<<(unsigned)grid, NT, 0, s>>>(d);
+  count_launch(); blockrow_direct_kernel<T, R, BC><<<(unsigned)grid, NT, 0, s>>>(d);
+}
+
+template <typename T, int R>
+void launch_direct(const BlockRowDesc& d, cudaStream_t s) {
+  switch (d.bc) {
+    case 3: launch_direct_bc<T, R, 3>(d, s); break;
+    case 4: launch_direct_bc<T, R, 4>(d, s); break;
+    case 9: launch_direct_bc<T, R, 9>(d, s); break;
+    case 16: launch_direct_bc<T, R, 16>(d, s); break;
+    case 20: launch_direct_bc<T, R, 20>(d, s); break;
+    case 27: launch_direct_bc<T, R, 27>(d, s); break;
+    case 45: launch_direct_bc<T, R, 45>(d, s); break;
+    default: launch_direct_bc<T, R, 0>(d, s); break;
+  }
 }
 
 template <typename T>
 void dispatch_R(const BlockRowDesc& d, int variant, cudaStream_t s) {
 #define HDG_BR_CASE(RR)                              \
   case RR:                                           \
-    if (variant == 0) launch_tma<T, RR>(d, s);       \
+    if (variant == 1) launch_tma<T, RR>(d, s);       \
     else launch_direct<T, RR>(d, s);                 \
     break;
   switch (d.R) {
@@ -269,6 +422,13 @@ void dispatch_R(const BlockRowDesc& d, int variant, cudaStream_t s) {
 }  // namespace
 
 int blockrow_variants() { return 2; }
+
+void to_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  count_launch(); to_f32_kernel<<<(unsigned)g, 256, 0, s>>>(x, y, n);
+}
 
 void blockrow(const BlockRowDesc& d, int variant, cudaStream_t s) {
   if (d.n_units <= 0) return;

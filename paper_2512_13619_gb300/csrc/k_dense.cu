@@ -4,7 +4,7 @@
 //
 // FP64 on this GPU runs on the CUDA-core FP64 pipes (about 1.2 TFLOP/s
 // measured), so both kernels are ALU-bound; they keep operands in shared
-// memory and each thread owns a 4x4 register tile.
+// memory and each thread owns a register tile sized to the product.
 #include "hdg_common.cuh"
 #include "hdg_internal.h"
 
@@ -12,9 +12,14 @@ namespace hdg {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 
+// Tile of (16*TM) x (16*TN) outputs per 256-thread CTA, each thread a TM x TN
+// register block; the tile shape is picked per product so that the 64-, 96-,
+// 135- or 162-wide operands of the condensation waste little work.
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int b0 = blockIdx.z / d.nb1, b1 = blockIdx.z % d.nb1;
@@ -23,51 +28,98 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
   double* C = d.C + b0 * d.sC0 + b1 * d.sC1;
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  double acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
   for (int k0 = 0; k0 < d.K; k0 += BK) {
-    // A tile: BM x BK, B tile: BK x BN (256 threads, 4 loads each)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      int idx = threadIdx.x + t * 256;
-      int r = idx / BK, c = idx % BK;
-      int gr = row0 + r, gc = k0 + c;
+    for (int t = 0; t < TM; ++t) {
+      const int idx = threadIdx.x + t * 256;
+      const int r = idx / BK, c = idx % BK;
+      const int gr = row0 + r, gc = k0 + c;
       As[c][r] = (gr < d.M && gc < d.K) ? A[(int64_t)gr * d.lda + gc] : 0.0;
-      int br = idx / BN, bcol = idx % BN;
-      int gbr = k0 + br, gbc = col0 + bcol;
+    }
+#pragma unroll
+    for (int t = 0; t < TN; ++t) {
+      const int idx = threadIdx.x + t * 256;
+      const int br = idx / BN, bcol = idx % BN;
+      const int gbr = k0 + br, gbc = col0 + bcol;
       Bs[br][bcol] = (gbr < d.K && gbc < d.N) ? B[(int64_t)gbr * d.ldb + gbc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], bv[4];
+      double a[TM], bv[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int gr = row0 + ty + 16 * i;
+  for (int i = 0; i < TM; ++i) {
+    const int gr = row0 + ty + 16 * i;
     if (gr >= d.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int gc = col0 + tx + 16 * j;
+    for (int j = 0; j < TN; ++j) {
+      const int gc = col0 + tx + 16 * j;
       if (gc >= d.N) continue;
-      int64_t cc = (int64_t)(gc / d.cg) * d.cgs + (gc % d.cg);
+      const int64_t cc = (int64_t)(gc / d.cg) * d.cgs + (gc % d.cg);
       double* p = C + (int64_t)gr * d.ldc + cc;
       *p = (d.beta == 0.0 ? 0.0 : d.beta * *p) + d.alpha * acc[i][j];
     }
+  }
+}
+
+// tile factor (2, 3, 4 or 6) that pads n least, preferring the larger tile on ties
+int pick_tile(int n) {
+  const int cand[4] = {6, 4, 3, 2};
+  int best = 2, bestpad = 1 << 30;
+  for (int t : cand) {
+    const int b = 16 * t;
+    const int pad = (n + b - 1) / b * b - n;
+    if (pad < bestpad) { bestpad = pad; best = t; }
+  }
+  return best;
+}
+
+template <int TM, int TN>
+void gemm_launch(const GemmDesc& d, cudaStream_t s) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
+  const int64_t nb = (int64_t)d.nb0 * d.nb1;
+  const int64_t zmax = 65535;
+  if (nb <= zmax) {
+    dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, (unsigned)nb);
+    count_launch(); gemm_f64_kernel<TM, TN><<<grid, 256, 0, s>>>(d);
+    return;
+  }
+  const int per = (int)(zmax / d.nb1);
+  for (int b0 = 0; b0 < d.nb0; b0 += per) {
+    GemmDesc e = d;
+    e.nb0 = (d.nb0 - b0 < per) ? d.nb0 - b0 : per;
+    e.A = d.A + b0 * d.sA0;
+    e.B = d.B + b0 * d.sB0;
+    e.C = d.C + b0 * d.sC0;
+    dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, (unsigned)((int64_t)e.nb0 * d.nb1));
+    count_launch(); gemm_f64_kernel<TM, TN><<<grid, 256, 0, s>>>(e);
+  }
+}
+
+template <int TM>
+void gemm_tn(const GemmDesc& d, int tn, cudaStream_t s) {
+  switch (tn) {
+    case 2: gemm_launch<TM, 2>(d, s); break;
+    case 3: gemm_launch<TM, 3>(d, s); break;
+    case 4: gemm_launch<TM, 4>(d, s); break;
+    default: gemm_launch<TM, 6>(d, s); break;
   }
 }
 
@@ -156,23 +208,12 @@ size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0 || d.nb0 <= 0 || d.nb1 <= 0) return;
-  int64_t nb = (int64_t)d.nb0 * d.nb1;
-  // grid.z is limited to 65535: split the outer batch if needed
-  const int64_t zmax = 65535;
-  if (nb <= zmax) {
-    dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, (unsigned)nb);
-    gemm_f64_kernel<<<grid, 256, 0, s>>>(d);
-    return;
-  }
-  int per = (int)(zmax / d.nb1);
-  for (int b0 = 0; b0 < d.nb0; b0 += per) {
-    GemmDesc e = d;
-    e.nb0 = (d.nb0 - b0 < per) ? d.nb0 - b0 : per;
-    e.A = d.A + b0 * d.sA0;
-    e.B = d.B + b0 * d.sB0;
-    e.C = d.C + b0 * d.sC0;
-    dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, (unsigned)((int64_t)e.nb0 * d.nb1));
-    gemm_f64_kernel<<<grid, 256, 0, s>>>(e);
+  const int tm = pick_tile(d.M), tn = pick_tile(d.N);
+  switch (tm) {
+    case 2: gemm_tn<2>(d, tn, s); break;
+    case 3: gemm_tn<3>(d, tn, s); break;
+    case 4: gemm_tn<4>(d, tn, s); break;
+    default: gemm_tn<6>(d, tn, s); break;
   }
 }
 
@@ -194,7 +235,7 @@ bool inverse_f64(double* A, int n, int64_t stride, int64_t count, unsigned* err,
   const int64_t gmax = 2147483647;
   for (int64_t c0 = 0; c0 < count; c0 += gmax) {
     int64_t c = count - c0 < gmax ? count - c0 : gmax;
-    inverse_kernel<<<(unsigned)c, kInvThreads, smem, s>>>(A + c0 * stride, n, stride, err);
+    count_launch(); inverse_kernel<<<(unsigned)c, kInvThreads, smem, s>>>(A + c0 * stride, n, stride, err);
   }
   return true;
 }

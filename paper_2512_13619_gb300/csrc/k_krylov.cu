@@ -198,6 +198,15 @@ __global__ void __launch_bounds__(kThreads) update_kernel(GmresView k, double* w
         }
       }
     }
+    if (finalize) {
+      __syncthreads();
+      if (threadIdx.x == 0 && k.hflag) {
+        int any = 0;
+        for (int r = 0; r < R; ++r) any |= k.running[r];
+        k.hflag[j] = any;
+        __threadfence_system();
+      }
+    }
     if (threadIdx.x == 0) *k.counter = 0;
   }
 }
@@ -582,43 +591,43 @@ int64_t gmres_chunk(int64_t len) {
 int gmres_blocks(int64_t len, int64_t chunk) { return (int)((len + chunk - 1) / chunk); }
 
 void launch_dots(const GmresView& k, const double* w, int i0, int i1, cudaStream_t s) {
-  dots_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, w, i0, i1);
+  count_launch(); dots_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, w, i0, i1);
 }
 void launch_update(const GmresView& k, double* w, int i0, int i1, int j, int hmode, int finalize, cudaStream_t s) {
-  update_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, w, i0, i1, j, hmode, finalize);
+  count_launch(); update_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, w, i0, i1, j, hmode, finalize);
 }
 void launch_norms(const GmresView& k, const double* v, double* out, int cycle, const double* denom, cudaStream_t s) {
-  norms_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, v, out, cycle, denom);
+  count_launch(); norms_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, v, out, cycle, denom);
 }
-void launch_backsolve(const GmresView& k, cudaStream_t s) { backsolve_kernel<<<1, 32, 0, s>>>(k); }
+void launch_backsolve(const GmresView& k, cudaStream_t s) { count_launch(); backsolve_kernel<<<1, 32, 0, s>>>(k); }
 void launch_xupdate(const GmresView& k, double* x, cudaStream_t s) {
-  xupdate_kernel<<<ew_grid(k.n * k.R), kThreads, 0, s>>>(k, x);
+  count_launch(); xupdate_kernel<<<ew_grid(k.n * k.R), kThreads, 0, s>>>(k, x);
 }
 void launch_axpby(double* y, const double* x, double a, double b, int64_t len, const int* running, int R,
                   cudaStream_t s) {
-  axpby_kernel<<<ew_grid(len), 256, 0, s>>>(y, x, a, b, len, running, R);
+  count_launch(); axpby_kernel<<<ew_grid(len), 256, 0, s>>>(y, x, a, b, len, running, R);
 }
 void launch_pp_real(double* w, double* q, const double* Aq, double inv_theta, int64_t len, int update_q,
                     const int* running, int R, int first, cudaStream_t s) {
-  pp_real_kernel<<<ew_grid(len), 256, 0, s>>>(w, q, Aq, inv_theta, len, update_q, running, R, first);
+  count_launch(); pp_real_kernel<<<ew_grid(len), 256, 0, s>>>(w, q, Aq, inv_theta, len, update_q, running, R, first);
 }
 void launch_pp_pair_t(double* t, double* w, const double* q, const double* Aq, double two_a, double inv_mod2,
                       int64_t len, const int* running, int R, int first, cudaStream_t s) {
-  pp_pair_t_kernel<<<ew_grid(len), 256, 0, s>>>(t, w, q, Aq, two_a, inv_mod2, len, running, R, first);
+  count_launch(); pp_pair_t_kernel<<<ew_grid(len), 256, 0, s>>>(t, w, q, Aq, two_a, inv_mod2, len, running, R, first);
 }
 void launch_pp_pair_q(double* q, const double* At, double inv_mod2, int64_t len, const int* running, int R,
                       cudaStream_t s) {
-  pp_pair_q_kernel<<<ew_grid(len), 256, 0, s>>>(q, At, inv_mod2, len, running, R);
+  count_launch(); pp_pair_q_kernel<<<ew_grid(len), 256, 0, s>>>(q, At, inv_mod2, len, running, R);
 }
 void launch_cheb(double* z, double* d, double* r, const double* Ad, double c1, double c2, int64_t len, int phase,
                  const int* running, int R, cudaStream_t s) {
-  cheb_kernel<<<ew_grid(len), 256, 0, s>>>(z, d, r, Ad, c1, c2, len, phase, running, R);
+  count_launch(); cheb_kernel<<<ew_grid(len), 256, 0, s>>>(z, d, r, Ad, c1, c2, len, phase, running, R);
 }
 void launch_ritz_leja(const double* H, int ldh, int P, int harmonic, double* re, double* im, int* nout,
                       unsigned* err, cudaStream_t s) {
   const size_t smem = sizeof(double) * 2 * kMaxPoly * kMaxPoly;
   cudaFuncSetAttribute(ritz_leja_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  ritz_leja_kernel<<<1, 1, smem, s>>>(H, ldh, P, harmonic, re, im, nout, err);
+  count_launch(); ritz_leja_kernel<<<1, 1, smem, s>>>(H, ldh, P, harmonic, re, im, nout, err);
 }
 
 }  // namespace hdg
