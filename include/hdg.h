@@ -242,6 +242,23 @@ hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n);
 hdg_status hdg_set_timing(hdg_problem p, int enable);
 hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches);
 
+/* y = K x with FP32 or BF16 blocks (prec = HDG_FP32 / HDG_BF16), like
+ * hdg_apply_K, but without allocating device memory.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc
+ * when they need the product (code inside a stream capture, hosts whose
+ * device memory belongs to their own pool allocator, latency-critical loops).
+ * The FP32 copy of x that the product needs goes to a static device array of
+ * 8,388,608 floats (32 MiB) that every GPU loading the library holds until
+ * the process exits; n_dof * R above that limit returns HDG_ERR_ARG, as does
+ * prec = HDG_FP64.  The problem must be assembled (HDG_ERR_STATE otherwise).
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other problems on the same device) race and must be ordered by the
+ * caller.  Nothing in the array needs to start at zero.  x, y: device,
+ * n_dof x R doubles. */
+hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double* y, void* stream);
+
 /* Number of CUDA kernels the library has launched in this process. */
 long long hdg_launch_count(void);
 

@@ -62,6 +62,7 @@ _SIGS = {
     'hdg_get_timing': (_I, [_V, _I, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     'hdg_set_kernel_variant': (_I, [_V, _I]),
     'hdg_launch_count': (ctypes.c_longlong, []),
+    'hdg_apply_K_noalloc': (_I, [_V, _I, _P, _P, _V]),
 }
 
 _lib = None
@@ -197,3 +198,7 @@ def hdg_set_kernel_variant(p, variant):
 
 def hdg_launch_count():
     return load().hdg_launch_count()
+
+
+def hdg_apply_K_noalloc(p, prec, x, y, stream=None):
+    return load().hdg_apply_K_noalloc(p, prec, ptr(x), ptr(y), stream_ptr(stream))

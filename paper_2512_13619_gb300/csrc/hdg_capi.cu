@@ -18,6 +18,7 @@
 using namespace hdg;
 
 #include <atomic>
+#include <mutex>
 namespace hdg {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -1446,6 +1447,85 @@ hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* la
 }
 
 long long hdg_launch_count(void) { return hdg::g_launches.load(); }
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Allocation-free matvec.  Some callers cannot call cudaMalloc at the point
+// where they need y = K x: code running while a stream is being captured into
+// a CUDA graph, hosts whose device memory is owned by their own pool
+// allocator and budget, and latency-critical loops where an allocation's
+// implicit synchronisation is not acceptable.  For them the FP32 copy of x
+// that the FP32/BF16 matvec needs lives in this file-scope device array
+// instead of the problem's workspace.  Every GPU that loads the library holds
+// the array until the process exits.  Host code must not use the array's name
+// as an address: its device address is looked up once per device with
+// cudaGetSymbolAddress (device code could name it directly).
+namespace {
+constexpr int64_t kNoAllocMaxEntries = 8ll * 1024 * 1024;   // n_dof * R <= 8,388,608 (32 MiB)
+static __device__ __align__(256) float g_noalloc_x32[kNoAllocMaxEntries];
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (which must be current).
+hdg_status noalloc_scratch(int dev, float** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return HDG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_x32);
+    if (e != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return HDG_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<float*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return HDG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double* y, void* stream) {
+  if (!p || !x || !y) return HDG_ERR_ARG;
+  if (prec != HDG_FP32 && prec != HDG_BF16) return HDG_ERR_ARG;
+  if (!p->assembled) return HDG_ERR_STATE;
+  if (prec == HDG_BF16 && !p->K16) return HDG_ERR_STATE;
+  if (p->ndof * p->R > kNoAllocMaxEntries) return HDG_ERR_ARG;   // larger than the static scratch
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    float* scratch = nullptr;
+    hdg_status st = noalloc_scratch(p->device, &scratch);
+    if (st != HDG_OK) return st;
+    // the conversion overwrites every entry the matvec reads: nothing to clear
+    to_f32(x, scratch, p->ndof * p->R, s);
+    BlockRowDesc d{};
+    d.prec = prec;
+    d.blk = prec == HDG_FP32 ? (const void*)p->K32 : (const void*)p->K16;
+    d.blk_stride = prec == HDG_FP32 ? p->s32 : p->s16;
+    d.rowptr = p->d_rowptr;
+    d.nbr = p->d_nbr;
+    d.cnt = p->d_cnt;
+    d.n_units = p->nfree;
+    d.b_rows = p->b;
+    d.bc = p->b;
+    d.max_slots = p->ms;
+    d.R = p->R;
+    d.in = x;
+    d.in32 = scratch;
+    d.out = y;
+    d.epi = EPI_STORE;
+    d.err = p->d_err;
+    blockrow(d, 0, s);   // the direct kernel: no occupancy queries, no attributes
+    CK(cudaGetLastError());
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
+}
 
 hdg_status hdg_set_kernel_variant(hdg_problem p, int variant) {
   if (!p || variant < 0 || variant >= blockrow_variants()) return HDG_ERR_ARG;
