@@ -43,6 +43,9 @@ def parse():
     ap.add_argument('--k', type=int, default=3)
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-cpu', action='store_true')
+    ap.add_argument('--profile', choices=['condense', 'matvec'], default=None,
+                    help='set up the workload and run only one hdg_condense call (condense) or one '
+                         'FP64 and one FP32 hdg_apply_K call (matvec), for profilers; prints no JSON')
     return ap.parse_args()
 
 
@@ -375,9 +378,39 @@ def run_reference(args, ws, rank):
             'e2e': {'value': round(ms, 1), 'unit': 'ms', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
 
 
+def run_profile(args):
+    """Minimal set-up for a profiler: the workload on cuda:0, then the
+    kernels under study once."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w = W.hex_poisson(n=args.n, k=args.k)
+    blk = w.blocks()
+    p = driver.Problem.from_workload(w, 0)
+    dblk = {k: torch.from_numpy(np.ascontiguousarray(blk[k])).cuda() for k in driver.BLOCK_NAMES}
+    p.condense(dblk, 0, on_device=True)
+    if args.profile == 'matvec':
+        o = driver.opts(pc='bj')
+        p.set_dirichlet(w.uhat_dirichlet())
+        p.assemble(o)
+        x = torch.randn(p.n_dof * w.R, dtype=torch.float64, device='cuda')
+        y = torch.empty_like(x)
+        for prec in (L.HDG_FP64, L.HDG_FP32):
+            driver.check(L.hdg_apply_K(p.h, prec, x, y), 'apply_K')
+    torch.cuda.synchronize()
+    p.close()
+    print('profile run done')
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == 'reference':
         out = run_reference(args, ws, rank)
     else:
