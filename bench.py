@@ -43,9 +43,10 @@ def parse():
     ap.add_argument('--k', type=int, default=3)
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-cpu', action='store_true')
-    ap.add_argument('--profile', choices=['condense', 'matvec'], default=None,
-                    help='set up the workload and run only one hdg_condense call (condense) or one '
-                         'FP64 and one FP32 hdg_apply_K call (matvec), for profilers; prints no JSON')
+    ap.add_argument('--no-graphs', action='store_true', help='launch GMRES iterations one by one')
+    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
+                    help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
+                         'one FP32 hdg_apply_K call (matvec) or one solve (solve-*), for profilers; no JSON')
     return ap.parse_args()
 
 
@@ -158,6 +159,8 @@ def run_ours(args, ws, rank, local):
     o_mixed = driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp32', inner_rtol=1e-4, max_iters=5000)
     o_fp64 = driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp64', max_iters=5000)
     p = driver.Problem.from_workload(w, local)
+    if args.no_graphs:
+        L.hdg_set_graphs(p.h, 0)
     u_dev = torch.empty((w.n_elem, w.M * w.PE, R), dtype=torch.float64, device=dev)
     q_dev = torch.empty((w.n_elem, w.M * w.D * w.PE, R), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -216,9 +219,30 @@ def run_ours(args, ws, rank, local):
     o_fp64_10 = driver.opts(restart=50, rtol=1e-10, pc='bj', inner='fp64', max_iters=5000)
     clk = Clocks(local)
     clk.start()
-    ms_fp64, ph_fp64, launches, tm_fp64 = timed(o_fp64, 'fp64', args.steps, timing=True)
-    ms_mixed, ph_mixed, launches_mixed, tm_mixed = timed(o_mixed, 'mixed', args.steps, timing=True)
+    ms_fp64, ph_fp64, launches, _ = timed(o_fp64, 'fp64', args.steps)
+    ms_mixed, ph_mixed, launches_mixed, _ = timed(o_mixed, 'mixed', args.steps)
     ms_fp64_10, _, _, _ = timed(o_fp64_10, 'fp64_1e-10', args.steps)
+
+    # block matvec alone: CUDA events around each launch on the launching stream,
+    # an L2 flush (a 256 MiB write) between launches, after 3 warm-up launches
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    xv = torch.randn(p.n_dof * R, dtype=torch.float64, device=dev)
+    yv = torch.empty_like(xv)
+    mv_ms = {}
+    for prec in (L.HDG_FP64, L.HDG_FP32):
+        for _ in range(3):
+            driver.check(L.hdg_apply_K(p.h, prec, xv, yv, st), 'apply_K')
+        tot = 0.0
+        nrep = max(10, args.steps * 4)
+        for _ in range(nrep):
+            flush.fill_(1.0)
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            driver.check(L.hdg_apply_K(p.h, prec, xv, yv, st), 'apply_K')
+            b_.record()
+            torch.cuda.synchronize(dev)
+            tot += a.elapsed_time(b_)
+        mv_ms[prec] = (tot / nrep, nrep)
     clocks = clk.stop()
 
     # condensation alone (the dominant kernels: batched FP64 GEMMs + inverses)
@@ -274,15 +298,17 @@ def run_ours(args, ws, rank, local):
     b = w.M * w.PF
     mv = {}
     for prec, name, sz in ((0, 'fp64', 8), (1, 'fp32', 4)):
-        tot = tm_mixed[prec][1] + tm_fp64[prec][1]
-        n = tm_mixed[prec][2] + tm_fp64[prec][2]
-        if n:
-            avg = tot / n
-            by = nnzb * b * b * sz + p.n_dof * R * (8 + 8)
-            gbs = by / avg / 1e6
-            mv[name] = {'avg_ms': round(avg, 5), 'launches': int(n), 'bytes_per_launch': int(by),
-                        'gbs': round(gbs, 1), 'frac_hbm': round(gbs / pk['hbm_gbs'], 3),
-                        'tflops': round(2 * nnzb * b * b * R / avg / 1e9, 3)}
+        avg, n = mv_ms[prec]
+        # FP64 blocks: K + x + y (FP64).  FP32 blocks: K + x (FP64, read by the
+        # conversion) + its FP32 copy (written, read) + y (FP64); both kernels
+        # of hdg_apply_K are inside the events
+        by = nnzb * b * b * sz + p.n_dof * R * (16 if prec == 0 else 24)
+        gbs = by / avg / 1e6
+        tf = 2 * nnzb * b * b * R / avg / 1e9
+        mv[name] = {'avg_ms': round(avg, 5), 'launches': int(n), 'bytes_per_launch': int(by),
+                    'gbs': round(gbs, 1), 'frac_hbm': round(gbs / pk['hbm_gbs'], 3), 'tflops': round(tf, 3),
+                    'frac_fp64_alu': round(tf / FP64_ALU_PEAK_TFLOPS, 3) if prec == 0 else None,
+                    'timing': 'CUDA events per launch, L2 flushed between launches'}
     achieved = cflops / ms_cond / 1e9
     roof = {'kernel': 'gemm_f64_kernel + inverse_kernel (batched static condensation, FP64)',
             'bound': 'alu', 'achieved': round(achieved, 4), 'peak': round(FP64_ALU_PEAK_TFLOPS, 4),
@@ -390,6 +416,8 @@ def run_profile(args):
     w = W.hex_poisson(n=args.n, k=args.k)
     blk = w.blocks()
     p = driver.Problem.from_workload(w, 0)
+    if args.no_graphs:
+        L.hdg_set_graphs(p.h, 0)
     dblk = {k: torch.from_numpy(np.ascontiguousarray(blk[k])).cuda() for k in driver.BLOCK_NAMES}
     p.condense(dblk, 0, on_device=True)
     if args.profile == 'matvec':
@@ -400,6 +428,16 @@ def run_profile(args):
         y = torch.empty_like(x)
         for prec in (L.HDG_FP64, L.HDG_FP32):
             driver.check(L.hdg_apply_K(p.h, prec, x, y), 'apply_K')
+    elif args.profile.startswith('solve'):
+        inner = 'fp32' if args.profile == 'solve-mixed' else 'fp64'
+        o = driver.opts(restart=50, rtol=1e-8, pc='bj', inner=inner, inner_rtol=1e-4, max_iters=5000)
+        p.set_dirichlet(w.uhat_dirichlet())
+        p.assemble(o)
+        p.setup_precond(o)
+        for _ in range(2):      # the first solve builds the cycle graphs
+            st, info = p.solve(o)
+            driver.check(st, 'solve')
+        print('iterations', info.iters, 'refinement', info.outer)
     torch.cuda.synchronize()
     p.close()
     print('profile run done')

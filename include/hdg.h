@@ -130,6 +130,10 @@ typedef struct {
 /* Human-readable name of a status. */
 const char* hdg_status_str(hdg_status s);
 
+/* Text of the last CUDA failure a library call met on this host thread
+ * (runtime error name and the failing call), "" if none. */
+const char* hdg_last_error(void);
+
 /* Create a problem on CUDA device `device` for `nrhs` right-hand sides.
  * Builds the face-row neighbour tables (free-face numbering, 2N_lfe-1 slots
  * per face row, Sec. 2.4) on the host and uploads them.  *out owns all device
@@ -258,6 +262,15 @@ hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* la
  * caller.  Nothing in the array needs to start at zero.  x, y: device,
  * n_dof x R doubles. */
 hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double* y, void* stream);
+
+/* GMRES cycles as CUDA graphs (default on): each cycle of hdg_solve is
+ * captured once per option set as m conditional (IF) nodes, one per
+ * iteration, and replayed; the device-side Givens step switches the
+ * remaining iterations off after convergence.  enable = 0 launches the
+ * iterations one by one instead (the host then polls a progress flag two
+ * iterations behind).  Event timing (hdg_set_timing) also uses the one-by-one
+ * launches.  Results are identical either way. */
+hdg_status hdg_set_graphs(hdg_problem p, int enable);
 
 /* Number of CUDA kernels the library has launched in this process. */
 long long hdg_launch_count(void);

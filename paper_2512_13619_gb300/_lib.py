@@ -63,6 +63,8 @@ _SIGS = {
     'hdg_set_kernel_variant': (_I, [_V, _I]),
     'hdg_launch_count': (ctypes.c_longlong, []),
     'hdg_apply_K_noalloc': (_I, [_V, _I, _P, _P, _V]),
+    'hdg_set_graphs': (_I, [_V, _I]),
+    'hdg_last_error': (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -202,3 +204,11 @@ def hdg_launch_count():
 
 def hdg_apply_K_noalloc(p, prec, x, y, stream=None):
     return load().hdg_apply_K_noalloc(p, prec, ptr(x), ptr(y), stream_ptr(stream))
+
+
+def hdg_set_graphs(p, enable):
+    return load().hdg_set_graphs(p, int(enable))
+
+
+def hdg_last_error():
+    return load().hdg_last_error().decode()

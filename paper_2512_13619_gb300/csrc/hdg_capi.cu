@@ -30,10 +30,21 @@ struct CudaError {
   cudaError_t e;
 };
 
+// last CUDA failure seen by a library call on this host thread
+thread_local char g_last_error[256] = "";
+
+void note_error(cudaError_t e, const char* what, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at %s:%d", cudaGetErrorString(e), cudaGetErrorName(e), what,
+           line);
+}
+
 #define CK(x)                                  \
   do {                                         \
     cudaError_t _e = (x);                      \
-    if (_e != cudaSuccess) throw CudaError{_e}; \
+    if (_e != cudaSuccess) {                   \
+      note_error(_e, #x, __LINE__);            \
+      throw CudaError{_e};                     \
+    }                                          \
   } while (0)
 
 template <typename T>
@@ -122,6 +133,18 @@ struct hdg_problem_s {
   double* h_dbl = nullptr;
   int* h_int = nullptr;
   unsigned* h_err = nullptr;
+
+  // captured GMRES cycles (CUDA graphs with one IF node per iteration)
+  struct CycleGraph {
+    unsigned long long key = 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphConditionalHandle> h;
+    long long kernels_per_iter = 0;
+  };
+  std::vector<CycleGraph> graphs;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
 
   // timing of block-matvec launches
   bool timing = false;
@@ -622,6 +645,11 @@ void ensure_workspace(hdg_problem p, int m) {
     CK(cudaMemset(p->counter, 0, sizeof(unsigned) * 4));
     CK(cudaMemset(p->d_x, 0, sizeof(double) * len));
   } else {
+    for (auto& cg : p->graphs) {
+      if (cg.exec) cudaGraphExecDestroy(cg.exec);
+      if (cg.g) cudaGraphDestroy(cg.g);
+    }
+    p->graphs.clear();
     p->dfree(p->V, 0);
     p->dfree(p->vscale, 0);
     p->dfree(p->H, 0);
@@ -708,6 +736,104 @@ void set_dbls(hdg_problem p, double* dptr, double v, int R, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
 }
 
+// Captured GMRES cycle: m IF nodes in sequence, node j's body is iteration j
+// (matvec, preconditioner, Gram-Schmidt, Givens).  The Givens step of
+// iteration j sets node j+1's condition to "some right-hand side still
+// running", so the iterations after convergence are skipped on the device.
+// Built once per (options, precisions) and replayed per cycle.
+struct IterLauncher {
+  hdg_problem p;
+  const hdg_solver_opts* o;
+  int kprec, mprec, kpoly, R;
+  void iteration(const GmresView& k, int j, cudaStream_t s) const {
+    Ops ops{p, s, R};
+    const int64_t len = p->ndof * R;
+    double* vj = p->V + (int64_t)j * len;
+    double* vn = p->V + (int64_t)(j + 1) * len;
+    ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running);
+    ops.Pinv(*o, mprec, kpoly, p->t1, vn, p->running);
+    orthogonalize(k, o->orth, j, s);
+  }
+};
+
+unsigned long long graph_key(const hdg_solver_opts& o, int kprec, int mprec, int kpoly, int variant) {
+  unsigned long long k = (unsigned long long)o.restart;
+  k = k * 4 + (unsigned)o.orth;
+  k = k * 4 + (unsigned)o.pc;
+  k = k * 4 + (unsigned)o.poly;
+  k = k * 64 + (unsigned)o.poly_degree;
+  k = k * 4 + (unsigned)kprec;
+  k = k * 4 + (unsigned)mprec;
+  k = k * 4 + (unsigned)kpoly;
+  k = k * 4 + (unsigned)variant;
+  return k + 1;
+}
+
+cudaGraphExec_t cycle_graph(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec, int kpoly,
+                            const GmresView& kin, long long* kernels_per_iter) {
+  const unsigned long long key = graph_key(o, kprec, mprec, kpoly, p->br_variant);
+  for (auto& cg : p->graphs)
+    if (cg.key == key) {
+      *kernels_per_iter = cg.kernels_per_iter;
+      return cg.exec;
+    }
+  if (!p->cap_stream) CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  hdg_problem_s::CycleGraph cg;
+  cg.key = key;
+  CK(cudaGraphCreate(&cg.g, 0));
+  // one handle per IF node: node 0 starts at 1, the others at 0 on every
+  // launch; iteration j's Givens step sets node j+1's handle, so a skipped
+  // node leaves all later ones switched off
+  cg.h.resize(o.restart);
+  for (int j = 0; j < o.restart; ++j)
+    CK(cudaGraphConditionalHandleCreate(&cg.h[j], cg.g, j == 0 ? 1 : 0, cudaGraphCondAssignDefault));
+  GmresView k = kin;
+  k.hflag = nullptr;
+  IterLauncher it{p, &o, kprec, mprec, kpoly, kin.R};
+  const bool timing = p->timing;
+  p->timing = false;  // no event records inside a graph
+  const long long n0 = hdg::g_launches.load();   // captured kernels are counted when they run
+  cudaGraphNode_t prev = nullptr;
+  for (int j = 0; j < o.restart; ++j) {
+    // all bytes of the tagged union past the used member must be zero
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cg.h[j];
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg.g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(p->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    k.use_cond = (j + 1 < o.restart) ? 1 : 0;
+    k.cond = (j + 1 < o.restart) ? cg.h[j + 1] : 0;
+    try {
+      it.iteration(k, j, p->cap_stream);
+      CK(cudaGetLastError());
+    } catch (...) {
+      cudaGraph_t dummy = nullptr;
+      cudaStreamEndCapture(p->cap_stream, &dummy);
+      cudaGetLastError();
+      p->timing = timing;
+      hdg::g_launches.store(n0);
+      cudaGraphDestroy(cg.g);
+      throw;
+    }
+    cudaGraph_t captured = nullptr;
+    CK(cudaStreamEndCapture(p->cap_stream, &captured));
+    prev = node;
+  }
+  p->timing = timing;
+  cg.kernels_per_iter = (hdg::g_launches.load() - n0) / std::max(o.restart, 1);
+  hdg::g_launches.store(n0);
+  CK(cudaGraphInstantiate(&cg.exec, cg.g, 0));
+  p->graphs.push_back(cg);
+  *kernels_per_iter = cg.kernels_per_iter;
+  return cg.exec;
+}
+
 struct GmresResult {
   int iters = 0, restarts = 0;
   bool converged = false;
@@ -790,7 +916,10 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
     // no right-hand side is still running (no empty launches after convergence).
     constexpr int kLag = 2;
     for (int j = 0; j <= m; ++j) p->h_flag[j] = 1;
-    for (int j = 0; j < m; ++j) {
+    const bool graph = p->use_graphs && !p->timing;
+    long long kpi = 0;
+    if (graph) CK(cudaGraphLaunch(cycle_graph(p, o, kprec, mprec, kpoly, k, &kpi), s));
+    for (int j = 0; j < m && !graph; ++j) {
       if (j >= kLag) {
         CK(cudaEventSynchronize(p->ev_iter[j - kLag]));
         if (!((volatile int*)p->h_flag)[j - kLag]) break;
@@ -807,6 +936,14 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
     // true residual with the FP64 matrix (outer) or the solve's own matrix (inner)
     ops.K(true_check ? HDG_FP64 : kprec, x, p->res, EPI_RESID, b, nullptr, nullptr);
     out.restarts += 1;
+    if (graph) {
+      // kernels the cycle graph ran: iterations done (max over RHS) x kernels per iteration
+      CK(cudaMemcpyAsync(p->h_int + 2 * kMaxR, p->jend, sizeof(int) * R, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int mx = 0;
+      for (int r = 0; r < R; ++r) mx = std::max(mx, p->h_int[2 * kMaxR + r]);
+      hdg::g_launches.fetch_add(kpi * mx);
+    }
   }
   out.iters = total_iters;
   return out;
@@ -925,6 +1062,11 @@ hdg_status hdg_problem_destroy(hdg_problem p) {
   p->allocs.clear();
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   for (auto e : p->ev_iter) cudaEventDestroy(e);
+  for (auto& cg : p->graphs) {
+    if (cg.exec) cudaGraphExecDestroy(cg.exec);
+    if (cg.g) cudaGraphDestroy(cg.g);
+  }
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->h_flag) cudaFreeHost(p->h_flag);
   if (p->h_dbl) cudaFreeHost(p->h_dbl);
   if (p->h_int) cudaFreeHost(p->h_int);
@@ -1525,6 +1667,14 @@ hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double*
   } catch (const CudaError& e) {
     return to_status(e);
   }
+}
+
+const char* hdg_last_error(void) { return g_last_error; }
+
+hdg_status hdg_set_graphs(hdg_problem p, int enable) {
+  if (!p) return HDG_ERR_ARG;
+  p->use_graphs = enable != 0;
+  return HDG_OK;
 }
 
 hdg_status hdg_set_kernel_variant(hdg_problem p, int variant) {

@@ -35,6 +35,8 @@ struct GmresView {
   int* iters;         // R
   int maxit;
   int* hflag;         // host-mapped: hflag[j] = 1 while any RHS is running after step j
+  int use_cond;       // inside a captured cycle: set `cond` after every Givens step
+  cudaGraphConditionalHandle cond;
   unsigned* counter;
   unsigned* err;
 };

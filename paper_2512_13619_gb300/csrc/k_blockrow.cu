@@ -20,6 +20,7 @@
 // FP32/BF16 blocks multiply an FP32 copy of x (converting each gathered FP64
 // value per product would run on the FP64 pipe, 1/57 of the FP32 rate here).
 #include <algorithm>
+#include <type_traits>
 #include "hdg_common.cuh"
 #include "hdg_internal.h"
 
@@ -292,6 +293,92 @@ __global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
   }
 }
 
+// FP32/BF16 blocks: each thread owns VR consecutive rows of a unit, so one
+// 16-byte load brings VR rows of a column (column-major blocks, rows
+// contiguous).  Requires b_rows % VR == 0; x comes from the FP32 copy.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  static constexpr int N = 4;
+  __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+};
+template <> struct Vec16<__nv_bfloat16> {
+  static constexpr int N = 8;
+  __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+};
+
+// Thread (unit, row group rg, slot part sp): rows rg*VR..rg*VR+VR-1, slots
+// sp, sp+SP, ...; the SP slot parts of a row group are adjacent lanes and
+// combine their sums with shuffles.  SP in {1, 2, 4}.
+template <typename T, int R, int BC, int SP>
+__global__ void __launch_bounds__(288) blockrow_vec_kernel(BlockRowDesc d, int G) {
+  constexpr int VR = Vec16<T>::N;
+  if (!any_active(d.active, R)) return;
+  const int tpu = (d.b_rows / VR) * SP;          // threads per unit; G units per CTA,
+                                                 // threads past G*tpu only join the shuffles
+  const int gu = threadIdx.x / tpu;
+  const int q = threadIdx.x - gu * tpu;
+  const int sp = q % SP, rg = q / SP;
+  const bool valid = gu < G;
+  const T* blk = static_cast<const T*>(d.blk);
+  const int64_t ngroups = (d.n_units + G - 1) / G;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int64_t u = grp * G + gu;
+    const bool act = valid && u < d.n_units;
+    float acc[VR][R];
+#pragma unroll
+    for (int v = 0; v < VR; ++v)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[v][r] = 0.f;
+    if (act) {
+      const int n = d.cnt[u];
+      const int64_t rp = d.rowptr[u];
+      const int32_t* nbr = d.nbr + u * d.max_slots;
+      for (int s = sp; s < n; s += SP) {
+        const float* xin = d.in32 + (int64_t)nbr[s] * BC * R;
+        const T* bs = blk + (rp + s) * d.blk_stride + rg * VR;
+#pragma unroll
+        for (int c = 0; c < BC; ++c) {
+          float kv[VR];
+          Vec16<T>::load(bs + (size_t)c * d.b_rows, kv);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float xv = __ldg(xin + c * R + r);
+#pragma unroll
+            for (int v = 0; v < VR; ++v) acc[v][r] = fmaf(kv[v], xv, acc[v][r]);
+          }
+        }
+      }
+    }
+    if (SP > 1) {
+#pragma unroll
+      for (int v = 0; v < VR; ++v)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+          for (int o = 1; o < SP; o <<= 1) acc[v][r] += __shfl_xor_sync(0xffffffffu, acc[v][r], o);
+        }
+    }
+    if (act && sp == 0) {
+#pragma unroll
+      for (int v = 0; v < VR; ++v)
+#pragma unroll
+        for (int r = 0; r < R; ++r) epi_store(d, u, rg * VR + v, r, (double)acc[v][r]);
+    }
+  }
+}
+
 __global__ void to_f32_kernel(const double* x, float* y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
@@ -378,8 +465,37 @@ int pick_nt_direct(int b_rows) {
   return best;
 }
 
+template <typename T, int R, int BC, int SP>
+void launch_vec_sp(const BlockRowDesc& d, cudaStream_t s) {
+  constexpr int VR = Vec16<T>::N;
+  const int tpu = (d.b_rows / VR) * SP;
+  const int G = std::max(1, 256 / tpu);
+  const int NT = (G * tpu + 31) / 32 * 32;        // whole warps for the full-mask shuffles
+  int64_t ngroups = (d.n_units + G - 1) / G;
+  int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * 16);
+  if (grid < 1) grid = 1;
+  count_launch(); blockrow_vec_kernel<T, R, BC, SP><<<(unsigned)grid, NT, 0, s>>>(d, G);
+}
+
+// slot parts: 4 for rows of several slots (matvec, ASM), 1 for one slot (BJ).
+// A shuffle group is SP adjacent lanes starting at a multiple of SP, so it
+// never straddles a warp.
+template <typename T, int R, int BC>
+void launch_vec(const BlockRowDesc& d, cudaStream_t s) {
+  constexpr int VR = Vec16<T>::N;
+  if (d.max_slots >= 4) launch_vec_sp<T, R, BC, 4>(d, s);
+  else if (d.max_slots >= 2) launch_vec_sp<T, R, BC, 2>(d, s);
+  else launch_vec_sp<T, R, BC, 1>(d, s);
+}
+
 template <typename T, int R, int BC>
 void launch_direct_bc(const BlockRowDesc& d, cudaStream_t s) {
+  if constexpr (!std::is_same<T, double>::value && BC > 0) {
+    if (d.b_rows % Vec16<T>::N == 0 && d.b_rows / Vec16<T>::N <= 64 && d.in32 != nullptr) {
+      launch_vec<T, R, BC>(d, s);
+      return;
+    }
+  }
   const int NT = pick_nt_direct(d.b_rows);
   const int G = NT / d.b_rows;
   int64_t ngroups = (d.n_units + G - 1) / G;

@@ -35,6 +35,53 @@ __device__ __forceinline__ double rhs_warp_sum(double v, int R) {
   return v;
 }
 
+// Deterministic block-wide sum of v[i*stride], i < n (every thread of the
+// block calls it; the result is returned in all threads).  A fixed tree of
+// per-thread strided sums, warp shuffles and one shared-memory level: on this
+// GPU a long serial chain of dependent FP64 adds costs tens of microseconds.
+__device__ double block_sum(const double* v, int n, int stride) {
+  __shared__ double ws[32];
+  __shared__ double total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[(int64_t)i * stride];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) ws[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Warp-wide deterministic sum of v[i*stride], i < n; result in all lanes.
+__device__ __forceinline__ double warp_strided_sum(const double* v, int n, int stride) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += v[(int64_t)i * stride];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__device__ __forceinline__ bool last_block_2d(unsigned* counter) {
+  __shared__ bool s_last2;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    s_last2 = (prev == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (s_last2) __threadfence();
+  return s_last2;
+}
+
 __device__ __forceinline__ bool last_block(unsigned* counter) {
   __shared__ bool s_last;
   __threadfence();
@@ -49,47 +96,74 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 }
 
 // --------------------------------------------------------------- dots
-// htmp[r][i] = vscale_i[r] * <V_i, w>_r  for i in [i0, i1)
-__global__ void __launch_bounds__(kThreads) dots_kernel(GmresView k, const double* w, int i0, int i1) {
+// htmp[r][i] = vscale_i[r] * <V_i, w>_r  for i in [i0, i1).
+// Grid: x = element chunks, y = groups of kGroup basis vectors.  Each thread
+// covers kDotsPerThread elements so the FP64 tree reduction (which costs as
+// much as the products on this GPU) is amortised.
+constexpr int kDotsThreads = 128;
+constexpr int kDotsPerThread = 32;
+// elements per block of the multi-dot: >= 32 per thread and <= 1024 blocks
+__host__ __device__ __forceinline__ int64_t dots_chunk(int64_t len) {
+  int64_t per = (len + 1023) / 1024;
+  per = ((per + kDotsThreads - 1) / kDotsThreads) * kDotsThreads;
+  const int64_t lo = (int64_t)kDotsThreads * kDotsPerThread;
+  return per < lo ? lo : per;
+}
+__global__ void __launch_bounds__(kDotsThreads) dots_kernel(GmresView k, const double* w, int i0, int i1) {
   if (!any_running(k.running, k.R)) return;
   const int R = k.R;
   const int64_t len = k.n * R;
-  const int64_t chunk = k.chunk;
+  const int64_t chunk = dots_chunk(len);
   const int64_t start = blockIdx.x * chunk;
   const int64_t stop = min(start + chunk, len);
-  __shared__ double red[kThreads / 32][kGroup][32];
+  __shared__ double red[kDotsThreads / 32][kGroup][32];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int ig = i0; ig < i1; ig += kGroup) {
-    const int ng = min(kGroup, i1 - ig);
-    double acc[kGroup];
+  const int ig = i0 + blockIdx.y * kGroup;
+  const int ng = min(kGroup, i1 - ig);
+  double acc[kGroup];
 #pragma unroll
-    for (int t = 0; t < kGroup; ++t) acc[t] = 0.0;
-    for (int64_t e = start + threadIdx.x; e < stop; e += kThreads) {
-      const double we = w[e];
+  for (int t = 0; t < kGroup; ++t) acc[t] = 0.0;
+  // four elements per step: 4 * (kGroup + 1) independent loads in flight
+  int64_t e = start + threadIdx.x;
+  for (; e + 3 * kDotsThreads < stop; e += 4 * kDotsThreads) {
+    double we[4], vv[4][kGroup];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) we[q] = w[e + q * kDotsThreads];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int t = 0; t < kGroup; ++t)
-        if (t < ng) acc[t] = fma(k.V[(int64_t)(ig + t) * len + e], we, acc[t]);
-    }
+        vv[q][t] = (t < ng) ? k.V[(int64_t)(ig + t) * len + e + q * kDotsThreads] : 0.0;
 #pragma unroll
-    for (int t = 0; t < kGroup; ++t) {
-      double v = rhs_warp_sum(acc[t], R);
-      if (lane < R) red[warp][t][lane] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < ng * R) {
-      const int t = threadIdx.x / R, r = threadIdx.x % R;
-      double s = 0.0;
-      for (int wv = 0; wv < kThreads / 32; ++wv) s += red[wv][t][r];
-      k.partial[((int64_t)(ig + t) * gridDim.x + blockIdx.x) * R + r] = s;
-    }
-    __syncthreads();
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int t = 0; t < kGroup; ++t)
+        if (t < ng) acc[t] = fma(vv[q][t], we[q], acc[t]);
   }
-  if (last_block(k.counter)) {
-    for (int idx = threadIdx.x; idx < (i1 - i0) * R; idx += kThreads) {
+  for (; e < stop; e += kDotsThreads) {
+    const double we1 = w[e];
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t)
+      if (t < ng) acc[t] = fma(k.V[(int64_t)(ig + t) * len + e], we1, acc[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < kGroup; ++t) {
+    double v = rhs_warp_sum(acc[t], R);
+    if (lane < R) red[warp][t][lane] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ng * R) {
+    const int t = threadIdx.x / R, r = threadIdx.x % R;
+    double sum = 0.0;
+    for (int wv = 0; wv < kDotsThreads / 32; ++wv) sum += red[wv][t][r];
+    k.partial[((int64_t)(ig + t) * gridDim.x + blockIdx.x) * R + r] = sum;
+  }
+  if (last_block_2d(k.counter)) {
+    // one warp per (vector, RHS): a fixed-order tree over the x-blocks
+    for (int idx = warp; idx < (i1 - i0) * R; idx += kDotsThreads / 32) {
       const int i = i0 + idx / R, r = idx % R;
-      double s = 0.0;
-      for (unsigned bb = 0; bb < gridDim.x; ++bb) s += k.partial[((int64_t)i * gridDim.x + bb) * R + r];
-      k.htmp[r * (k.m + 2) + i] = k.vscale[i * R + r] * s;
+      const double sum = warp_strided_sum(k.partial + ((int64_t)i * gridDim.x) * R + r, gridDim.x, R);
+      if (lane == 0) k.htmp[r * (k.m + 2) + i] = k.vscale[i * R + r] * sum;
     }
     if (threadIdx.x == 0) *k.counter = 0;
   }
@@ -113,9 +187,18 @@ __global__ void __launch_bounds__(kThreads) update_kernel(GmresView k, double* w
   const int64_t stop = min(start + k.chunk, len);
   double nrm = 0.0;
   for (int64_t e = start + threadIdx.x; e < stop; e += kThreads) {
-    const int r = (int)(e % R);
+    const int r = (int)e & (R - 1);   // R is a power of two
     double v = w[e];
-    for (int i = i0; i < i1; ++i) v = fma(-coef[(i - i0) * R + r], k.V[(int64_t)i * len + e], v);
+    int i = i0;
+    // eight independent loads in flight per step
+    for (; i + 8 <= i1; i += 8) {
+      double vv[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) vv[t] = k.V[(int64_t)(i + t) * len + e];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v = fma(-coef[(i + t - i0) * R + r], vv[t], v);
+    }
+    for (; i < i1; ++i) v = fma(-coef[(i - i0) * R + r], k.V[(int64_t)i * len + e], v);
     w[e] = v;
     nrm = fma(v, v, nrm);
   }
@@ -140,11 +223,17 @@ __global__ void __launch_bounds__(kThreads) update_kernel(GmresView k, double* w
       *hc = hmode ? *hc + h : h;
     }
     __syncthreads();
+    __shared__ double s_nrm[kMaxR];
+    if (finalize) {
+      for (int r = 0; r < R; ++r) {
+        const double t = block_sum(k.partial + r, gridDim.x, R);
+        if (threadIdx.x == 0) s_nrm[r] = t;
+      }
+      __syncthreads();
+    }
     if (finalize && threadIdx.x < R) {
       const int r = threadIdx.x;
-      double s = 0.0;
-      for (unsigned bb = 0; bb < gridDim.x; ++bb) s += k.partial[(int64_t)bb * R + r];
-      const double hn = sqrt(s);
+      const double hn = sqrt(s_nrm[r]);
       if (k.running[r] && finalize == 2) {
         // Arnoldi only (polynomial setup): store the column unrotated; stop on
         // breakdown h_{j+1,j} <= 1e-14 |h_{1,1}| or after m steps
@@ -200,11 +289,16 @@ __global__ void __launch_bounds__(kThreads) update_kernel(GmresView k, double* w
     }
     if (finalize) {
       __syncthreads();
-      if (threadIdx.x == 0 && k.hflag) {
+      if (threadIdx.x == 0) {
         int any = 0;
         for (int r = 0; r < R; ++r) any |= k.running[r];
-        k.hflag[j] = any;
-        __threadfence_system();
+        if (k.hflag) {
+          k.hflag[j] = any;
+          __threadfence_system();
+        }
+        // in a captured cycle the next iteration's IF node runs only while
+        // some right-hand side is still iterating
+        if (k.use_cond) cudaGraphSetConditional(k.cond, any ? 1u : 0u);
       }
     }
     if (threadIdx.x == 0) *k.counter = 0;
@@ -233,11 +327,15 @@ __global__ void __launch_bounds__(kThreads) norms_kernel(GmresView k, const doub
     k.partial[(int64_t)blockIdx.x * R + threadIdx.x] = t;
   }
   if (last_block(k.counter)) {
+    __shared__ double s_sq[kMaxR];
+    for (int r = 0; r < R; ++r) {
+      const double t = block_sum(k.partial + r, gridDim.x, R);
+      if (threadIdx.x == 0) s_sq[r] = t;
+    }
+    __syncthreads();
     if (threadIdx.x < R) {
       const int r = threadIdx.x;
-      double t = 0.0;
-      for (unsigned bb = 0; bb < gridDim.x; ++bb) t += k.partial[(int64_t)bb * R + r];
-      double nv = sqrt(t);
+      double nv = sqrt(s_sq[r]);
       if (!isfinite(nv)) atomicOr(k.err, ERRBIT_NAN);
       if (out) out[r] = denom ? (denom[r] > 0.0 ? nv / denom[r] : 0.0) : nv;
       if (cycle) {
@@ -258,20 +356,43 @@ __global__ void __launch_bounds__(kThreads) norms_kernel(GmresView k, const doub
 }
 
 // y = R^{-1} g for each RHS (R = rotated H, jend steps); ycoef_i = y_i vscale_i.
+// One warp per RHS: lane l keeps g_i for i = l, l+32, ...; each step divides
+// on the owner lane, broadcasts y_i and updates the earlier entries in
+// parallel (a serial FP64 chain of O(m^2) dependent operations is slow here).
 __global__ void backsolve_kernel(GmresView k) {
-  const int r = threadIdx.x;
+  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (r >= k.R) return;
   const int m = k.m, n = k.jend[r];
   const double* H = &k.H[(int64_t)r * (m + 1) * m];
   const double* g = &k.g[r * (m + 1)];
   double* y = &k.ycoef[r * (m + 1)];
-  for (int i = 0; i <= m; ++i) y[i] = 0.0;
-  for (int i = n - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int c = i + 1; c < n; ++c) s -= H[i * m + c] * y[c];
-    y[i] = (H[i * m + i] != 0.0) ? s / H[i * m + i] : 0.0;
+  double gl[kMaxBasis / 32];
+#pragma unroll
+  for (int q = 0; q < kMaxBasis / 32; ++q) {
+    const int i = lane + 32 * q;
+    gl[q] = (i < n) ? g[i] : 0.0;
   }
-  for (int i = 0; i < n; ++i) y[i] *= k.vscale[i * k.R + r];
+  for (int i = lane; i <= m; i += 32) y[i] = 0.0;
+  __syncwarp();
+  for (int i = n - 1; i >= 0; --i) {
+    const int owner = i & 31, slot = i >> 5;
+    double yi = 0.0;
+    if (lane == owner) {
+      double gi = 0.0;
+#pragma unroll
+      for (int q = 0; q < kMaxBasis / 32; ++q)
+        if (q == slot) gi = gl[q];
+      const double d = H[i * m + i];
+      yi = (d != 0.0) ? gi / d : 0.0;
+    }
+    yi = __shfl_sync(0xffffffffu, yi, owner);
+#pragma unroll
+    for (int q = 0; q < kMaxBasis / 32; ++q) {
+      const int kk = lane + 32 * q;
+      if (kk < i) gl[q] = fma(-H[kk * m + i], yi, gl[q]);
+    }
+    if (lane == 0) y[i] = yi * k.vscale[i * k.R + r];
+  }
 }
 
 // x += sum_i ycoef[r][i] V_i  (i < jend[r])
@@ -292,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) xupdate_kernel(GmresView k, double* 
   __syncthreads();
   const int n = s_n;
   for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < len; e += (int64_t)gridDim.x * kThreads) {
-    const int r = (int)(e % R);
+    const int r = (int)e & (R - 1);
     double v = x[e];
     for (int i = 0; i < n; ++i) v = fma(coef[i * R + r], k.V[(int64_t)i * len + e], v);
     x[e] = v;
@@ -582,16 +703,20 @@ inline unsigned ew_grid(int64_t len) {
 }  // namespace
 
 int64_t gmres_chunk(int64_t len) {
-  // contiguous element range per block: a multiple of kThreads, ~1024 blocks max
+  // contiguous element range per block of the update / norm kernels: at
+  // least 4 elements per thread (the FP64 reduction is amortised), a multiple
+  // of kThreads, at most 1024 blocks
   int64_t per = (len + 1023) / 1024;
-  per = ((per + kThreads * 4 - 1) / (kThreads * 4)) * (kThreads * 4);
-  if (per < kThreads * 4) per = kThreads * 4;
+  per = ((per + kThreads - 1) / kThreads) * kThreads;
+  if (per < 4 * kThreads) per = 4 * kThreads;
   return per;
 }
 int gmres_blocks(int64_t len, int64_t chunk) { return (int)((len + chunk - 1) / chunk); }
 
 void launch_dots(const GmresView& k, const double* w, int i0, int i1, cudaStream_t s) {
-  count_launch(); dots_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, w, i0, i1);
+  if (i1 <= i0) return;
+  dim3 grid(gmres_blocks(k.n * k.R, dots_chunk(k.n * k.R)), (i1 - i0 + kGroup - 1) / kGroup);
+  count_launch(); dots_kernel<<<grid, kDotsThreads, 0, s>>>(k, w, i0, i1);
 }
 void launch_update(const GmresView& k, double* w, int i0, int i1, int j, int hmode, int finalize, cudaStream_t s) {
   count_launch(); update_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, w, i0, i1, j, hmode, finalize);
@@ -599,7 +724,7 @@ void launch_update(const GmresView& k, double* w, int i0, int i1, int j, int hmo
 void launch_norms(const GmresView& k, const double* v, double* out, int cycle, const double* denom, cudaStream_t s) {
   count_launch(); norms_kernel<<<gmres_blocks(k.n * k.R, k.chunk), kThreads, 0, s>>>(k, v, out, cycle, denom);
 }
-void launch_backsolve(const GmresView& k, cudaStream_t s) { count_launch(); backsolve_kernel<<<1, 32, 0, s>>>(k); }
+void launch_backsolve(const GmresView& k, cudaStream_t s) { count_launch(); backsolve_kernel<<<1, 32 * k.R, 0, s>>>(k); }
 void launch_xupdate(const GmresView& k, double* x, cudaStream_t s) {
   count_launch(); xupdate_kernel<<<ew_grid(k.n * k.R), kThreads, 0, s>>>(k, x);
 }

@@ -14,7 +14,10 @@ _ORTH = {'cgs': L.HDG_ORTH_CGS, 'mgs': L.HDG_ORTH_MGS, 'cgs2': L.HDG_ORTH_CGS2}
 
 class HdgError(RuntimeError):
     def __init__(self, status, what=''):
-        super().__init__('%s: %s' % (what, L.hdg_status_str(status)))
+        msg = '%s: %s' % (what, L.hdg_status_str(status))
+        if status == L.HDG_ERR_CUDA:
+            msg += ' [%s]' % L.hdg_last_error()
+        super().__init__(msg)
         self.status = status
 
 

@@ -252,3 +252,26 @@ def test_mixed_precision_reaches_1e8(pc, poly, deg):
         assert np.linalg.norm(b - s.K @ x[:, r]) / np.linalg.norm(b) <= 1e-8
         assert np.linalg.norm(x[:, r] - xd[:, r]) / np.linalg.norm(xd[:, r]) <= cond * 1e-8
     p.close()
+
+
+@pytest.mark.parametrize('inner', ['fp64', 'fp32'])
+def test_graph_cycles_equal_launch_by_launch(inner):
+    """GMRES cycles replayed as CUDA graphs (conditional IF node per
+    iteration) give bit-identical results to iteration-by-iteration launches
+    (the reductions are deterministic)."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w = W.hex_elasticity(n=2, k=1, R=2)
+    o = driver.opts(restart=12, rtol=1e-9, pc='bj', inner=inner, max_iters=3000)
+    sols = []
+    for graphs in (1, 0, 1):
+        p = _problem(w)
+        p.assemble(o)
+        p.setup_precond(o)
+        assert L.hdg_set_graphs(p.h, graphs) == 0
+        st, info = p.solve(o)
+        assert st == 0
+        sols.append((p.free_trace(), info.iters))
+        p.close()
+    assert np.array_equal(sols[0][0], sols[1][0]) and sols[0][1] == sols[1][1]
+    assert np.array_equal(sols[0][0], sols[2][0])
