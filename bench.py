@@ -44,6 +44,10 @@ def parse():
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-graphs', action='store_true', help='launch GMRES iterations one by one')
+    ap.add_argument('--serving-requests', type=int, default=512,
+                    help='requests of the serving stream timed beside the step (0: none)')
+    ap.add_argument('--lanes', type=int, default=4, help='concurrent requests of the serving loop')
+    ap.add_argument('--serving-budget-gb', type=float, default=64.0)
     ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
                     help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
                          'one FP32 hdg_apply_K call (matvec) or one solve (solve-*), for profilers; no JSON')
@@ -337,13 +341,68 @@ def run_ours(args, ws, rank, local):
     }
     if e2e:
         out['e2e'] = e2e
+    p.close()
+    if args.serving_requests > 0:
+        out['serving'] = serving_leg(args, local)
     if rank == 0 and not args.no_cpu:
         out['cpu_baseline'] = cpu_baseline(args, w, blk)
-    p.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def serving_leg(args, local):
+    """The serving stream: HDG convection-diffusion requests (kappa
+    log-uniform in [1e-3, 1], seeded unit velocity, n^3 hex meshes with n in
+    8..24 and Q1..Q3) arriving as a seeded Poisson process at 0.8x the
+    capacity measured on a burst of the first requests; FP32 blocks with FP64
+    refinement, BJ-GMRES(30) to 1e-8 in CUDA graphs, `lanes` requests in
+    flight on their own streams, admission by a device-memory budget.  The
+    meshes of the 51 shapes are generated before the stream starts (a request
+    names a mesh the server holds); the element blocks of each request are
+    computed from its kappa and velocity inside its latency."""
+    import numpy as np
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver
+    from paper_2512_13619_gb300.serving import HdgBackend, Server
+    o = driver.opts(restart=30, rtol=1e-8, pc='bj', inner='fp32', inner_rtol=1e-4, max_iters=20000)
+
+    def inputs(shape, req):
+        n, k = shape
+        kappa, beta = (1.0, (1.0, 0.0, 0.0)) if req is None else (req['kappa'], req['beta'])
+        return W.structured_convdiff_inputs(n, k, kappa, beta)
+
+    reqs = W.serving_requests(args.serving_requests)
+    for r in reqs:
+        r['shape'] = (r['n'], r['k'])
+    be = HdgBackend(inputs, o, device=local)
+    t0 = time.perf_counter()
+    for sh in sorted({r['shape'] for r in reqs}):
+        be.slot_bytes(sh)                              # generates and caches the mesh
+    t_mesh = time.perf_counter() - t0
+    budget = int(args.serving_budget_gb * (1 << 30))
+    srv = Server(be, lanes=args.lanes, mem_budget=budget)
+    ncal = min(32, len(reqs))
+    cal = [dict(r, id=('cal', r['id'])) for r in reqs[:ncal]]
+    st_cal = srv.run(cal, np.zeros(ncal))              # burst: capacity (and first slots)
+    rate = 0.8 * st_cal['solves_per_s']
+    arr = W.poisson_arrivals(len(reqs), rate)
+    st = srv.run(reqs, arr)
+    res = [srv.results[r['id']] for r in reqs if r['id'] in srv.results]
+    srv.close()
+    its = np.array([x['iters'] for x in res]) if res else np.zeros(1)
+    rel = max([x['rel'] for x in res] + [0.0])
+    return {
+        'requests': len(reqs), 'completed': st['completed'], 'errors': st['errors'], 'lanes': args.lanes,
+        'arrival_rate_per_s': round(rate, 2), 'capacity_burst_solves_per_s': round(st_cal['solves_per_s'], 2),
+        'p50_ms': round(st['p50_ms'], 3), 'p99_ms': round(st['p99_ms'], 3), 'mean_ms': round(st['mean_ms'], 3),
+        'solves_per_s': round(st['solves_per_s'], 2), 'slot_creations': st['slot_creations'] + st_cal['slot_creations'],
+        'evictions': st['evictions'] + st_cal['evictions'], 'max_in_flight': st['max_in_flight'],
+        'budget_gb': args.serving_budget_gb, 'gmres_iters_mean': float(its.mean()), 'gmres_iters_max': int(its.max()),
+        'max_rel_resid': rel, 'mesh_generation_s': round(t_mesh, 2),
+        'solve': 'FP32 blocks + FP64 refinement, BJ-GMRES(30) to 1e-8, CUDA graphs',
+        'latency': 'arrival to trace in host memory (includes element-block generation on the host)'}
 
 
 def oracle_step(w, blk):

@@ -193,3 +193,37 @@ def poisson_arrivals(n, rate, seed=41):
     """Arrival times (s) of a Poisson process with the given rate (1/s)."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+# --------------------------------------------------------------- serving inputs
+_STRUCT_CACHE = {}
+
+
+def structured_convdiff_inputs(n, k, kappa, beta, R=1):
+    """Inputs of one convection-diffusion request (f = 1, homogeneous
+    Dirichlet) on the structured n^3 mesh: the mesh arrays and ONE element's
+    blocks, valid for every element (all elements are the same cube and every
+    face is parametrised the same way from both sides, which is checked), with
+    element strides 0 for hdg_condense_strided."""
+    key = (n, k)
+    if key not in _STRUCT_CACHE:
+        m = meshmod.hex_mesh(n)
+        ref = blk.reference_element(m, k)
+        perm = blk.face_permutations(m, ref)
+        assert np.all(perm == np.arange(ref.PF)), "face permutations differ between elements"
+        mats = blk.element_matrices(m, ref, perm, np.array([0]))
+        fd = m.face_boundary.astype(np.uint8)
+        mesh = dict(dim=3, n_lfe=6, M=1, PE=ref.PE, PF=ref.PF, elem_face=m.elem_face,
+                    face_elem=m.face_elem, face_dirichlet=fd)
+        _STRUCT_CACHE[key] = (mesh, ref, mats)
+    mesh, ref, mats = _STRUCT_CACHE[key]
+    beta = np.asarray(beta, float)
+    phys = blk.cdr(3, 1, beta, kappa, np.zeros((1, 1)), np.linalg.norm(beta) + kappa)
+    out = blk.hdg_blocks(mats, phys)
+    one = lambda x: np.ones(x.shape[:-1] + (1,))
+    ru = blk.load_vector_from_function(mats, ref, one, 1)[:, :, None]
+    out['ru'] = np.ascontiguousarray(np.repeat(ru, R, axis=2))
+    out['ruh'] = np.zeros((1, 6 * ref.PF, R))
+    strides = [0] * 11
+    uD = np.zeros((len(mesh['face_dirichlet']), ref.PF, R))
+    return mesh, {k2: np.ascontiguousarray(v) for k2, v in out.items()}, strides, uD

@@ -175,6 +175,17 @@ hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count,
                         const double* G, const double* H, const double* J,
                         const double* ru, const double* ruh, int on_device, void* stream);
 
+/* hdg_condense with per-input element strides.  blocks[11] are the inputs in
+ * the order Me, Bd, Cd, D, E, F, G, H, J, ru, ruh; elem_stride[i] (doubles)
+ * is either the input's size per element (one block per element, as in
+ * hdg_condense) or 0: one block shared by all `count` elements (identical
+ * elements of a structured mesh with constant coefficients).  A shared M^e is
+ * inverted once; when all eleven inputs are shared, one element is condensed
+ * and its results are copied to the others.  elem_stride may be NULL (all
+ * per element).  Errors as hdg_condense; HDG_ERR_ARG for any other stride. */
+hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const double* const* blocks,
+                                const int64_t* elem_stride, int on_device, void* stream);
+
 /* Dirichlet trace values u_D (b_hat = uhat - u_D on Dirichlet faces, Sec.
  * 2.1): host or device, n_face x b x R; rows of free faces are ignored.
  * Defaults to zero.  Must be set before hdg_assemble. */

@@ -47,6 +47,7 @@ _SIGS = {
     'hdg_problem_device_bytes': (ctypes.c_size_t, [_V]),
     'hdg_workspace_bytes': (ctypes.c_size_t, [ctypes.POINTER(hdg_mesh), _I, ctypes.POINTER(hdg_solver_opts)]),
     'hdg_condense': (_I, [_V, _I64, _I64] + [_P] * 11 + [_I, _V]),
+    'hdg_condense_strided': (_I, [_V, _I64, _I64, ctypes.POINTER(_P), ctypes.POINTER(_I64), _I, _V]),
     'hdg_set_dirichlet': (_I, [_V, _P, _I, _V]),
     'hdg_assemble': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _V]),
     'hdg_setup_precond': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _P, _V]),
@@ -135,6 +136,12 @@ def hdg_workspace_bytes(mesh, nrhs, opts):
 def hdg_condense(p, e0, count, Me, Bd, Cd, D, E, F, G, H, J, ru, ruh, on_device, stream=None):
     return load().hdg_condense(p, e0, count, *[ptr(a) for a in (Me, Bd, Cd, D, E, F, G, H, J, ru, ruh)],
                                int(on_device), stream_ptr(stream))
+
+
+def hdg_condense_strided(p, e0, count, blocks, elem_stride, on_device, stream=None):
+    arr = (_P * 11)(*[ptr(a) for a in blocks])
+    st = (_I64 * 11)(*[int(x) for x in elem_stride]) if elem_stride is not None else None
+    return load().hdg_condense_strided(p, e0, count, arr, st, int(on_device), stream_ptr(stream))
 
 
 def hdg_set_dirichlet(p, uhat_dirichlet, on_device, stream=None):

@@ -114,6 +114,10 @@ struct hdg_problem_s {
   double* d_poly = nullptr;
   double cheb_a = 0.0, cheb_b = 0.0;
 
+  // buffers reused across calls (no per-call cudaMalloc / cudaFree, which
+  // would synchronise the device and serialise concurrent problems)
+  double *d_full = nullptr, *d_uout = nullptr, *d_qout = nullptr, *d_bjtmp = nullptr, *d_asmP = nullptr;
+
   // solve workspace
   double* d_x = nullptr;
   int ws_m = -1;
@@ -378,10 +382,19 @@ GemmDesc gd(int M, int N, int K, const double* A, int64_t lda, int64_t sA0, int6
   return d;
 }
 
-// Condense elements [e0, e0+ec) whose inputs are device arrays laid out as in hdg.h.
+// Copy the inputs E, F, H, J or r_uh into the per-element work arrays: one
+// contiguous copy, or `count` copies of a block shared by all elements.
+void copy_in(double* dst, const double* src, int64_t per, int64_t count, bool shared, cudaStream_t s) {
+  if (shared) bcast_copy(dst, src, per, count, s);
+  else CK(cudaMemcpyAsync(dst, src, sizeof(double) * per * count, cudaMemcpyDeviceToDevice, s));
+}
+
+// Condense elements [e0, e0+ec) whose inputs are device arrays laid out as in
+// hdg.h.  sh[i] = true when input i is one block shared by every element
+// (batch stride 0 in the products).
 void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, const double* Bd, const double* Cd,
                     const double* Dm, const double* Em, const double* Fm, const double* Gm, const double* Hm,
-                    const double* Jm, const double* ru, const double* ruh, cudaStream_t s) {
+                    const double* Jm, const double* ru, const double* ruh, const bool* sh, cudaStream_t s) {
   const int PE = p->PE, D = p->D, M = p->M, PF = p->PF, MPE = p->MPE, MDPE = p->MDPE, nlb = p->nlb,
             nlPF = p->nlPF, R = p->R;
   const int n = (int)ec;
@@ -395,42 +408,45 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
   double* Xr = p->d_Xr + e0 * MPE * R;
   double* Kb = p->d_Kbar + e0 * nlb * nlb;
   double* rb = p->d_rbar + e0 * nlb * R;
-  // (M^e)^{-1}                                                   (Eq. w16)
-  CK(cudaMemcpyAsync(Minv, Me, sizeof(double) * ec * PE * PE, cudaMemcpyDeviceToDevice, s));
-  inverse_f64(Minv, PE, (int64_t)PE * PE, ec, p->d_err, s);
+  // batch strides of the inputs (0 = one block shared by every element)
+  const int64_t sMe = sh[0] ? 0 : (int64_t)PE * PE, sBd = sh[1] ? 0 : (int64_t)D * PE * PE,
+                sCd = sh[2] ? 0 : (int64_t)D * PE * nlPF, sD = sh[3] ? 0 : (int64_t)MPE * MDPE,
+                sG = sh[6] ? 0 : (int64_t)nlb * MDPE, sru = sh[9] ? 0 : (int64_t)MPE * R;
+  // (M^e)^{-1}  (Eq. w16); a shared mass matrix is inverted once
+  const int64_t nM = sh[0] ? 1 : ec;
+  CK(cudaMemcpyAsync(Minv, Me, sizeof(double) * nM * PE * PE, cudaMemcpyDeviceToDevice, s));
+  inverse_f64(Minv, PE, (int64_t)PE * PE, nM, p->d_err, s);
   // (M^e)^{-1} B_d, (M^e)^{-1} C_d
-  gemm_f64(gd(PE, PE, PE, Minv, PE, PE * PE, 0, Bd, PE, (int64_t)D * PE * PE, PE * PE, MinvB, PE,
-              (int64_t)D * PE * PE, PE * PE, 1.0, 0.0, n, D), s);
-  gemm_f64(gd(PE, nlPF, PE, Minv, PE, PE * PE, 0, Cd, nlPF, (int64_t)D * PE * nlPF, (int64_t)PE * nlPF, MinvC, nlPF,
+  gemm_f64(gd(PE, PE, PE, Minv, PE, sMe, 0, Bd, PE, sBd, PE * PE, MinvB, PE, (int64_t)D * PE * PE, PE * PE, 1.0, 0.0,
+              n, D), s);
+  gemm_f64(gd(PE, nlPF, PE, Minv, PE, sMe, 0, Cd, nlPF, sCd, (int64_t)PE * nlPF, MinvC, nlPF,
               (int64_t)D * PE * nlPF, (int64_t)PE * nlPF, 1.0, 0.0, n, D), s);
   // Ebar = E - D A^{-1} B, per component block b: D[:, (b,.,.)] * stack_d (M^e)^{-1}B_d   (Eq. w19)
-  CK(cudaMemcpyAsync(Eb, Em, sizeof(double) * ec * MPE * MPE, cudaMemcpyDeviceToDevice, s));
-  gemm_f64(gd(MPE, PE, D * PE, Dm, MDPE, (int64_t)MPE * MDPE, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0,
-              Eb, MPE, (int64_t)MPE * MPE, PE, -1.0, 1.0, n, M), s);
+  copy_in(Eb, Em, (int64_t)MPE * MPE, ec, sh[4], s);
+  gemm_f64(gd(MPE, PE, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Eb, MPE,
+              (int64_t)MPE * MPE, PE, -1.0, 1.0, n, M), s);
   // Fbar = F - D A^{-1} C, output columns (l, b, j)
-  CK(cudaMemcpyAsync(Fb, Fm, sizeof(double) * ec * MPE * nlb, cudaMemcpyDeviceToDevice, s));
-  gemm_f64(gd(MPE, nlPF, D * PE, Dm, MDPE, (int64_t)MPE * MDPE, (int64_t)D * PE, MinvC, nlPF,
-              (int64_t)D * PE * nlPF, 0, Fb, nlb, (int64_t)MPE * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF),
-           s);
+  copy_in(Fb, Fm, (int64_t)MPE * nlb, ec, sh[5], s);
+  gemm_f64(gd(MPE, nlPF, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Fb, nlb,
+              (int64_t)MPE * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
   // Hbar = H - G A^{-1} B                                       (Eq. w21)
-  CK(cudaMemcpyAsync(Hb, Hm, sizeof(double) * ec * nlb * MPE, cudaMemcpyDeviceToDevice, s));
-  gemm_f64(gd(nlb, PE, D * PE, Gm, MDPE, (int64_t)nlb * MDPE, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0,
-              Hb, MPE, (int64_t)nlb * MPE, PE, -1.0, 1.0, n, M), s);
+  copy_in(Hb, Hm, (int64_t)nlb * MPE, ec, sh[7], s);
+  gemm_f64(gd(nlb, PE, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Hb, MPE,
+              (int64_t)nlb * MPE, PE, -1.0, 1.0, n, M), s);
   // Jbar = J - G A^{-1} C  (written into Kbar)
-  CK(cudaMemcpyAsync(Kb, Jm, sizeof(double) * ec * nlb * nlb, cudaMemcpyDeviceToDevice, s));
-  gemm_f64(gd(nlb, nlPF, D * PE, Gm, MDPE, (int64_t)nlb * MDPE, (int64_t)D * PE, MinvC, nlPF,
-              (int64_t)D * PE * nlPF, 0, Kb, nlb, (int64_t)nlb * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF),
-           s);
+  copy_in(Kb, Jm, (int64_t)nlb * nlb, ec, sh[8], s);
+  gemm_f64(gd(nlb, nlPF, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Kb, nlb,
+              (int64_t)nlb * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
   // Ebar^{-1}; X_F = Ebar^{-1} Fbar; X_r = Ebar^{-1} r_u
   inverse_f64(Eb, MPE, (int64_t)MPE * MPE, ec, p->d_err, s);
   gemm_f64(gd(MPE, nlb, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlb, (int64_t)MPE * nlb, 0, XF, nlb,
               (int64_t)MPE * nlb, 0, 1.0, 0.0, n, 1), s);
-  gemm_f64(gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, (int64_t)MPE * R, 0, Xr, R, (int64_t)MPE * R, 0, 1.0,
-              0.0, n, 1), s);
+  gemm_f64(gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, sru, 0, Xr, R, (int64_t)MPE * R, 0, 1.0, 0.0, n, 1),
+           s);
   // Kbar = Jbar - Hbar X_F ; rbar = r_uh - Hbar X_r              (Eq. w22)
   gemm_f64(gd(nlb, nlb, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, XF, nlb, (int64_t)MPE * nlb, 0, Kb, nlb,
               (int64_t)nlb * nlb, 0, -1.0, 1.0, n, 1), s);
-  CK(cudaMemcpyAsync(rb, ruh, sizeof(double) * ec * nlb * R, cudaMemcpyDeviceToDevice, s));
+  copy_in(rb, ruh, (int64_t)nlb * R, ec, sh[10], s);
   gemm_f64(gd(nlb, R, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, Xr, R, (int64_t)MPE * R, 0, rb, R, (int64_t)nlb * R, 0,
               -1.0, 1.0, n, 1), s);
 }
@@ -1088,7 +1104,14 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
   int64_t by = 0;
   by += NE * (nlb * nlb + nlb * R + D * PE * PE + D * PE * nl * mesh->PF + MPE * nlb + MPE * R) * 8;
   by += NF * b * R * 8;
-  by += (int64_t)(1ll << 30) + (1ll << 28);                     // staging + temporaries (upper bound)
+  {  // condensation staging + temporaries, sized as hdg_problem_create sizes them
+    const int64_t MDPE = MPE * D, nlPF = nl * mesh->PF;
+    const int64_t in_total = PE * PE + D * PE * PE + D * PE * nlPF + MPE * MDPE + MPE * MPE + MPE * nlb +
+                             nlb * MDPE + nlb * MPE + nlb * nlb + MPE * R + nlb * R;
+    const int64_t tmp = PE * PE + MPE * MPE + MPE * nlb + nlb * MPE;
+    const int64_t ch = std::max<int64_t>(1, std::min<int64_t>((1ll << 30) / ((in_total + tmp) * 8), NE));
+    by += ch * (in_total + tmp) * 8 + (16ll << 20);               // + small per-call buffers
+  }
   by += nfree * ms * b * b * (8 + 4);                             // K in FP64 + FP32
   if (opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16)) by += nfree * ms * b * b * 2;
   by += nfree * b * b * (8 + 4 + 8);                              // BJ
@@ -1099,36 +1122,62 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
   return (size_t)by;
 }
 
-hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count, const double* Me, const double* Bd,
-                        const double* Cd, const double* Dm, const double* Em, const double* Fm, const double* Gm,
-                        const double* Hm, const double* Jm, const double* ru, const double* ruh, int on_device,
-                        void* stream) {
-  if (!p) return HDG_ERR_ARG;
+hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const double* const* blocks,
+                                const int64_t* elem_stride, int on_device, void* stream) {
+  if (!p || !blocks) return HDG_ERR_ARG;
   if (e0 < 0 || count < 0 || e0 + count > p->NE) return HDG_ERR_ARG;
-  if (!Me || !Bd || !Cd || !Dm || !Em || !Fm || !Gm || !Hm || !Jm || !ru || !ruh) return HDG_ERR_ARG;
+  const InSizes z = in_sizes(p);
+  const int64_t sz[11] = {z.Me, z.Bd, z.Cd, z.D, z.E, z.F, z.G, z.H, z.J, z.ru, z.ruh};
+  bool sh[11];
+  for (int i = 0; i < 11; ++i) {
+    if (!blocks[i]) return HDG_ERR_ARG;
+    const int64_t st = elem_stride ? elem_stride[i] : sz[i];
+    if (st != 0 && st != sz[i]) return HDG_ERR_ARG;
+    sh[i] = (st == 0);
+  }
   cudaStream_t s = (cudaStream_t)stream;
+  bool all_shared = true;
+  for (int i = 0; i < 11; ++i) all_shared = all_shared && sh[i];
   try {
     DeviceGuard dg(p->device);
-    const InSizes z = in_sizes(p);
     const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (all_shared && count > 1) {
+      // identical elements: condense element e0 once, then copy its results
+      // (Kbar, rbar and the recovery data) to the other elements
+      hdg_status st = hdg_condense_strided(p, e0, 1, blocks, elem_stride, on_device, stream);
+      if (st != HDG_OK) return st;
+      const int64_t per[6] = {(int64_t)p->nlb * p->nlb, (int64_t)p->nlb * p->R, (int64_t)p->D * p->PE * p->PE,
+                              (int64_t)p->D * p->PE * p->nlPF, (int64_t)p->MPE * p->nlb, (int64_t)p->MPE * p->R};
+      double* base[6] = {p->d_Kbar, p->d_rbar, p->d_MinvB, p->d_MinvC, p->d_XF, p->d_Xr};
+      for (int i = 0; i < 6; ++i)
+        bcast_copy(base[i] + (e0 + 1) * per[i], base[i] + e0 * per[i], per[i], count - 1, s);
+      CK(cudaGetLastError());
+      for (int64_t e = e0; e < e0 + count; ++e) {
+        if (!p->condensed[e]) {
+          p->condensed[e] = 1;
+          p->n_condensed++;
+        }
+      }
+      p->assembled = false;
+      return HDG_OK;
+    }
     for (int64_t c0 = 0; c0 < count; c0 += p->chunk) {
       const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
-      const double* src[11] = {Me, Bd, Cd, Dm, Em, Fm, Gm, Hm, Jm, ru, ruh};
-      const int64_t sz[11] = {z.Me, z.Bd, z.Cd, z.D, z.E, z.F, z.G, z.H, z.J, z.ru, z.ruh};
       const double* dev[11];
       double* st = p->d_stage;
       for (int i = 0; i < 11; ++i) {
-        const double* base = src[i] + c0 * sz[i];
+        const double* base = blocks[i] + (sh[i] ? 0 : c0 * sz[i]);
+        const int64_t ncopy = sh[i] ? 1 : ec;
         if (on_device) {
           dev[i] = base;
         } else {
-          CK(cudaMemcpyAsync(st, base, sizeof(double) * ec * sz[i], kind, s));
+          CK(cudaMemcpyAsync(st, base, sizeof(double) * ncopy * sz[i], kind, s));
           dev[i] = st;
-          st += ec * sz[i];
+          st += ncopy * sz[i];
         }
       }
       condense_chunk(p, e0 + c0, ec, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], dev[7], dev[8], dev[9],
-                     dev[10], s);
+                     dev[10], sh, s);
       CK(cudaGetLastError());
       for (int64_t e = e0 + c0; e < e0 + c0 + ec; ++e) {
         if (!p->condensed[e]) {
@@ -1142,6 +1191,14 @@ hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count, const double* 
   } catch (const CudaError& e) {
     return to_status(e);
   }
+}
+
+hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count, const double* Me, const double* Bd,
+                        const double* Cd, const double* Dm, const double* Em, const double* Fm, const double* Gm,
+                        const double* Hm, const double* Jm, const double* ru, const double* ruh, int on_device,
+                        void* stream) {
+  const double* blocks[11] = {Me, Bd, Cd, Dm, Em, Fm, Gm, Hm, Jm, ru, ruh};
+  return hdg_condense_strided(p, e0, count, blocks, nullptr, on_device, stream);
 }
 
 hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhatD, int on_device, void* stream) {
@@ -1220,7 +1277,8 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
     const int b = p->b;
     const bool need16 = (o->poly_prec == HDG_BF16 || o->inner_prec == HDG_BF16);
     if (o->pc == HDG_PC_BJ) {
-      double* tmp = (double*)p->dalloc(sizeof(double) * p->nfree * b * b);
+      if (!p->d_bjtmp) p->d_bjtmp = (double*)p->dalloc(sizeof(double) * p->nfree * b * b);
+      double* tmp = p->d_bjtmp;
       extract_diag(p->K64, p->s64, p->d_rowptr, b, p->nfree, tmp, s);
       inverse_f64(tmp, b, (int64_t)b * b, p->nfree, p->d_err, s);
       p->bs64 = padded_stride<double>((int64_t)b * b);
@@ -1231,12 +1289,12 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       if (need16 && !p->bj16) p->bj16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * p->nfree * p->bs16);
       pack_blocks(tmp, b, p->nfree, p->bj64, p->bs64, p->bj32, p->bs32, p->bj16, p->bs16, s);
       hdg_status st = check_err(p, s);
-      p->dfree(tmp, sizeof(double) * p->nfree * b * b);
       if (st != HDG_OK) return st;
     } else if (o->pc == HDG_PC_ASM) {
       const int nlb = p->nlb;
       if (nlb > inverse_max_n()) return HDG_ERR_ARG;
-      double* P = (double*)p->dalloc(sizeof(double) * p->NE * nlb * nlb);
+      if (!p->d_asmP) p->d_asmP = (double*)p->dalloc(sizeof(double) * p->NE * nlb * nlb);
+      double* P = p->d_asmP;
       asm_build(p->d_Kbar, nlb, b, p->nl, p->NE, p->d_asm_lf, p->d_asm_cnt, p->d_asm_face_free, p->K64, p->s64,
                 p->d_rowptr, P, s);
       inverse_f64(P, nlb, (int64_t)nlb * nlb, p->NE, p->d_err, s);
@@ -1250,7 +1308,6 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       asm_pack(P, nlb, b, p->nl, p->NE, p->d_asm_rowptr, p->as64, p->as_s64, p->as32, p->as_s32, p->as16, p->as_s16,
                s);
       hdg_status st = check_err(p, s);
-      p->dfree(P, sizeof(double) * p->NE * nlb * nlb);
       if (st != HDG_OK) return st;
     }
     p->pc_ready = o->pc;
@@ -1402,12 +1459,12 @@ hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* strea
   try {
     DeviceGuard dg(p->device);
     const int64_t n = p->NF * p->b * p->R;
-    double* full = on_device ? uhat : (double*)p->dalloc(sizeof(double) * n);
+    if (!on_device && !p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * n);
+    double* full = on_device ? uhat : p->d_full;
     expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
     if (!on_device) {
       CK(cudaMemcpyAsync(uhat, full, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      p->dfree(full, sizeof(double) * n);
     }
     return HDG_OK;
   } catch (const CudaError& e) {
@@ -1424,9 +1481,12 @@ hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void*
   try {
     DeviceGuard dg(p->device);
     const int64_t nu = p->NE * p->MPE * p->R, nq = p->NE * p->MDPE * p->R, nt = p->NF * p->b * p->R;
-    double* full = (double*)p->dalloc(sizeof(double) * nt);
-    double* du = on_device ? u : (double*)p->dalloc(sizeof(double) * nu);
-    double* dq = on_device ? q : (double*)p->dalloc(sizeof(double) * nq);
+    if (!p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * nt);
+    if (!on_device && !p->d_uout) p->d_uout = (double*)p->dalloc(sizeof(double) * nu);
+    if (!on_device && !p->d_qout) p->d_qout = (double*)p->dalloc(sizeof(double) * nq);
+    double* full = p->d_full;
+    double* du = on_device ? u : p->d_uout;
+    double* dq = on_device ? q : p->d_qout;
     expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
     RecoverDesc d{};
     d.XF = p->d_XF;
@@ -1451,11 +1511,6 @@ hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void*
       CK(cudaMemcpyAsync(q, dq, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
-    p->dfree(full, sizeof(double) * nt);
-    if (!on_device) {
-      p->dfree(du, sizeof(double) * nu);
-      p->dfree(dq, sizeof(double) * nq);
-    }
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);

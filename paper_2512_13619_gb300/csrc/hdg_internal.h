@@ -109,6 +109,8 @@ struct RecoverDesc {
   double* uhe;               // scratch n_elem * nl*b * R
 };
 void recover(const RecoverDesc& d, cudaStream_t s);
+// count copies of the n-element block src into dst
+void bcast_copy(double* dst, const double* src, int64_t n, int64_t count, cudaStream_t s);
 // free-vector -> full trace (Dirichlet faces from uhatD)
 void expand_trace(const double* x, const double* uhatD, const int32_t* free_of_face, int64_t n_face, int b, int R,
                   double* full, cudaStream_t s);

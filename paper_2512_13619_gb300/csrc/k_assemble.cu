@@ -194,6 +194,11 @@ __global__ void recover_kernel(RecoverDesc d) {
   }
 }
 
+__global__ void bcast_copy_kernel(double* dst, const double* src, int64_t n, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i % n];
+}
+
 inline unsigned grid_for(int64_t total, int threads) {
   int64_t g = (total + threads - 1) / threads;
   if (g > 65535 * 16) g = 65535 * 16;
@@ -238,6 +243,12 @@ void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const
   int64_t total = n_free * b * R;
   if (total <= 0) return;
   count_launch(); asm_face_sum_kernel<<<grid_for(total, 256), 256, 0, s>>>(ze, nlb, b, R, n_free, fsum, z);
+}
+
+void bcast_copy(double* dst, const double* src, int64_t n, int64_t count, cudaStream_t s) {
+  const int64_t total = n * count;
+  if (total <= 0) return;
+  count_launch(); bcast_copy_kernel<<<grid_for(total, 256), 256, 0, s>>>(dst, src, n, total);
 }
 
 void expand_trace(const double* x, const double* uhatD, const int32_t* free_of_face, int64_t n_face, int b, int R,

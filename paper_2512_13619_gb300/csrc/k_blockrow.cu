@@ -384,15 +384,11 @@ __global__ void to_f32_kernel(const double* x, float* y, int64_t n) {
     y[i] = (float)x[i];
 }
 
-int g_num_sms = 0;
 int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);  // a cached attribute query
+  return n > 0 ? n : 1;
 }
 
 constexpr size_t kStageTarget = 40 * 1024;
@@ -442,11 +438,7 @@ void launch_tma(const BlockRowDesc& d, cudaStream_t s) {
   const size_t red = (pl.P > 1) ? (size_t)pl.P * pl.G * d.b_rows * R * sizeof(typename Acc<T>::type) : 0;
   const size_t smem = 256 + (size_t)pl.nstage * pl.stage_bytes + red;
   auto kern = blockrow_tma_kernel<T, R>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);  // per context; cheap
   const int threads = pl.NT + 32 * pl.NPW;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);

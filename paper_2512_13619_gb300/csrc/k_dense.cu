@@ -227,11 +227,7 @@ bool inverse_f64(double* A, int n, int64_t stride, int64_t count, unsigned* err,
   if (n <= 0 || count <= 0) return true;
   size_t smem = inverse_smem(n);
   if (smem > kInvSmemMax - 1024) return false;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kInvSmemMax - 1024));
-    attr_set = true;
-  }
+  cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kInvSmemMax - 1024));
   const int64_t gmax = 2147483647;
   for (int64_t c0 = 0; c0 < count; c0 += gmax) {
     int64_t c = count - c0 < gmax ? count - c0 : gmax;

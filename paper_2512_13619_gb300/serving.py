@@ -1,0 +1,249 @@
+"""Continuous-batching serving loop for HDG solves on one GPU.
+
+Requests (one HDG problem each) arrive over time.  A request is admitted as
+soon as a lane is free and its problem fits the device-memory budget; up to
+`lanes` requests run at once, each on its own CUDA stream, so their
+condensation, assembly and GMRES kernels overlap on the device.  A *slot* is
+a resident problem of one mesh shape: its condensed blocks, preconditioner
+factors and Krylov basis stay allocated after a request finishes and are
+reused by the next request of the same shape; idle slots of other shapes are
+evicted when the budget requires it.  Latency is measured from a request's
+arrival to the moment its trace is back in host memory.
+
+Every numerical step runs in libhdg.so; this module only schedules.  The
+scheduler is independent of the backend (`Backend`), so its admission and
+eviction logic can be exercised without a GPU.
+"""
+import collections
+import threading
+import time
+
+import numpy as np
+
+
+class Backend:
+    """What the scheduler needs from a solver: slot sizes, slot creation and
+    destruction, and one solve of a request on a slot (on the lane's stream)."""
+
+    def slot_bytes(self, shape):
+        raise NotImplementedError
+
+    def create_slot(self, shape, lane):
+        raise NotImplementedError
+
+    def destroy_slot(self, slot):
+        raise NotImplementedError
+
+    def solve(self, slot, request, lane):
+        """Returns a result object (e.g. the trace) once it is on the host."""
+        raise NotImplementedError
+
+    def lane_setup(self, lane):
+        pass
+
+
+class Slot:
+    def __init__(self, shape, handle, nbytes):
+        self.shape = shape
+        self.handle = handle
+        self.nbytes = nbytes
+        self.busy = False
+        self.last_used = 0.0
+        self.uses = 0
+
+
+class Server:
+    def __init__(self, backend, lanes=4, mem_budget=64 << 30):
+        self.backend = backend
+        self.lanes = lanes
+        self.mem_budget = mem_budget
+        self.slots = []
+        self.used_bytes = 0
+        self.cv = threading.Condition()
+        self.ready = collections.deque()
+        self.results = {}
+        self.t_done = {}
+        self.errors = []
+        self.evictions = 0
+        self.creations = 0
+        self.max_in_flight = 0
+        self.in_flight = 0
+
+    # ---------------------------------------------------------------- slots
+    def _acquire_slot(self, shape):
+        """Called with self.cv held.  Returns an idle slot of `shape`
+        (creating one within the budget, evicting idle slots of other shapes
+        if needed) or None when the request has to wait."""
+        for sl in self.slots:
+            if sl.shape == shape and not sl.busy:
+                sl.busy = True
+                return sl
+        need = self.backend.slot_bytes(shape)
+        if need > self.mem_budget:
+            raise MemoryError('request of shape %s needs %d bytes > budget %d' % (shape, need, self.mem_budget))
+        while self.used_bytes + need > self.mem_budget:
+            idle = [s for s in self.slots if not s.busy]
+            if not idle:
+                return None
+            victim = min(idle, key=lambda s: s.last_used)
+            self.slots.remove(victim)
+            self.used_bytes -= victim.nbytes
+            self.backend.destroy_slot(victim)
+            self.evictions += 1
+        sl = Slot(shape, None, need)
+        sl.busy = True
+        self.slots.append(sl)
+        self.used_bytes += need
+        self.creations += 1
+        return sl
+
+    # ---------------------------------------------------------------- lanes
+    def _lane(self, lane):
+        self.backend.lane_setup(lane)
+        while True:
+            with self.cv:
+                while True:
+                    if not self.ready and self._closed:
+                        return
+                    if self.ready:
+                        req = self.ready[0]
+                        try:
+                            sl = self._acquire_slot(req['shape'])
+                        except MemoryError as exc:   # can never fit: reject it
+                            self.ready.popleft()
+                            self.errors.append((req['id'], repr(exc)))
+                            self.cv.notify_all()
+                            continue
+                        if sl is not None:
+                            self.ready.popleft()
+                            break
+                    self.cv.wait(timeout=0.05)
+                self.in_flight += 1
+                self.max_in_flight = max(self.max_in_flight, self.in_flight)
+            try:
+                if sl.handle is None:
+                    sl.handle = self.backend.create_slot(sl.shape, lane)
+                res = self.backend.solve(sl.handle, req, lane)
+                t = time.perf_counter()
+                with self.cv:
+                    self.results[req['id']] = res
+                    self.t_done[req['id']] = t
+            except Exception as exc:  # recorded, the server keeps serving
+                with self.cv:
+                    self.errors.append((req['id'], repr(exc)))
+            finally:
+                with self.cv:
+                    sl.busy = False
+                    sl.last_used = time.perf_counter()
+                    sl.uses += 1
+                    self.in_flight -= 1
+                    self.cv.notify_all()
+
+    def run(self, requests, arrivals):
+        """Serve `requests` (dicts with 'id' and 'shape'), request i arriving
+        arrivals[i] seconds after the start.  Returns the statistics."""
+        self._closed = False
+        threads = [threading.Thread(target=self._lane, args=(i,), daemon=True) for i in range(self.lanes)]
+        for th in threads:
+            th.start()
+        t0 = time.perf_counter()
+        t_arr = {}
+        for req, a in sorted(zip(requests, arrivals), key=lambda x: x[1]):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            with self.cv:
+                t_arr[req['id']] = t0 + a
+                self.ready.append(req)
+                self.cv.notify_all()
+        with self.cv:
+            self._closed = True
+            self.cv.notify_all()
+        for th in threads:
+            th.join()
+        ids = [i for i in t_arr if i in self.t_done]      # this run's completed requests
+        lat = np.array([self.t_done[i] - t_arr[i] for i in ids])
+        done = len(ids)
+        span = (max(self.t_done[i] for i in ids) - t0) if done else 0.0
+        return {
+            'completed': done, 'errors': sum(1 for i, _ in self.errors if i in t_arr), 'lanes': self.lanes,
+            'p50_ms': float(np.percentile(lat, 50) * 1e3) if done else None,
+            'p99_ms': float(np.percentile(lat, 99) * 1e3) if done else None,
+            'mean_ms': float(lat.mean() * 1e3) if done else None,
+            'solves_per_s': done / span if span > 0 else None,
+            'slot_creations': self.creations, 'evictions': self.evictions,
+            'max_in_flight': self.max_in_flight, 'resident_bytes': self.used_bytes,
+        }
+
+    def close(self):
+        for sl in self.slots:
+            if sl.handle is not None:
+                self.backend.destroy_slot(sl)
+        self.slots = []
+        self.used_bytes = 0
+
+
+# ------------------------------------------------------------ HDG backend
+class HdgBackend(Backend):
+    """Solves HDG convection-diffusion requests through the C ABI.
+
+    `inputs(shape, request)` returns (mesh dict, blocks, strides, uhatD) for
+    a request: the mesh arrays of the shape and the element blocks, shared
+    (stride 0) where all elements are identical.  opts: hdg_solver_opts."""
+
+    def __init__(self, inputs, opts, device=0, nrhs=1):
+        import torch
+        from . import _lib as L
+        from . import driver
+        self.L, self.driver, self.torch = L, driver, torch
+        self.inputs = inputs
+        self.opts = opts
+        self.device = device
+        self.nrhs = nrhs
+        self.streams = {}
+        self._mesh_cache = {}
+
+    def lane_setup(self, lane):
+        self.torch.cuda.set_device(self.device)
+        self.streams[lane] = self.torch.cuda.Stream(device=self.device)
+
+    def _mesh(self, shape):
+        if shape not in self._mesh_cache:
+            self._mesh_cache[shape] = self.inputs(shape, None)[0]
+        return self._mesh_cache[shape]
+
+    def slot_bytes(self, shape):
+        m = self._mesh(shape)
+        mesh = self.L.hdg_mesh()
+        ef = np.ascontiguousarray(m['elem_face'], np.int32)
+        fe = np.ascontiguousarray(m['face_elem'], np.int32)
+        fd = np.ascontiguousarray(m['face_dirichlet'], np.uint8)
+        mesh.dim, mesh.n_lfe, mesh.M, mesh.PE, mesh.PF = m['dim'], m['n_lfe'], m['M'], m['PE'], m['PF']
+        mesh.n_elem, mesh.n_face = ef.shape[0], fd.shape[0]
+        mesh.elem_face, mesh.face_elem, mesh.face_dirichlet = ef.ctypes.data, fe.ctypes.data, fd.ctypes.data
+        return int(self.L.hdg_workspace_bytes(mesh, self.nrhs, self.opts))
+
+    def create_slot(self, shape, lane):
+        m = self._mesh(shape)
+        return self.driver.Problem(m['dim'], m['n_lfe'], m['M'], m['PE'], m['PF'], m['elem_face'],
+                                   m['face_elem'], m['face_dirichlet'], self.nrhs, self.device)
+
+    def destroy_slot(self, slot):
+        if slot.handle is not None:
+            slot.handle.close()
+
+    def solve(self, prob, request, lane):
+        L, check = self.L, self.driver.check
+        st = self.streams[lane].cuda_stream
+        _, blocks, strides, uD = self.inputs(request['shape'], request)
+        check(L.hdg_condense_strided(prob.h, 0, prob.n_elem, [blocks[k] for k in self.driver.BLOCK_NAMES],
+                                     strides, 0, st), 'condense')
+        check(L.hdg_set_dirichlet(prob.h, uD, 0, st), 'dirichlet')
+        check(L.hdg_assemble(prob.h, self.opts, st), 'assemble')
+        check(L.hdg_setup_precond(prob.h, self.opts, None, st), 'setup')
+        info = L.hdg_solve_info()
+        s = L.hdg_solve(prob.h, self.opts, st, info)
+        check(s, 'solve')
+        out = np.empty((prob.n_face, prob.b, prob.R))
+        check(L.hdg_get_trace(prob.h, out, 0, st), 'trace')
+        return {'trace': out, 'iters': info.iters, 'outer': info.outer, 'rel': info.rel_resid}

@@ -275,3 +275,30 @@ def test_graph_cycles_equal_launch_by_launch(inner):
         p.close()
     assert np.array_equal(sols[0][0], sols[1][0]) and sols[0][1] == sols[1][1]
     assert np.array_equal(sols[0][0], sols[2][0])
+
+
+@pytest.mark.parametrize('shared', ['all', 'geometry'])
+def test_condense_strided_shared_blocks(shared):
+    """hdg_condense_strided with blocks shared by all elements (stride 0)
+    equals hdg_condense with per-element copies, on a structured mesh whose
+    elements are identical."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w = W.hex_convdiff(3, 2, 0.3, (0.6, 0.0, 0.8))
+    full = w.blocks()
+    _, one, strides, _ = W.structured_convdiff_inputs(3, 2, 0.3, (0.6, 0.0, 0.8))
+    names = driver.BLOCK_NAMES
+    if shared == 'geometry':     # only the q-equation blocks shared
+        blocks = [one[k] if i < 3 else np.ascontiguousarray(full[k]) for i, k in enumerate(names)]
+        strides = [0, 0, 0] + [full[k][0].size for k in names[3:]]
+    else:
+        blocks = [one[k] for k in names]
+    p = driver.Problem.from_workload(w)
+    assert L.hdg_condense_strided(p.h, 0, w.n_elem, blocks, strides, 0) == 0
+    K1, r1 = p.condensed()
+    p.close()
+    p2 = driver.Problem.from_workload(w)
+    p2.condense(full)
+    K2, r2 = p2.condensed()
+    p2.close()
+    assert rel(K1, K2) < 1e-13 and rel(r1, r2) < 1e-13

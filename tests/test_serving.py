@@ -1,0 +1,122 @@
+"""Serving loop: admission by memory budget, slot reuse and eviction (CPU,
+with a fake backend), and on the GPU that every request's trace is the same
+solved alone and in the mix, and equals the oracle's solution."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2512_13619_gb300.serving import Backend, Server
+
+
+class FakeBackend(Backend):
+    def __init__(self, sizes, delay=0.01):
+        self.sizes = sizes
+        self.delay = delay
+        self.live = 0
+        self.max_live_bytes = 0
+        self.lock = threading.Lock()
+        self.active = 0
+        self.max_active = 0
+
+    def slot_bytes(self, shape):
+        return self.sizes[shape]
+
+    def create_slot(self, shape, lane):
+        with self.lock:
+            self.live += self.sizes[shape]
+            self.max_live_bytes = max(self.max_live_bytes, self.live)
+        return {'shape': shape}
+
+    def destroy_slot(self, slot):
+        with self.lock:
+            self.live -= self.sizes[slot.shape]
+
+    def solve(self, slot, request, lane):
+        with self.lock:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+        time.sleep(self.delay)
+        with self.lock:
+            self.active -= 1
+        return request['id'] * 2
+
+
+def test_scheduler_budget_reuse_and_eviction():
+    sizes = {'a': 40, 'b': 30, 'c': 50}
+    be = FakeBackend(sizes)
+    srv = Server(be, lanes=3, mem_budget=100)
+    shapes = ['a', 'b', 'c', 'a', 'a', 'b', 'c', 'c', 'a', 'b'] * 3
+    reqs = [{'id': i, 'shape': s} for i, s in enumerate(shapes)]
+    arr = np.linspace(0.0, 0.2, len(reqs))
+    st = srv.run(reqs, arr)
+    assert st['completed'] == len(reqs) and st['errors'] == 0
+    assert all(srv.results[i] == 2 * i for i in range(len(reqs)))
+    assert be.max_live_bytes <= 100              # never above the budget
+    assert st['max_in_flight'] <= 3 and be.max_active <= 3
+    assert st['evictions'] > 0                   # the three shapes do not fit together
+    assert st['slot_creations'] < len(reqs)      # slots are reused
+    assert st['p99_ms'] >= st['p50_ms'] > 0
+
+
+def test_request_larger_than_budget_is_an_error():
+    be = FakeBackend({'big': 500})
+    srv = Server(be, lanes=1, mem_budget=100)
+    be.sizes['small'] = 10
+    st = srv.run([{'id': 0, 'shape': 'big'}, {'id': 1, 'shape': 'small'}], [0.0, 0.01])
+    assert st['errors'] == 1 and srv.errors[0][0] == 0       # rejected, the server keeps serving
+    assert st['completed'] == 1 and srv.results[1] == 2
+
+
+@pytest.mark.gpu
+def test_serving_results_alone_equal_mixed_and_oracle():
+    from tests.gpu_helpers import need_gpu
+    need_gpu()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver
+    from paper_2512_13619_gb300.serving import HdgBackend
+    from tests.oracle_helpers import OracleSystem
+    o = driver.opts(restart=30, rtol=1e-8, pc='bj', inner='fp32', inner_rtol=1e-4, max_iters=3000)
+
+    def inputs(shape, req):
+        n, k = shape
+        kappa, beta = (0.1, (1.0, 0.0, 0.0)) if req is None else (req['kappa'], req['beta'])
+        return W.structured_convdiff_inputs(n, k, kappa, beta)
+
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(10):
+        b = rng.standard_normal(3)
+        reqs.append({'id': i, 'shape': (int(rng.integers(3, 5)), int(rng.integers(1, 3))),
+                     'kappa': float(10 ** rng.uniform(-2, 0)), 'beta': b / np.linalg.norm(b)})
+    alone = {}
+    srv1 = Server(HdgBackend(inputs, o), lanes=1, mem_budget=8 << 30)
+    for r in reqs:
+        srv1.run([r], [0.0])
+        alone[r['id']] = srv1.results[r['id']]['trace']
+    srv1.close()
+    srv = Server(HdgBackend(inputs, o), lanes=4, mem_budget=8 << 30)
+    st = srv.run(reqs, np.zeros(len(reqs)))
+    srv.close()
+    assert st['completed'] == len(reqs) and st['errors'] == 0
+    for r in reqs:
+        assert np.array_equal(srv.results[r['id']]['trace'], alone[r['id']])
+    # one request against the oracle (per-element blocks, direct solve)
+    r = reqs[0]
+    n, k = r['shape']
+    w = W.hex_convdiff(n, k, r['kappa'], r['beta'])
+    s = OracleSystem(w)
+    x = s.direct().reshape(-1)
+    fd = w.face_dirichlet
+    xg = srv.results[r['id']]['trace'][fd == 0].reshape(-1)
+    assert np.linalg.norm(xg - x) / np.linalg.norm(x) < 1e-5
+
+
+def test_server_runs_twice_statistics_per_run():
+    be = FakeBackend({'a': 10})
+    srv = Server(be, lanes=2, mem_budget=100)
+    st1 = srv.run([{'id': 0, 'shape': 'a'}], [0.0])
+    st2 = srv.run([{'id': 1, 'shape': 'a'}, {'id': 2, 'shape': 'a'}], [0.0, 0.0])
+    assert st1['completed'] == 1 and st2['completed'] == 2
+    assert st2['slot_creations'] <= 2 and srv.results[2] == 4
