@@ -48,6 +48,12 @@ def parse():
                     help='requests of the serving stream timed beside the step (0: none)')
     ap.add_argument('--lanes', type=int, default=4, help='concurrent requests of the serving loop')
     ap.add_argument('--serving-budget-gb', type=float, default=64.0)
+    ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
+    ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
+    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40'], default='poisson16',
+                    help='poisson16: the step above; elasticity32 / cdr40: solver and kernel measurements '
+                         'on the 32^3 perturbed Q2 elasticity (8 RHS) and 40^3 Q2 5-component CDR (4 RHS) '
+                         'problems, one JSON line')
     ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
                     help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
                          'one FP32 hdg_apply_K call (matvec) or one solve (solve-*), for profilers; no JSON')
@@ -405,6 +411,127 @@ def serving_leg(args, local):
         'latency': 'arrival to trace in host memory (includes element-block generation on the host)'}
 
 
+def run_config(args, local):
+    """Solver and kernel measurements on a large problem: condensation,
+    assembly, preconditioner set-up and GMRES to 1e-8 with the plain FP64
+    path and the mixed path (FP32 blocks, FP64 refinement), per
+    preconditioner; block-row products after autotuning (HBM GB/s)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    names = driver.BLOCK_NAMES
+    t_gen = time.perf_counter()
+    nmesh = args.mesh_n or (40 if args.workload == 'cdr40' else 32)
+    if args.workload == 'cdr40':
+        w = W.hex_cdr(n=nmesh, k=2, R=4)
+        hb, strides = W.shared_blocks(w)
+        dblk = {k: torch.from_numpy(hb[k]).to(dev) for k in names}
+        cases = [('bj', None, 0, 'fp32', 'fp32'), ('bj', 'gmres', 10, 'fp32', 'bf16')]
+        desc = 'HDG 5-component CDR, %d^3 hex, Q2 (45 dofs/face, 270x270 element blocks), 4 RHS' % nmesh
+    else:
+        w = W.hex_elasticity(n=nmesh, k=2, R=8)
+        dblk = {}
+        sizes = None
+        ch = 1024
+        for c0 in range(0, w.n_elem, ch):
+            b = w.blocks(c0, min(w.n_elem, c0 + ch))
+            if sizes is None:
+                dblk = {k: torch.empty((w.n_elem,) + b[k].shape[1:], dtype=torch.float64, device=dev) for k in names}
+                sizes = True
+            for k in names:
+                dblk[k][c0:c0 + b[k].shape[0]].copy_(torch.from_numpy(np.ascontiguousarray(b[k])))
+        strides = [dblk[k][0].numel() for k in names]
+        cases = [('asm', None, 0, 'fp32', 'fp32'), ('bj', 'chebyshev', 4, 'fp32', 'fp32')]
+        desc = 'HDG elasticity, %d^3 perturbed hex, Q2 (27 dofs/face, 162x162 element blocks), 8 RHS' % nmesh
+    t_gen = time.perf_counter() - t_gen
+    R = w.R
+    st = torch.cuda.current_stream(dev).cuda_stream
+    p = driver.Problem.from_workload(w, local)
+    ptrs = [dblk[k] for k in names]
+
+    def ev_time(fn, reps=1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    def condense():
+        driver.check(L.hdg_condense_strided(p.h, 0, w.n_elem, ptrs, strides, 1, st), 'condense')
+    condense()
+    ms_cond = ev_time(condense)
+    print('condensation %.1f ms' % ms_cond, file=sys.stderr, flush=True)
+    cflops = condense_flops(w) * w.n_elem
+    driver.check(L.hdg_set_dirichlet(p.h, w.uhat_dirichlet(), 0, st), 'dirichlet')
+    out = {'workload': desc, 'n_elem': w.n_elem, 'n_dof': p.n_dof, 'rhs': R, 'input_generation_s': round(t_gen, 1),
+           'condense_ms': round(ms_cond, 2), 'condense_tflops': round(cflops / ms_cond / 1e9, 3),
+           'condense_frac_fp64_alu': round(cflops / ms_cond / 1e9 / FP64_ALU_PEAK_TFLOPS, 3), 'solves': []}
+    pk = peaks()
+    v0 = torch.from_numpy(w.random_vector(11)).to(dev)       # start vector of the polynomial's Arnoldi cycle
+    for pc, poly, deg, inner, pprec in cases:
+        row = {'pc': pc, 'poly': poly, 'degree': deg}
+        for tag in ('fp64', 'mixed'):
+            o = driver.opts(restart=50, rtol=1e-8, pc=pc, poly=poly, degree=deg,
+                            inner='fp64' if tag == 'fp64' else inner, poly_prec='fp64' if tag == 'fp64' else pprec,
+                            inner_rtol=1e-4, max_iters=args.max_iters)
+            ms_setup = ev_time(lambda: (driver.check(L.hdg_assemble(p.h, o, st), 'assemble'),
+                                        driver.check(L.hdg_setup_precond(p.h, o, v0 if poly else None, st),
+                                                     'setup')))
+            info = L.hdg_solve_info()
+            stt = L.hdg_solve(p.h, o, st, info)          # builds the cycle graphs
+            print('%s %s %s: status %s, %d iterations, rel %.3g' % (pc, poly, tag, L.hdg_status_str(stt),
+                                                                   info.iters, info.rel_resid),
+                  file=sys.stderr, flush=True)
+            if stt == 0:
+                ms = ev_time(lambda: L.hdg_solve(p.h, o, st, info))
+            else:
+                ms = float('nan')
+            row[tag] = {'setup_ms': round(ms_setup, 2), 'solve_ms': round(ms, 2), 'gmres': info.iters,
+                        'refinement': info.outer, 'rel_resid': info.rel_resid, 'status': L.hdg_status_str(stt)}
+        row['speedup_mixed_vs_fp64'] = round(row['fp64']['solve_ms'] / row['mixed']['solve_ms'], 3)
+        out['solves'].append(row)
+        # block-row products after autotuning: K at every stored precision, the base preconditioner
+        driver.check(L.hdg_autotune(p.h, 10, 0, st), 'autotune')
+        fd = w.face_dirichlet
+        nfree_e = (fd[w.mesh.elem_face] == 0).sum(axis=1)
+        nnzb = int((nfree_e ** 2).sum() - w.n_free)
+        b = w.M * w.PF
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        xv = torch.randn(p.n_dof * R, dtype=torch.float64, device=dev)
+        yv = torch.empty_like(xv)
+        kern = {}
+        for prec, pname, sz in ((0, 'fp64', 8), (1, 'fp32', 4), (2, 'bf16', 2)):
+            if L.hdg_apply_K(p.h, prec, xv, yv, st) != 0:
+                continue
+            tot = 0.0
+            for _ in range(5):
+                flush.fill_(1.0)
+                tot += ev_time(lambda: driver.check(L.hdg_apply_K(p.h, prec, xv, yv, st), 'apply_K'))
+            avg = tot / 5
+            by = nnzb * b * b * sz + p.n_dof * R * (16 if prec == 0 else 24)
+            _, cfg, us, us0 = L.hdg_get_tuning(p.h, 0, prec)
+            kern['K_' + pname] = {'avg_ms': round(avg, 4), 'gbs': round(by / avg / 1e6, 1),
+                                  'frac_hbm': round(by / avg / 1e6 / pk['hbm_gbs'], 3), 'tuned_cfg': cfg,
+                                  'tuned_us': round(us, 1), 'default_us': round(us0, 1)}
+        op = 1 if pc == 'bj' else 2
+        o = driver.opts(restart=50, pc=pc)
+        for prec, pname in ((0, 'fp64'), (1, 'fp32')):
+            _, cfg, us, us0 = L.hdg_get_tuning(p.h, op, prec)
+            if us > 0:
+                kern[pc + '_' + pname] = {'tuned_cfg': cfg, 'tuned_us': round(us, 1), 'default_us': round(us0, 1)}
+        row['kernels'] = kern
+    p.close()
+    return out
+
+
 def oracle_step(w, blk):
     """One step of the workload with the FP64 oracle (condense, assemble,
     block-Jacobi, GMRES(50) to 1e-8, recover).  Returns (ms, iterations)."""
@@ -510,6 +637,8 @@ def main():
         return
     if args.impl == 'reference':
         out = run_reference(args, ws, rank)
+    elif args.workload != 'poisson16':
+        out = run_config(args, local)
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:

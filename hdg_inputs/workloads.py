@@ -227,3 +227,30 @@ def structured_convdiff_inputs(n, k, kappa, beta, R=1):
     strides = [0] * 11
     uD = np.zeros((len(mesh['face_dirichlet']), ref.PF, R))
     return mesh, {k2: np.ascontiguousarray(v) for k2, v in out.items()}, strides, uD
+
+
+def shared_blocks(w):
+    """Element blocks of a workload whose elements are all the same (an
+    unperturbed structured hex mesh, constant coefficients, every face
+    parametrised the same way from both sides; all three are checked):
+    element 0's matrices, valid for every element, plus the per-element load
+    vectors of its 'nodal' right-hand sides.  Returns (blocks, strides) for
+    hdg_condense_strided: stride 0 for the shared blocks, the per-element size
+    for ru and ruh."""
+    m = w.mesh
+    X = m.verts[m.elems]
+    assert np.allclose(X - X[:, :1], X[:1] - X[:1, :1], atol=1e-13), "elements are not translates"
+    assert np.all(w.perm == np.arange(w.PF)), "face permutations differ between elements"
+    assert w.rhs_kind == 'nodal'
+    b0 = w.blocks(0, 1)
+    mats = b0.pop('_mats')
+    cols = []
+    for s in w.rhs_seeds:
+        fn = np.random.default_rng(s).standard_normal((w.n_elem, w.M, w.PE))
+        cols.append(np.einsum('ij,eaj->eai', mats['Me'][0], fn).reshape(w.n_elem, -1))
+    out = {k: np.ascontiguousarray(v) for k, v in b0.items()}
+    out['ru'] = np.ascontiguousarray(np.stack(cols, axis=2))
+    out['ruh'] = np.zeros((w.n_elem, w.n_lfe * w.M * w.PF, w.R))
+    names = ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J', 'ru', 'ruh')
+    strides = [0] * 9 + [out['ru'][0].size, out['ruh'][0].size]
+    return {k: out[k] for k in names}, strides

@@ -204,7 +204,9 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
  * polynomial preconditioner one Arnoldi(P) cycle (MGS) with A = M^{-1} K from
  * the start vector `v0` (device, n_dof doubles), harmonic Ritz values and
  * Leja order (Sec. 4.7) or Chebyshev bounds.  v0 may be NULL when
- * opts->poly == HDG_POLY_NONE.  Errors: HDG_ERR_SINGULAR, HDG_ERR_ARG. */
+ * opts->poly == HDG_POLY_NONE.  Errors: HDG_ERR_SINGULAR, HDG_ERR_ARG (also
+ * for ASM when n_lfe*M*PF > 169: the element matrices are inverted in shared
+ * memory). */
 hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* opts, const double* v0, void* stream);
 
 /* Restarted left-preconditioned GMRES(m) on K x = r for all R right-hand
@@ -291,6 +293,46 @@ long long hdg_launch_count(void);
  * 1 = shared-memory staging with bulk copies.  Used by the autotuner;
  * results agree to rounding. */
 hdg_status hdg_set_kernel_variant(hdg_problem p, int variant);
+
+/* ---------------------------------------------------------------- autotuner
+ * Launch configurations of the block-row products (the face-block matvec of
+ * Sec. 4.2, the block-Jacobi apply of Sec. 4.3 and the additive-Schwarz
+ * element solves of Sec. 4.3), chosen by measurement.  The paper fixes one
+ * mapping per kernel; this tuning has no counterpart there.
+ *
+ * op: 0 = K (matvec), 1 = block-Jacobi apply, 2 = additive-Schwarz apply.
+ * prec: HDG_FP64 / HDG_FP32 / HDG_BF16 block storage.
+ * A configuration is three ints {kind, sp, cps}: kind 0 = heuristic default
+ * (vectorised 16-byte loads for FP32/BF16 blocks whose rows divide into
+ * 16-byte groups, else one thread per row), 1 = shared-memory staging with
+ * bulk copies, 2 = one thread per output row, 3 = 16-byte loads of 4 (FP32)
+ * or 8 (BF16) rows per thread with the slots of a row split over sp adjacent
+ * lanes (sp in {1,2,4,8}); cps = CTAs per SM of the grid-stride launch
+ * (0 = heuristic).  Every configuration computes the same sums; they differ
+ * in summation order only. */
+
+/* Time every candidate configuration of every operation the problem can run
+ * now (K at each stored precision; BJ or ASM when set up) with `reps`
+ * back-to-back launches (0 = 10) after two warm-up launches, on `stream`, and
+ * keep the fastest.  Choices are cached per block shape for the process:
+ * unless `force`, a problem whose shapes were tuned before adopts the cached
+ * choice without timing.  Synchronizes `stream`.  Requires hdg_assemble
+ * (HDG_ERR_STATE otherwise).  Overwrites the problem's GMRES scratch
+ * vectors (not the solution). */
+hdg_status hdg_autotune(hdg_problem p, int reps, int force, void* stream);
+
+/* The configuration in use for (op, prec) -> cfg3[3], with the measured
+ * microseconds per launch of it and of the heuristic default (0 when not
+ * tuned). */
+hdg_status hdg_get_tuning(hdg_problem p, int op, int prec, int* cfg3, float* us_tuned, float* us_default);
+
+/* Candidate configurations for (op, prec): writes min(n, cap) triples to
+ * cfg3 (may be NULL) and returns n; -1 on bad arguments. */
+int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap);
+
+/* Use configuration cfg3 for (op, prec) (e.g. one from
+ * hdg_tuning_candidates).  HDG_ERR_ARG for values outside the ranges above. */
+hdg_status hdg_set_tuning(hdg_problem p, int op, int prec, const int* cfg3);
 
 #ifdef __cplusplus
 }

@@ -66,6 +66,11 @@ _SIGS = {
     'hdg_apply_K_noalloc': (_I, [_V, _I, _P, _P, _V]),
     'hdg_set_graphs': (_I, [_V, _I]),
     'hdg_last_error': (ctypes.c_char_p, []),
+    'hdg_autotune': (_I, [_V, _I, _I, _V]),
+    'hdg_get_tuning': (_I, [_V, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float),
+                            ctypes.POINTER(ctypes.c_float)]),
+    'hdg_tuning_candidates': (_I, [_V, _I, _I, ctypes.POINTER(_I), _I]),
+    'hdg_set_tuning': (_I, [_V, _I, _I, ctypes.POINTER(_I)]),
 }
 
 _lib = None
@@ -219,3 +224,30 @@ def hdg_set_graphs(p, enable):
 
 def hdg_last_error():
     return load().hdg_last_error().decode()
+
+
+def hdg_autotune(p, reps=0, force=0, stream=None):
+    return load().hdg_autotune(p, reps, int(force), stream_ptr(stream))
+
+
+def hdg_get_tuning(p, op, prec):
+    """Returns (status, (kind, sp, cps), us_tuned, us_default)."""
+    c = (_I * 3)()
+    a, b = ctypes.c_float(), ctypes.c_float()
+    st = load().hdg_get_tuning(p, op, prec, c, ctypes.byref(a), ctypes.byref(b))
+    return st, tuple(c), a.value, b.value
+
+
+def hdg_tuning_candidates(p, op, prec):
+    """Returns the list of (kind, sp, cps) candidates (empty on bad arguments)."""
+    n = load().hdg_tuning_candidates(p, op, prec, None, 0)
+    if n <= 0:
+        return []
+    c = (_I * (3 * n))()
+    load().hdg_tuning_candidates(p, op, prec, c, n)
+    return [tuple(c[3 * i:3 * i + 3]) for i in range(n)]
+
+
+def hdg_set_tuning(p, op, prec, cfg):
+    c = (_I * 3)(*cfg)
+    return load().hdg_set_tuning(p, op, prec, c)

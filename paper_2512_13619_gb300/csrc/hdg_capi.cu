@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hdg_common.cuh"
@@ -18,6 +19,7 @@
 using namespace hdg;
 
 #include <atomic>
+#include <map>
 #include <mutex>
 namespace hdg {
 static std::atomic<long long> g_launches{0};
@@ -96,6 +98,7 @@ struct hdg_problem_s {
   float* K32 = nullptr;
   __nv_bfloat16* K16 = nullptr;
   int64_t s64 = 0, s32 = 0, s16 = 0;
+  int ld32 = 0, ld16 = 0;          // leading dimensions of the FP32 / BF16 face blocks (K and BJ)
   double* d_r = nullptr;
   bool assembled = false;
 
@@ -108,6 +111,7 @@ struct hdg_problem_s {
   float* as32 = nullptr;
   __nv_bfloat16* as16 = nullptr;
   int64_t as_s64 = 0, as_s32 = 0, as_s16 = 0;
+  int as_ld32 = 0, as_ld16 = 0;
   int pc_ready = -1;  // which base preconditioner is set up
   int poly_kind = 0, poly_n = 0;
   std::vector<double> th_re, th_im;
@@ -157,7 +161,12 @@ struct hdg_problem_s {
   double t_mv_ms[3] = {0.0, 0.0, 0.0};
   int64_t n_mv[3] = {0, 0, 0};
   std::vector<int> ev_prec;
-  int br_variant = 0;
+  int br_variant = 0;              // 1: bulk-copy staging for every block-row product
+  // autotuned launch configurations [operation: K, BJ, ASM][precision]
+  BrCfg tune[3][3];
+  float tune_us[3][3] = {};        // measured time of the chosen configuration
+  float tune_us0[3][3] = {};       // measured time of the heuristic default
+  unsigned tune_gen = 0;           // changes the cycle-graph key when a tuning changes
 
   void* dalloc(size_t nbytes) {
     if (nbytes == 0) nbytes = 16;
@@ -452,6 +461,16 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
 }
 
 // ------------------------------------------------------------------ operators
+enum { TUNE_K = 0, TUNE_BJ = 1, TUNE_ASM = 2 };
+BrCfg cfg_of(hdg_problem p, int op, int prec) {
+  if (p->br_variant == 1) {
+    BrCfg c;
+    c.kind = BR_TMA;
+    return c;
+  }
+  return p->tune[op][prec];
+}
+
 struct Ops {
   hdg_problem p;
   cudaStream_t s;
@@ -487,6 +506,7 @@ struct Ops {
     d.cnt = p->d_cnt;
     d.n_units = p->nfree;
     d.b_rows = p->b;
+    d.ld = prec == HDG_FP64 ? p->b : prec == HDG_FP32 ? p->ld32 : p->ld16;
     d.bc = p->b;
     d.max_slots = p->ms;
     d.R = R;
@@ -504,7 +524,7 @@ struct Ops {
     d.err = p->d_err;
     cudaEvent_t a;
     mv_timed_begin(&a);
-    blockrow(d, p->br_variant, s);
+    blockrow(d, cfg_of(p, TUNE_K, prec), s);
     mv_timed_end(prec);
   }
   // y = M^{-1} x for the base preconditioner
@@ -534,9 +554,10 @@ struct Ops {
       d.cnt = p->d_bj_cnt;
       d.n_units = p->nfree;
       d.b_rows = p->b;
+      d.ld = prec == HDG_FP64 ? p->b : prec == HDG_FP32 ? p->ld32 : p->ld16;
       d.max_slots = 1;
       d.out = y;
-      blockrow(d, p->br_variant, s);
+      blockrow(d, cfg_of(p, TUNE_BJ, prec), s);
     } else {
       d.blk = prec == HDG_FP64 ? (const void*)p->as64 : prec == HDG_FP32 ? (const void*)p->as32 : (const void*)p->as16;
       d.blk_stride = prec == HDG_FP64 ? p->as_s64 : prec == HDG_FP32 ? p->as_s32 : p->as_s16;
@@ -545,9 +566,10 @@ struct Ops {
       d.cnt = p->d_asm_cnt;
       d.n_units = p->NE;
       d.b_rows = p->nlb;
+      d.ld = prec == HDG_FP64 ? p->nlb : prec == HDG_FP32 ? p->as_ld32 : p->as_ld16;
       d.max_slots = p->nl;
       d.out = p->ze;
-      blockrow(d, p->br_variant, s);
+      blockrow(d, cfg_of(p, TUNE_ASM, prec), s);
       asm_face_sum(p->ze, p->nlb, p->b, R, p->nfree, p->d_fsum, y, s);
     }
   }
@@ -781,13 +803,13 @@ unsigned long long graph_key(const hdg_solver_opts& o, int kprec, int mprec, int
   k = k * 4 + (unsigned)kprec;
   k = k * 4 + (unsigned)mprec;
   k = k * 4 + (unsigned)kpoly;
-  k = k * 4 + (unsigned)variant;
+  k = k * 4096 + (unsigned)variant;
   return k + 1;
 }
 
 cudaGraphExec_t cycle_graph(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec, int kpoly,
                             const GmresView& kin, long long* kernels_per_iter) {
-  const unsigned long long key = graph_key(o, kprec, mprec, kpoly, p->br_variant);
+  const unsigned long long key = graph_key(o, kprec, mprec, kpoly, p->br_variant + 2 * (p->tune_gen & 2047));
   for (auto& cg : p->graphs)
     if (cg.key == key) {
       *kernels_per_iter = cg.kernels_per_iter;
@@ -862,7 +884,12 @@ struct GmresResult {
 //  true_check = 1: accept on the true residual ||b - K64 x|| <= rtol ||b||
 //                  (FP64), dividing the cycle tolerance by 10 after a false
 //                  stop on the least-squares estimate.
-//  true_check = 0: (inner solve) stop when a cycle ends on the estimate.
+//  true_check = 0: (inner solve) stop when a cycle ends on the estimate, when
+//                  the true residual with the solve's own matrix is below
+//                  rtol, or when three cycles in a row reduced that residual
+//                  by less than 10% (an inexact low-precision operator can
+//                  hold the estimate above rtol; the outer refinement
+//                  corrects what the inner solve leaves).
 GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec, int kpoly, const double* b,
                   double* x, double rtol, int maxit, int true_check, cudaStream_t s) {
   GmresResult out;
@@ -880,8 +907,8 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
   ops.Pinv(o, mprec, kpoly, b, p->t1, p->running);
   launch_norms(k, p->t1, p->zb, 0, nullptr, s);
   CK(cudaMemcpyAsync(p->res, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-  std::vector<double> cf(R, 1.0);
-  std::vector<int> done(R, 0);
+  std::vector<double> cf(R, 1.0), last(R, 0.0);
+  std::vector<int> done(R, 0), slow(R, 0);
   int total_iters = 0;
   while (true) {
     // true relative residual of the current iterate
@@ -906,7 +933,9 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
         if (out.restarts > 0 && p->h_int[r] && rel > rtol) cf[r] *= 0.1;
         done[r] = rel <= rtol ? 1 : 0;
       } else {
-        done[r] = (out.restarts > 0 && p->h_int[r]) || rel == 0.0 ? 1 : 0;
+        if (out.restarts > 0) slow[r] = rel > 0.9 * last[r] ? slow[r] + 1 : 0;
+        last[r] = rel;
+        done[r] = (out.restarts > 0 && p->h_int[r]) || rel <= rtol || slow[r] >= 3 ? 1 : 0;
       }
       if (!done[r]) all_done = false;
     }
@@ -1058,8 +1087,10 @@ hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_pr
     p->d_stage = (double*)p->dalloc(sizeof(double) * ch * in_sizes(p).total);
     p->d_tmp = (double*)p->dalloc(sizeof(double) * ch * tmp_per_elem(p));
     p->s64 = padded_stride<double>((int64_t)p->b * p->b);
-    p->s32 = padded_stride<float>((int64_t)p->b * p->b);
-    p->s16 = padded_stride<__nv_bfloat16>((int64_t)p->b * p->b);
+    p->ld32 = ld_f32(p->b);
+    p->ld16 = ld_bf16(p->b);
+    p->s32 = (int64_t)p->ld32 * p->b;      // whole 16-byte columns: a multiple of 16 bytes
+    p->s16 = (int64_t)p->ld16 * p->b;
     *out = p;
     return HDG_OK;
   } catch (const CudaError& e) {
@@ -1223,9 +1254,15 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
     DeviceGuard dg(p->device);
     const int64_t rows = std::max<int64_t>(p->nnzb, 1);
     if (!p->K64) p->K64 = (double*)p->dalloc(sizeof(double) * rows * p->s64);
-    if (!p->K32) p->K32 = (float*)p->dalloc(sizeof(float) * rows * p->s32);
+    if (!p->K32) {
+      p->K32 = (float*)p->dalloc(sizeof(float) * rows * p->s32);
+      CK(cudaMemsetAsync(p->K32, 0, sizeof(float) * rows * p->s32, s));   // padding rows stay 0
+    }
     const bool need16 = opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16);
-    if (need16 && !p->K16) p->K16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * rows * p->s16);
+    if (need16 && !p->K16) {
+      p->K16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * rows * p->s16);
+      CK(cudaMemsetAsync(p->K16, 0, sizeof(__nv_bfloat16) * rows * p->s16, s));
+    }
     if (!p->d_r) p->d_r = (double*)p->dalloc(sizeof(double) * p->ndof * p->R);
     AssembleDesc d{};
     d.Kbar = p->d_Kbar;
@@ -1249,8 +1286,10 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
     d.s64 = p->s64;
     d.K32 = p->K32;
     d.s32 = p->s32;
+    d.ld32 = p->ld32;
     d.K16 = p->K16;
     d.s16 = p->s16;
+    d.ld16 = p->ld16;
     d.r = p->d_r;
     assemble(d, s);
     CK(cudaGetLastError());
@@ -1282,12 +1321,18 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       extract_diag(p->K64, p->s64, p->d_rowptr, b, p->nfree, tmp, s);
       inverse_f64(tmp, b, (int64_t)b * b, p->nfree, p->d_err, s);
       p->bs64 = padded_stride<double>((int64_t)b * b);
-      p->bs32 = padded_stride<float>((int64_t)b * b);
-      p->bs16 = padded_stride<__nv_bfloat16>((int64_t)b * b);
+      p->bs32 = (int64_t)p->ld32 * b;
+      p->bs16 = (int64_t)p->ld16 * b;
       if (!p->bj64) p->bj64 = (double*)p->dalloc(sizeof(double) * p->nfree * p->bs64);
-      if (!p->bj32) p->bj32 = (float*)p->dalloc(sizeof(float) * p->nfree * p->bs32);
-      if (need16 && !p->bj16) p->bj16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * p->nfree * p->bs16);
-      pack_blocks(tmp, b, p->nfree, p->bj64, p->bs64, p->bj32, p->bs32, p->bj16, p->bs16, s);
+      if (!p->bj32) {
+        p->bj32 = (float*)p->dalloc(sizeof(float) * p->nfree * p->bs32);
+        CK(cudaMemsetAsync(p->bj32, 0, sizeof(float) * p->nfree * p->bs32, s));
+      }
+      if (need16 && !p->bj16) {
+        p->bj16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * p->nfree * p->bs16);
+        CK(cudaMemsetAsync(p->bj16, 0, sizeof(__nv_bfloat16) * p->nfree * p->bs16, s));
+      }
+      pack_blocks(tmp, b, p->nfree, p->bj64, p->bs64, p->bj32, p->bs32, p->ld32, p->bj16, p->bs16, p->ld16, s);
       hdg_status st = check_err(p, s);
       if (st != HDG_OK) return st;
     } else if (o->pc == HDG_PC_ASM) {
@@ -1299,14 +1344,22 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
                 p->d_rowptr, P, s);
       inverse_f64(P, nlb, (int64_t)nlb * nlb, p->NE, p->d_err, s);
       p->as_s64 = padded_stride<double>((int64_t)nlb * b);
-      p->as_s32 = padded_stride<float>((int64_t)nlb * b);
-      p->as_s16 = padded_stride<__nv_bfloat16>((int64_t)nlb * b);
+      p->as_ld32 = ld_f32(nlb);
+      p->as_ld16 = ld_bf16(nlb);
+      p->as_s32 = (int64_t)p->as_ld32 * b;
+      p->as_s16 = (int64_t)p->as_ld16 * b;
       const int64_t npan = std::max<int64_t>(p->asm_nblk, 1);
       if (!p->as64) p->as64 = (double*)p->dalloc(sizeof(double) * npan * p->as_s64);
-      if (!p->as32) p->as32 = (float*)p->dalloc(sizeof(float) * npan * p->as_s32);
-      if (need16 && !p->as16) p->as16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * npan * p->as_s16);
-      asm_pack(P, nlb, b, p->nl, p->NE, p->d_asm_rowptr, p->as64, p->as_s64, p->as32, p->as_s32, p->as16, p->as_s16,
-               s);
+      if (!p->as32) {
+        p->as32 = (float*)p->dalloc(sizeof(float) * npan * p->as_s32);
+        CK(cudaMemsetAsync(p->as32, 0, sizeof(float) * npan * p->as_s32, s));
+      }
+      if (need16 && !p->as16) {
+        p->as16 = (__nv_bfloat16*)p->dalloc(sizeof(__nv_bfloat16) * npan * p->as_s16);
+        CK(cudaMemsetAsync(p->as16, 0, sizeof(__nv_bfloat16) * npan * p->as_s16, s));
+      }
+      asm_pack(P, nlb, b, p->nl, p->NE, p->d_asm_rowptr, p->as64, p->as_s64, p->as32, p->as_s32, p->as_ld32, p->as16,
+               p->as_s16, p->as_ld16, s);
       hdg_status st = check_err(p, s);
       if (st != HDG_OK) return st;
     }
@@ -1708,6 +1761,7 @@ hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double*
     d.cnt = p->d_cnt;
     d.n_units = p->nfree;
     d.b_rows = p->b;
+    d.ld = prec == HDG_FP32 ? p->ld32 : p->ld16;
     d.bc = p->b;
     d.max_slots = p->ms;
     d.R = p->R;
@@ -1716,7 +1770,9 @@ hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double*
     d.out = y;
     d.epi = EPI_STORE;
     d.err = p->d_err;
-    blockrow(d, 0, s);   // the direct kernel: no occupancy queries, no attributes
+    BrCfg direct;
+    direct.kind = BR_DIRECT;
+    blockrow(d, direct, s);   // the direct kernel: no occupancy queries, no attributes
     CK(cudaGetLastError());
     return HDG_OK;
   } catch (const CudaError& e) {
@@ -1735,6 +1791,181 @@ hdg_status hdg_set_graphs(hdg_problem p, int enable) {
 hdg_status hdg_set_kernel_variant(hdg_problem p, int variant) {
   if (!p || variant < 0 || variant >= blockrow_variants()) return HDG_ERR_ARG;
   p->br_variant = variant;
+  return HDG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Process-wide tuning cache: problems of the same block shape reuse a choice.
+struct TuneKey {
+  int op, prec, R, b_rows, max_slots, units_log2;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(op, prec, R, b_rows, max_slots, units_log2) <
+           std::tie(o.op, o.prec, o.R, o.b_rows, o.max_slots, o.units_log2);
+  }
+};
+struct TuneVal {
+  BrCfg cfg;
+  float us, us0;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while (v > 1) { v >>= 1; ++l; }
+  return l;
+}
+
+// the block-row operations the problem can run now, per precision
+bool tune_available(hdg_problem p, int op, int prec) {
+  if (op == TUNE_K) return prec == HDG_FP64 ? p->K64 != nullptr : prec == HDG_FP32 ? p->K32 != nullptr : p->K16 != nullptr;
+  if (op == TUNE_BJ)
+    return p->pc_ready == HDG_PC_BJ &&
+           (prec == HDG_FP64 ? p->bj64 != nullptr : prec == HDG_FP32 ? p->bj32 != nullptr : p->bj16 != nullptr);
+  return p->pc_ready == HDG_PC_ASM &&
+         (prec == HDG_FP64 ? p->as64 != nullptr : prec == HDG_FP32 ? p->as32 != nullptr : p->as16 != nullptr);
+}
+
+int ld_of(hdg_problem p, int op, int prec) {
+  if (op == TUNE_ASM) return prec == HDG_FP64 ? p->nlb : prec == HDG_FP32 ? ld_f32(p->nlb) : ld_bf16(p->nlb);
+  return prec == HDG_FP64 ? p->b : prec == HDG_FP32 ? p->ld32 : p->ld16;
+}
+
+TuneKey tune_key(hdg_problem p, int op, int prec) {
+  TuneKey k;
+  k.op = op; k.prec = prec; k.R = p->R;
+  k.b_rows = op == TUNE_ASM ? p->nlb : p->b;
+  k.max_slots = op == TUNE_K ? p->ms : op == TUNE_BJ ? 1 : p->nl;
+  k.units_log2 = ilog2(op == TUNE_ASM ? p->NE : p->nfree);
+  return k;
+}
+}  // namespace
+
+extern "C" {
+
+hdg_status hdg_autotune(hdg_problem p, int reps, int force, void* stream) {
+  if (!p || reps < 0) return HDG_ERR_ARG;
+  if (!p->assembled) return HDG_ERR_STATE;
+  if (reps == 0) reps = 10;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    DeviceGuard dg(p->device);
+    ensure_workspace(p, std::max(p->ws_m, 1));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double* x = p->pt;
+    double* y = p->pAq;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * p->ndof * p->R, s));
+    Ops ops{p, s, p->R};
+    const bool timing = p->timing;
+    p->timing = false;
+    for (int op = 0; op < 3; ++op)
+      for (int prec = 0; prec < 3; ++prec) {
+        if (!tune_available(p, op, prec)) continue;
+        const TuneKey key = tune_key(p, op, prec);
+        if (!force) {
+          std::lock_guard<std::mutex> lk(g_tune_mu);
+          auto it = g_tune_cache.find(key);
+          if (it != g_tune_cache.end()) {
+            p->tune[op][prec] = it->second.cfg;
+            p->tune_us[op][prec] = it->second.us;
+            p->tune_us0[op][prec] = it->second.us0;
+            continue;
+          }
+        }
+        auto run = [&]() {
+          if (op == TUNE_K) ops.K(prec, x, y, EPI_STORE, nullptr, nullptr, nullptr);
+          else ops.Minv(op == TUNE_BJ ? HDG_PC_BJ : HDG_PC_ASM, prec, x, y, nullptr);
+        };
+        auto time_cfg = [&](const BrCfg& c) -> float {
+          p->tune[op][prec] = c;
+          run();
+          run();
+          CK(cudaEventRecord(e0, s));
+          for (int i = 0; i < reps; ++i) run();
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          CK(cudaGetLastError());
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          return ms * 1000.f / reps;
+        };
+        BlockRowDesc d{};
+        d.prec = prec;
+        d.R = p->R;
+        d.b_rows = key.b_rows;
+        d.ld = ld_of(p, op, prec);
+        d.bc = p->b;
+        d.max_slots = key.max_slots;
+        d.in32 = p->x32;
+        BrCfg cand[32];
+        const int nc = blockrow_candidates(d, cand, 32);
+        BrCfg best;
+        const float us0 = time_cfg(best);
+        float bus = us0;
+        for (int i = 0; i < nc; ++i) {
+          const float us = time_cfg(cand[i]);
+          if (us < bus) { bus = us; best = cand[i]; }
+        }
+        p->tune[op][prec] = best;
+        p->tune_us[op][prec] = bus;
+        p->tune_us0[op][prec] = us0;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = TuneVal{best, bus, us0};
+      }
+    p->timing = timing;
+    p->tune_gen++;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return check_err(p, s);
+  } catch (const CudaError& e) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap) {
+  if (!p || op < 0 || op > 2 || prec < 0 || prec > 2 || cap < 0) return -1;
+  BlockRowDesc d{};
+  const TuneKey key = tune_key(p, op, prec);
+  d.prec = prec;
+  d.R = p->R;
+  d.b_rows = key.b_rows;
+  d.ld = ld_of(p, op, prec);
+  d.bc = p->b;
+  d.max_slots = key.max_slots;
+  d.in32 = reinterpret_cast<const float*>(16);   // only tested for non-null
+  BrCfg cand[32];
+  const int nc = blockrow_candidates(d, cand, 32);
+  for (int i = 0; i < nc && i < cap && cfg3; ++i) {
+    cfg3[3 * i] = cand[i].kind; cfg3[3 * i + 1] = cand[i].sp; cfg3[3 * i + 2] = cand[i].cps;
+  }
+  return nc;
+}
+
+hdg_status hdg_set_tuning(hdg_problem p, int op, int prec, const int* cfg3) {
+  if (!p || op < 0 || op > 2 || prec < 0 || prec > 2 || !cfg3) return HDG_ERR_ARG;
+  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_VEC || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
+    return HDG_ERR_ARG;
+  p->tune[op][prec].kind = cfg3[0];
+  p->tune[op][prec].sp = cfg3[1];
+  p->tune[op][prec].cps = cfg3[2];
+  p->tune_gen++;
+  return HDG_OK;
+}
+
+hdg_status hdg_get_tuning(hdg_problem p, int op, int prec, int* cfg3, float* us_tuned, float* us_default) {
+  if (!p || op < 0 || op > 2 || prec < 0 || prec > 2) return HDG_ERR_ARG;
+  const BrCfg c = p->tune[op][prec];
+  if (cfg3) { cfg3[0] = c.kind; cfg3[1] = c.sp; cfg3[2] = c.cps; }
+  if (us_tuned) *us_tuned = p->tune_us[op][prec];
+  if (us_default) *us_default = p->tune_us0[op][prec];
   return HDG_OK;
 }
 

@@ -45,6 +45,7 @@ struct BlockRowDesc {
   const int32_t* cnt;     // n_units
   int64_t n_units;
   int b_rows, bc, max_slots, R;
+  int ld;                 // stored rows per block column (>= b_rows; rows past b_rows are padding)
   const double* in;
   const float* in32;      // FP32 copy of `in` (required for FP32/BF16 blocks)
   double* out;
@@ -54,7 +55,22 @@ struct BlockRowDesc {
   const int* active;      // optional: skip the launch work when all R entries are 0
   unsigned* err;
 };
-void blockrow(const BlockRowDesc& d, int variant, cudaStream_t s);
+// Launch configuration of a block-row product.  kind: BR_DEFAULT (heuristic:
+// vectorised loads for FP32/BF16 where the rows allow, else one thread per
+// row), BR_TMA (bulk-copy staging), BR_DIRECT (one thread per row), BR_VEC
+// (VR rows per thread, 16-byte loads, sp slot parts).  cps: CTAs per SM of the
+// grid-stride launch (0 = heuristic).
+enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3 };
+struct BrCfg {
+  int kind = BR_DEFAULT, sp = 0, cps = 0;
+};
+void blockrow(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s);
+// Leading dimension of FP32 / BF16 block copies: the column length rounded up
+// to a whole 16-byte vector, so that every column starts 16-byte aligned.
+inline int ld_f32(int rows) { return (rows + 3) / 4 * 4; }
+inline int ld_bf16(int rows) { return (rows + 7) / 8 * 8; }
+// valid configurations for d (at most cap); returns their number
+int blockrow_candidates(const BlockRowDesc& d, BrCfg* out, int cap);
 int blockrow_variants();
 // FP64 -> FP32 copy of a vector (rounding to nearest)
 void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
@@ -74,8 +90,8 @@ struct AssembleDesc {
   const uint8_t* face_dir;       // n_face
   const int64_t* rowptr;         // n_free + 1 compact block offsets of the face rows
   double* K64; int64_t s64;
-  float* K32; int64_t s32;
-  __nv_bfloat16* K16; int64_t s16;
+  float* K32; int64_t s32; int ld32;
+  __nv_bfloat16* K16; int64_t s16; int ld16;
   double* r;
 };
 void assemble(const AssembleDesc& d, cudaStream_t s);
@@ -85,7 +101,7 @@ void extract_diag(const double* K64, int64_t s64, const int64_t* rowptr, int b, 
                   cudaStream_t s);
 // dense row-major FP64 n x n blocks -> column-major padded blocks in the three precisions
 void pack_blocks(const double* in, int n, int64_t count, double* o64, int64_t s64, float* o32, int64_t s32,
-                 __nv_bfloat16* o16, int64_t s16, cudaStream_t s);
+                 int ld32, __nv_bfloat16* o16, int64_t s16, int ld16, cudaStream_t s);
 // ASM element matrices from Kbar: rows/cols restricted to free faces in local order
 // (compacted), diagonal blocks of interior faces replaced by K_ff, padding = identity.
 void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const int32_t* asm_lf,
@@ -93,7 +109,8 @@ void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const
                const int64_t* rowptr, double* P, cudaStream_t s);
 // ASM panels: column-major (nl*b) x b panels for the free local faces of each element
 void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, const int64_t* arowptr, double* o64,
-              int64_t s64, float* o32, int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s);
+              int64_t s64, float* o32, int64_t s32, int ld32, __nv_bfloat16* o16, int64_t s16, int ld16,
+              cudaStream_t s);
 // z_f = z^{e1}[slot s1] + z^{e2}[slot s2] (face-parallel, no atomics)
 void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum, double* z,
                   cudaStream_t s);

@@ -32,8 +32,8 @@ __global__ void assemble_kernel(AssembleDesc d) {
         if (e2 >= 0) v += d.Kbar[(int64_t)e2 * nlb * nlb + (int64_t)(l2 * b + i) * nlb + l2 * b + j];
       }
       if (d.K64) d.K64[dst * d.s64 + idx] = v;
-      if (d.K32) d.K32[dst * d.s32 + idx] = (float)v;
-      if (d.K16) d.K16[dst * d.s16 + idx] = __float2bfloat16_rn((float)v);
+      if (d.K32) d.K32[dst * d.s32 + (int64_t)j * d.ld32 + i] = (float)v;
+      if (d.K16) d.K16[dst * d.s16 + (int64_t)j * d.ld16 + i] = __float2bfloat16_rn((float)v);
     }
   }
   // right-hand side: r_f = sum over the face's elements of rbar^e_l minus the
@@ -69,14 +69,14 @@ __global__ void extract_diag_kernel(const double* K64, int64_t s64, const int64_
 }
 
 __global__ void pack_blocks_kernel(const double* in, int n, double* o64, int64_t s64, float* o32, int64_t s32,
-                                   __nv_bfloat16* o16, int64_t s16) {
+                                   int ld32, __nv_bfloat16* o16, int64_t s16, int ld16) {
   const int64_t m = blockIdx.x;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int c = idx / n, row = idx - c * n;
     const double v = in[m * n * n + (int64_t)row * n + c];
     if (o64) o64[m * s64 + idx] = v;
-    if (o32) o32[m * s32 + idx] = (float)v;
-    if (o16) o16[m * s16 + idx] = __float2bfloat16_rn((float)v);
+    if (o32) o32[m * s32 + (int64_t)c * ld32 + row] = (float)v;
+    if (o16) o16[m * s16 + (int64_t)c * ld16 + row] = __float2bfloat16_rn((float)v);
   }
 }
 
@@ -108,7 +108,8 @@ __global__ void asm_build_kernel(const double* Kbar, int nlb, int b, int nl, con
 }
 
 __global__ void asm_pack_kernel(const double* Pinv, int nlb, int b, int nl, const int64_t* arowptr, double* o64,
-                                int64_t s64, float* o32, int64_t s32, __nv_bfloat16* o16, int64_t s16) {
+                                int64_t s64, float* o32, int64_t s32, int ld32, __nv_bfloat16* o16, int64_t s16,
+                                int ld16) {
   const int64_t e = blockIdx.x;
   const int n = nlb;
   const int ns = (int)(arowptr[e + 1] - arowptr[e]);
@@ -118,8 +119,8 @@ __global__ void asm_pack_kernel(const double* Pinv, int nlb, int b, int nl, cons
       const int c = idx / n, row = idx - c * n;
       const double v = Pinv[e * (int64_t)n * n + (int64_t)row * n + s * b + c];
       if (o64) o64[panel * s64 + idx] = v;
-      if (o32) o32[panel * s32 + idx] = (float)v;
-      if (o16) o16[panel * s16 + idx] = __float2bfloat16_rn((float)v);
+      if (o32) o32[panel * s32 + (int64_t)c * ld32 + row] = (float)v;
+      if (o16) o16[panel * s16 + (int64_t)c * ld16 + row] = __float2bfloat16_rn((float)v);
     }
   }
 }
@@ -219,9 +220,9 @@ void extract_diag(const double* K64, int64_t s64, const int64_t* rowptr, int b, 
 }
 
 void pack_blocks(const double* in, int n, int64_t count, double* o64, int64_t s64, float* o32, int64_t s32,
-                 __nv_bfloat16* o16, int64_t s16, cudaStream_t s) {
+                 int ld32, __nv_bfloat16* o16, int64_t s16, int ld16, cudaStream_t s) {
   if (count <= 0) return;
-  count_launch(); pack_blocks_kernel<<<(unsigned)count, 256, 0, s>>>(in, n, o64, s64, o32, s32, o16, s16);
+  count_launch(); pack_blocks_kernel<<<(unsigned)count, 256, 0, s>>>(in, n, o64, s64, o32, s32, ld32, o16, s16, ld16);
 }
 
 void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const int32_t* asm_lf,
@@ -233,9 +234,11 @@ void asm_build(const double* Kbar, int nlb, int b, int nl, int64_t n_elem, const
 }
 
 void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, const int64_t* arowptr, double* o64,
-              int64_t s64, float* o32, int64_t s32, __nv_bfloat16* o16, int64_t s16, cudaStream_t s) {
+              int64_t s64, float* o32, int64_t s32, int ld32, __nv_bfloat16* o16, int64_t s16, int ld16,
+              cudaStream_t s) {
   if (n_elem <= 0) return;
-  count_launch(); asm_pack_kernel<<<(unsigned)n_elem, 256, 0, s>>>(Pinv, nlb, b, nl, arowptr, o64, s64, o32, s32, o16, s16);
+  count_launch(); asm_pack_kernel<<<(unsigned)n_elem, 256, 0, s>>>(Pinv, nlb, b, nl, arowptr, o64, s64, o32, s32, ld32, o16,
+                                                                   s16, ld16);
 }
 
 void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum, double* z,

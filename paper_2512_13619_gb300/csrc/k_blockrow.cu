@@ -1,533 +1,27 @@
-// Block-row products: the face-block matrix-vector product y_f = K_f x_f
-// (Sec. 4.3, each face row couples the face with the faces of its two
-// elements), the block-Jacobi apply z_f = P_f^{-1} y_f (Sec. 4.5) and the
-// element solves z^e = (Pbar^e)^{-1} y^e of the ASM apply (Sec. 4.6) all have
-// the form
-//     out[u][row] = sum_{s < cnt[u]} sum_c blk[u][s](row, c) * in[nbr[u][s]][c]
-// with dense column-major slot blocks stored compactly (unit u's blocks at
-// rowptr[u] .. rowptr[u+1]-1).  Instead of materialising the paper's extended
-// x vector, the gather goes through the neighbour table.
-//
-// Kernel "tma": a persistent CTA takes tasks (a group of G consecutive units,
-// or one unit split into slot ranges when a row is long); each task's blocks
-// are contiguous in HBM and arrive with ONE 1D bulk copy (cp.async.bulk,
-// completion by mbarrier transaction count) into a ring of shared-memory
-// stages filled by a producer warp.  Consumer thread (unit g, row, part p)
-// accumulates columns c = p, p+P, ... of every slot (column-major blocks make
-// the shared-memory reads conflict-free), gathers x through L1/L2, and the P
-// partial sums meet in shared memory before the epilogue.
-// Kernel "direct": one thread per output row with plain global loads.
-// FP32/BF16 blocks multiply an FP32 copy of x (converting each gathered FP64
-// value per product would run on the FP64 pipe, 1/57 of the FP32 rate here).
-#include <algorithm>
-#include <type_traits>
-#include "hdg_common.cuh"
-#include "hdg_internal.h"
+// Entry points of the block-row products (face-block matvec, block-Jacobi
+// apply, additive-Schwarz element solves): dispatch by block precision to the
+// per-precision units, the FP32 copy of x, and the candidate launch
+// configurations the autotuner times.  The kernels are in k_blockrow.cuh.
+#include "k_blockrow.cuh"
 
 namespace hdg {
 
+void blockrow_f64(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s);
+void blockrow_f32(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s);
+void blockrow_bf16(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s);
+
 namespace {
-
-template <typename T> struct Acc { using type = float; };
-template <> struct Acc<double> { using type = double; };
-
-__device__ __forceinline__ void epi_store(const BlockRowDesc& d, int64_t u, int row, int r, double v) {
-  const int64_t o = (u * d.b_rows + row) * d.R + r;
-  if (d.epi == EPI_RESID) v = d.rhs[o] - v;
-  else if (d.epi == EPI_SCALE) v = d.scale[r] * v;
-  d.out[o] = v;
-}
-
-__device__ __forceinline__ bool any_active(const int* active, int R) {
-  if (active == nullptr) return true;
-  for (int r = 0; r < R; ++r)
-    if (active[r]) return true;
-  return false;
-}
-
-// x in the accumulation precision: FP64 from `in`, FP32 from the FP32 copy
-template <typename A> __device__ __forceinline__ A load_x(const BlockRowDesc& d, int64_t i);
-template <> __device__ __forceinline__ double load_x<double>(const BlockRowDesc& d, int64_t i) { return __ldg(d.in + i); }
-template <> __device__ __forceinline__ float load_x<float>(const BlockRowDesc& d, int64_t i) { return __ldg(d.in32 + i); }
-
-__device__ __forceinline__ void consumer_bar(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
-
-struct Plan {
-  int G, P, S, nch, nstage, NT, NPW;   // units/task, column parts, slots/chunk, chunks/task, stages, consumers, producer warps
-  int stage_bytes;                    // bytes of one stage (blocks + gathered x + metadata)
-  int kbytes;                         // block area of a stage
-  int xoff, moff;                     // offsets of the x area and the metadata area inside a stage
-  int64_t ntasks;
-};
-
-// Stage layout: [blocks: kbytes][x: G*S*bc*R doubles][meta: G ints cnt, G ints block offset, G*S ints unused]
-template <typename T, int R>
-__global__ void __launch_bounds__(640) blockrow_tma_kernel(BlockRowDesc d, Plan pl) {
-  using A = typename Acc<T>::type;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* empty = full + pl.nstage;
-  unsigned char* stages = smem + 256;
-  A* red = reinterpret_cast<A*>(stages + (size_t)pl.nstage * pl.stage_bytes);
-  __shared__ volatile int s_abort;
-  __shared__ long long s_issued[8];   // last iteration issued on each stage (drain after an abort)
-
-  const int NT = pl.NT;
-  const int tid = threadIdx.x;
-  if (!any_active(d.active, R)) return;
-  if (tid == 0) {
-    s_abort = 0;
-    for (int i = 0; i < pl.nstage; ++i) {
-      s_issued[i] = -1;
-      mbar_init(&full[i], 32);
-      mbar_init(&empty[i], NT / 32);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
-  const T* blk = static_cast<const T*>(d.blk);
-  const int G = pl.G, P = pl.P, S = pl.S, bc = d.bc;
-  const bool whole = (pl.nch == 1);
-
-  if (tid >= NT) {
-    // ------------------------------------------------------------ producers
-    // Warp w of NPW takes the CTA's tasks k = w, w+NPW, ...  For each chunk it
-    // loads the metadata and gathers x for the chunk into the stage with plain
-    // loads, lane 0 issues one bulk copy for the blocks, and all 32 lanes
-    // arrive on the stage's full barrier (lane 0 with the byte count).
-    const int w = (tid - NT) >> 5, lane = tid & 31;
-    bool abort = false;
-    for (int64_t k = w, t = blockIdx.x + (int64_t)w * gridDim.x; t < pl.ntasks;
-         k += pl.NPW, t += (int64_t)pl.NPW * gridDim.x) {
-      const int64_t u0 = t * G;
-      const int64_t u1 = min(u0 + G, d.n_units);
-      for (int ch = 0; ch < pl.nch; ++ch) {
-        const int64_t it = k * pl.nch + ch;
-        const int st = (int)(it % pl.nstage);
-        const unsigned ph = (unsigned)((it / pl.nstage) & 1);
-        if (s_abort || !mbar_wait_bounded(&empty[st], ph ^ 1u)) {
-          if (!s_abort) atomicOr(d.err, ERRBIT_TIMEOUT);
-          s_abort = 1;
-          abort = true;
-          break;
-        }
-        unsigned char* sbase = stages + (size_t)st * pl.stage_bytes;
-        A* xs = reinterpret_cast<A*>(sbase + pl.xoff);
-        int* meta = reinterpret_cast<int*>(sbase + pl.moff);
-        const int s0 = whole ? 0 : ch * S;
-        int64_t b0, nb;
-        if (whole) {
-          b0 = d.rowptr[u0];
-          nb = d.rowptr[u1] - b0;
-        } else {
-          b0 = d.rowptr[u0] + s0;
-          nb = max(0, min(S, d.cnt[u0] - s0));
-        }
-        if (lane == 0) {
-          // register the bytes first (no arrival), then start the copy; the
-          // 32 arrivals of the warp come after the x stores below
-          const unsigned bytes = (unsigned)(nb * blk_bytes);
-          s_issued[st] = it;
-          if (bytes) {
-            mbar_expect_tx(&full[st], bytes);
-            bulk_g2s(sbase, blk + b0 * d.blk_stride, bytes, &full[st]);
-          }
-        }
-        // per-unit metadata: number of slots in this chunk and block offset in the stage
-        for (int g = lane; g < G; g += 32) {
-          const int64_t u = u0 + g;
-          int ns = 0, off = 0;
-          if (u < d.n_units) {
-            ns = whole ? d.cnt[u] : max(0, min(S, d.cnt[u] - s0));
-            off = whole ? (int)(d.rowptr[u] - b0) : 0;
-          }
-          meta[g] = ns;
-          meta[G + g] = off;
-        }
-        // gathered x of every (unit, slot in chunk, column)
-        const int per_unit = S * bc * R;
-        for (int idx = lane; idx < G * per_unit; idx += 32) {
-          const int g = idx / per_unit;
-          const int rem = idx - g * per_unit;
-          const int sl = rem / (bc * R);
-          const int cr = rem - sl * bc * R;
-          const int64_t u = u0 + g;
-          A v = (A)0;
-          if (u < d.n_units) {
-            const int ns = whole ? d.cnt[u] : min(S, d.cnt[u] - s0);
-            if (sl < ns) v = load_x<A>(d, (int64_t)d.nbr[u * d.max_slots + s0 + sl] * bc * R + cr);
-          }
-          xs[idx] = v;
-        }
-        mbar_arrive(&full[st]);  // one arrival per lane (count 32); release orders the x stores
-      }
-      if (abort) break;
-    }
-  } else {
-  // -------------------------------------------------------------- consumers
-  const int rows = G * d.b_rows;
-  const int lr = tid % rows;
-  const int part = tid / rows;
-  const int g = lr / d.b_rows;
-  const int row = lr - g * d.b_rows;
-  const int lane = tid & 31;
-  const bool in_part = part < P;
-  bool abort = false;
-  int64_t k = 0;
-  for (int64_t t = blockIdx.x; t < pl.ntasks; t += gridDim.x, ++k) {
-    const int64_t u = t * G + g;
-    A acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = (A)0;
-    for (int ch = 0; ch < pl.nch; ++ch) {
-      const int64_t it = k * pl.nch + ch;
-      const int st = (int)(it % pl.nstage);
-      const unsigned ph = (unsigned)((it / pl.nstage) & 1);
-      if (!abort && !mbar_wait_bounded(&full[st], ph)) {
-        atomicOr(d.err, ERRBIT_TIMEOUT);
-        abort = true;
-        s_abort = 1;
-      }
-      if (!abort && in_part) {
-        const unsigned char* sbase = stages + (size_t)st * pl.stage_bytes;
-        const int* meta = reinterpret_cast<const int*>(sbase + pl.moff);
-        const int ns = meta[g];
-        const T* sb = reinterpret_cast<const T*>(sbase) + (int64_t)meta[G + g] * d.blk_stride + row;
-        const A* xs = reinterpret_cast<const A*>(sbase + pl.xoff) + (int64_t)g * S * bc * R;
-        for (int sl = 0; sl < ns; ++sl) {
-          const T* bs = sb + (int64_t)sl * d.blk_stride;
-          const A* xv = xs + sl * bc * R;
-#pragma unroll 4
-          for (int c = part; c < bc; c += P) {
-            const A kv = cvt<A>(bs[c * d.b_rows]);
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = fma(kv, xv[c * R + r], acc[r]);
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);
-    }
-    if (abort) break;
-    // reduce the P column parts of each output row
-    if (P == 1) {
-      if (in_part && u < d.n_units) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) epi_store(d, u, row, r, (double)acc[r]);
-      }
-    } else {
-      if (in_part) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) red[((int64_t)part * rows + lr) * R + r] = acc[r];
-      }
-      consumer_bar(NT);
-      if (part == 0 && u < d.n_units) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          A sum = red[(int64_t)lr * R + r];
-          for (int q = 1; q < P; ++q) sum += red[((int64_t)q * rows + lr) * R + r];
-          epi_store(d, u, row, r, (double)sum);
-        }
-      }
-      consumer_bar(NT);
-    }
-  }
-  }
-  // After an abort, bulk copies may still be in flight on stages nobody
-  // consumed: wait (bounded) for them before the CTA's shared memory goes away.
-  __syncthreads();
-  if (tid == 0 && s_abort) {
-    for (int i = 0; i < pl.nstage; ++i) {
-      const long long q = s_issued[i];
-      if (q >= 0 && !mbar_wait_bounded(&full[i], (unsigned)((q / pl.nstage) & 1))) atomicOr(d.err, ERRBIT_TIMEOUT);
-    }
-  }
-}
-
-// One thread per output row; BC > 0 fixes the column count at compile time so
-// the loads of a whole slot block are in flight together.
-template <typename T, int R, int BC>
-__global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
-  using A = typename Acc<T>::type;
-  if (!any_active(d.active, R)) return;
-  const int bc = BC > 0 ? BC : d.bc;
-  const int G = blockDim.x / d.b_rows;
-  const int gu = threadIdx.x / d.b_rows;
-  const int row = threadIdx.x - gu * d.b_rows;
-  if (gu >= G) return;
-  const T* blk = static_cast<const T*>(d.blk);
-  const int64_t ngroups = (d.n_units + G - 1) / G;
-  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int64_t u = grp * G + gu;
-    if (u >= d.n_units) continue;
-    A acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = (A)0;
-    const int n = d.cnt[u];
-    const int64_t rp = d.rowptr[u];
-    const int32_t* nbr = d.nbr + u * d.max_slots;
-    for (int s = 0; s < n; ++s) {
-      const int64_t xb = (int64_t)nbr[s] * bc * R;
-      const T* bs = blk + (rp + s) * d.blk_stride + row;
-      if (BC > 0) {
-        T kv[BC > 0 ? BC : 1];
-#pragma unroll
-        for (int c = 0; c < (BC > 0 ? BC : 1); ++c) kv[c] = __ldg(bs + (size_t)c * d.b_rows);
-#pragma unroll
-        for (int c = 0; c < (BC > 0 ? BC : 1); ++c)
-#pragma unroll
-          for (int r = 0; r < R; ++r) acc[r] = fma(cvt<A>(kv[c]), load_x<A>(d, xb + c * R + r), acc[r]);
-      } else {
-#pragma unroll 4
-        for (int c = 0; c < bc; ++c) {
-          const A kv = cvt<A>(__ldg(bs + (size_t)c * d.b_rows));
-#pragma unroll
-          for (int r = 0; r < R; ++r) acc[r] = fma(kv, load_x<A>(d, xb + c * R + r), acc[r]);
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) epi_store(d, u, row, r, (double)acc[r]);
-  }
-}
-
-// FP32/BF16 blocks: each thread owns VR consecutive rows of a unit, so one
-// 16-byte load brings VR rows of a column (column-major blocks, rows
-// contiguous).  Requires b_rows % VR == 0; x comes from the FP32 copy.
-template <typename T> struct Vec16;
-template <> struct Vec16<float> {
-  static constexpr int N = 4;
-  __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-  }
-};
-template <> struct Vec16<__nv_bfloat16> {
-  static constexpr int N = 8;
-  __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
-    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = __bfloat1622float2(h[i]);
-      v[2 * i] = f.x;
-      v[2 * i + 1] = f.y;
-    }
-  }
-};
-
-// Thread (unit, row group rg, slot part sp): rows rg*VR..rg*VR+VR-1, slots
-// sp, sp+SP, ...; the SP slot parts of a row group are adjacent lanes and
-// combine their sums with shuffles.  SP in {1, 2, 4}.
-template <typename T, int R, int BC, int SP>
-__global__ void __launch_bounds__(288) blockrow_vec_kernel(BlockRowDesc d, int G) {
-  constexpr int VR = Vec16<T>::N;
-  if (!any_active(d.active, R)) return;
-  const int tpu = (d.b_rows / VR) * SP;          // threads per unit; G units per CTA,
-                                                 // threads past G*tpu only join the shuffles
-  const int gu = threadIdx.x / tpu;
-  const int q = threadIdx.x - gu * tpu;
-  const int sp = q % SP, rg = q / SP;
-  const bool valid = gu < G;
-  const T* blk = static_cast<const T*>(d.blk);
-  const int64_t ngroups = (d.n_units + G - 1) / G;
-  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int64_t u = grp * G + gu;
-    const bool act = valid && u < d.n_units;
-    float acc[VR][R];
-#pragma unroll
-    for (int v = 0; v < VR; ++v)
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[v][r] = 0.f;
-    if (act) {
-      const int n = d.cnt[u];
-      const int64_t rp = d.rowptr[u];
-      const int32_t* nbr = d.nbr + u * d.max_slots;
-      for (int s = sp; s < n; s += SP) {
-        const float* xin = d.in32 + (int64_t)nbr[s] * BC * R;
-        const T* bs = blk + (rp + s) * d.blk_stride + rg * VR;
-#pragma unroll
-        for (int c = 0; c < BC; ++c) {
-          float kv[VR];
-          Vec16<T>::load(bs + (size_t)c * d.b_rows, kv);
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float xv = __ldg(xin + c * R + r);
-#pragma unroll
-            for (int v = 0; v < VR; ++v) acc[v][r] = fmaf(kv[v], xv, acc[v][r]);
-          }
-        }
-      }
-    }
-    if (SP > 1) {
-#pragma unroll
-      for (int v = 0; v < VR; ++v)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-#pragma unroll
-          for (int o = 1; o < SP; o <<= 1) acc[v][r] += __shfl_xor_sync(0xffffffffu, acc[v][r], o);
-        }
-    }
-    if (act && sp == 0) {
-#pragma unroll
-      for (int v = 0; v < VR; ++v)
-#pragma unroll
-        for (int r = 0; r < R; ++r) epi_store(d, u, rg * VR + v, r, (double)acc[v][r]);
-    }
-  }
-}
-
 __global__ void to_f32_kernel(const double* x, float* y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
-
-int num_sms() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);  // a cached attribute query
-  return n > 0 ? n : 1;
-}
-
-constexpr size_t kStageTarget = 40 * 1024;
-constexpr size_t kSmemCap = 200 * 1024;
-
-int largest_divisor_leq(int n, int cap) {
-  for (int p = std::min(n, cap); p >= 1; --p)
-    if (n % p == 0) return p;
-  return 1;
-}
-
-template <typename T, int R>
-Plan make_plan(const BlockRowDesc& d) {
-  Plan pl{};
-  const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
-  const size_t row_bytes = (size_t)d.max_slots * blk_bytes;
-  const int nt_max = 512;
-  if (row_bytes <= kStageTarget) {
-    pl.G = (int)std::max<size_t>(1, std::min<size_t>(kStageTarget / row_bytes, (size_t)(nt_max / d.b_rows)));
-    pl.S = d.max_slots;
-    pl.nch = 1;
-    pl.kbytes = (int)(pl.G * row_bytes);
-  } else {
-    pl.G = 1;
-    pl.S = (int)std::max<size_t>(1, kStageTarget / blk_bytes);
-    if (pl.S > d.max_slots) pl.S = d.max_slots;
-    pl.nch = (d.max_slots + pl.S - 1) / pl.S;
-    pl.kbytes = (int)(pl.S * blk_bytes);
-  }
-  pl.P = largest_divisor_leq(d.bc, std::max(1, nt_max / (pl.G * d.b_rows)));
-  pl.NT = ((pl.G * d.b_rows * pl.P + 31) / 32) * 32;
-  pl.NPW = 4;
-  const size_t xbytes = (size_t)pl.G * pl.S * d.bc * R * sizeof(typename Acc<T>::type);
-  pl.xoff = (pl.kbytes + 15) / 16 * 16;
-  pl.moff = (int)((pl.xoff + xbytes + 15) / 16 * 16);
-  pl.stage_bytes = (int)((pl.moff + 2 * pl.G * sizeof(int) + 127) / 128 * 128);
-  const size_t red = (pl.P > 1) ? (size_t)pl.P * pl.G * d.b_rows * R * sizeof(typename Acc<T>::type) : 0;
-  pl.nstage = (int)std::min<size_t>(8, (kSmemCap - red) / pl.stage_bytes);
-  if (pl.nstage < 2) pl.nstage = 2;
-  pl.ntasks = (d.n_units + pl.G - 1) / pl.G;
-  return pl;
-}
-
-template <typename T, int R>
-void launch_tma(const BlockRowDesc& d, cudaStream_t s) {
-  const Plan pl = make_plan<T, R>(d);
-  const size_t red = (pl.P > 1) ? (size_t)pl.P * pl.G * d.b_rows * R * sizeof(typename Acc<T>::type) : 0;
-  const size_t smem = 256 + (size_t)pl.nstage * pl.stage_bytes + red;
-  auto kern = blockrow_tma_kernel<T, R>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);  // per context; cheap
-  const int threads = pl.NT + 32 * pl.NPW;
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = std::min<int64_t>(pl.ntasks, (int64_t)num_sms() * per_sm);
-  if (grid < 1) grid = 1;
-  count_launch(); kern<<<(unsigned)grid, threads, smem, s>>>(d, pl);
-}
-
-int pick_nt_direct(int b_rows) {
-  int best = 32 * ((b_rows + 31) / 32), bestu = -1;
-  for (int nt = best; nt <= 512; nt += 32) {
-    int util = (nt / b_rows) * b_rows * 1000 / nt;
-    if (util > bestu || (util == bestu && nt <= 256)) { bestu = util; best = nt; }
-  }
-  return best;
-}
-
-template <typename T, int R, int BC, int SP>
-void launch_vec_sp(const BlockRowDesc& d, cudaStream_t s) {
-  constexpr int VR = Vec16<T>::N;
-  const int tpu = (d.b_rows / VR) * SP;
-  const int G = std::max(1, 256 / tpu);
-  const int NT = (G * tpu + 31) / 32 * 32;        // whole warps for the full-mask shuffles
-  int64_t ngroups = (d.n_units + G - 1) / G;
-  int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * 16);
-  if (grid < 1) grid = 1;
-  count_launch(); blockrow_vec_kernel<T, R, BC, SP><<<(unsigned)grid, NT, 0, s>>>(d, G);
-}
-
-// slot parts: 4 for rows of several slots (matvec, ASM), 1 for one slot (BJ).
-// A shuffle group is SP adjacent lanes starting at a multiple of SP, so it
-// never straddles a warp.
-template <typename T, int R, int BC>
-void launch_vec(const BlockRowDesc& d, cudaStream_t s) {
-  constexpr int VR = Vec16<T>::N;
-  if (d.max_slots >= 4) launch_vec_sp<T, R, BC, 4>(d, s);
-  else if (d.max_slots >= 2) launch_vec_sp<T, R, BC, 2>(d, s);
-  else launch_vec_sp<T, R, BC, 1>(d, s);
-}
-
-template <typename T, int R, int BC>
-void launch_direct_bc(const BlockRowDesc& d, cudaStream_t s) {
-  if constexpr (!std::is_same<T, double>::value && BC > 0) {
-    if (d.b_rows % Vec16<T>::N == 0 && d.b_rows / Vec16<T>::N <= 64 && d.in32 != nullptr) {
-      launch_vec<T, R, BC>(d, s);
-      return;
-    }
-  }
-  const int NT = pick_nt_direct(d.b_rows);
-  const int G = NT / d.b_rows;
-  int64_t ngroups = (d.n_units + G - 1) / G;
-  int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * 8);
-  if (grid < 1) grid = 1;
-  count_launch(); blockrow_direct_kernel<T, R, BC><<<(unsigned)grid, NT, 0, s>>>(d);
-}
-
-template <typename T, int R>
-void launch_direct(const BlockRowDesc& d, cudaStream_t s) {
-  switch (d.bc) {
-    case 3: launch_direct_bc<T, R, 3>(d, s); break;
-    case 4: launch_direct_bc<T, R, 4>(d, s); break;
-    case 9: launch_direct_bc<T, R, 9>(d, s); break;
-    case 16: launch_direct_bc<T, R, 16>(d, s); break;
-    case 20: launch_direct_bc<T, R, 20>(d, s); break;
-    case 27: launch_direct_bc<T, R, 27>(d, s); break;
-    case 45: launch_direct_bc<T, R, 45>(d, s); break;
-    default: launch_direct_bc<T, R, 0>(d, s); break;
-  }
-}
-
-template <typename T>
-void dispatch_R(const BlockRowDesc& d, int variant, cudaStream_t s) {
-#define HDG_BR_CASE(RR)                              \
-  case RR:                                           \
-    if (variant == 1) launch_tma<T, RR>(d, s);       \
-    else launch_direct<T, RR>(d, s);                 \
-    break;
-  switch (d.R) {
-    HDG_BR_CASE(1)
-    HDG_BR_CASE(2)
-    HDG_BR_CASE(4)
-    HDG_BR_CASE(8)
-    default: break;
-  }
-#undef HDG_BR_CASE
-}
-
 }  // namespace
+
+int blockrow_candidates(const BlockRowDesc& d, BrCfg* out, int cap) {
+  if (d.prec == HDG_FP64) return candidates_T<double>(d, out, cap);
+  if (d.prec == HDG_FP32) return candidates_T<float>(d, out, cap);
+  return candidates_T<__nv_bfloat16>(d, out, cap);
+}
 
 int blockrow_variants() { return 2; }
 
@@ -538,11 +32,11 @@ void to_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
   count_launch(); to_f32_kernel<<<(unsigned)g, 256, 0, s>>>(x, y, n);
 }
 
-void blockrow(const BlockRowDesc& d, int variant, cudaStream_t s) {
+void blockrow(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
   if (d.n_units <= 0) return;
-  if (d.prec == HDG_FP64) dispatch_R<double>(d, variant, s);
-  else if (d.prec == HDG_FP32) dispatch_R<float>(d, variant, s);
-  else dispatch_R<__nv_bfloat16>(d, variant, s);
+  if (d.prec == HDG_FP64) blockrow_f64(d, cfg, s);
+  else if (d.prec == HDG_FP32) blockrow_f32(d, cfg, s);
+  else blockrow_bf16(d, cfg, s);
 }
 
 }  // namespace hdg

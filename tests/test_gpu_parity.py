@@ -20,6 +20,7 @@ SMALL = {
     'elast_R2': lambda: W.hex_elasticity(n=2, k=1, R=2),
     'cdr_M5_R4': lambda: W.hex_cdr(n=2, k=1, R=4),
     'elast_pert_k2_R8': lambda: W.hex_elasticity(n=2, k=2, R=8),
+    'cdr_k2_R4': lambda: W.hex_cdr(n=2, k=2, R=4),     # b = 45: face rows span several staging chunks
 }
 
 
@@ -302,3 +303,57 @@ def test_condense_strided_shared_blocks(shared):
     K2, r2 = p2.condensed()
     p2.close()
     assert rel(K1, K2) < 1e-13 and rel(r1, r2) < 1e-13
+
+
+@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'cdr_k2_R4'])
+def test_every_tuning_candidate_matches_oracle(name):
+    """Every launch configuration the autotuner may pick computes the same
+    block-row products: K x at each storage precision (bounds as in the
+    matvec test) and the FP64 BJ / ASM applies (1e-10 normwise, as in the
+    apply test), against the
+    oracle; then hdg_autotune picks one and the results stay within them."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w = SMALL[name]()
+    s = OracleSystem(w)
+    x = np.random.default_rng(9).standard_normal((s.K.shape[0], w.R))
+    y_ref = sparse_mv(s.K, x)
+    bound = sparse_mv(abs(s.K), np.abs(x))
+    nterm = (2 * w.n_lfe - 1) * s.bsz
+    tol = {0: None, 1: U32 + (nterm + 1) * U32, 2: U16 + (nterm + 1) * U32}
+    names = {0: 'fp64', 1: 'fp32', 2: 'bf16'}
+    # ASM inverts n_lfe*b square element matrices in shared memory (n <= 169)
+    for pc in ('bj', 'asm') if w.n_lfe * w.M * w.PF <= 169 else ('bj',):
+        o = driver.opts(pc=pc, poly_prec='bf16')
+        p = _problem(w, o)
+        p.assemble(o)
+        p.setup_precond(o)
+        if pc == 'bj':
+            Binv = precond.bj_setup(s.K, s.bsz)
+            z_ref = np.column_stack([precond.bj_apply(Binv, x[:, r]) for r in range(w.R)])
+        else:
+            subs = precond.asm_setup(s.K, s.elem_dofs)
+            z_ref = np.column_stack([precond.asm_apply(subs, x[:, r]) for r in range(w.R)])
+        ncand = 0
+        for prec in (0, 1, 2):
+            for cfg in L.hdg_tuning_candidates(p.h, 0, prec):
+                assert L.hdg_set_tuning(p.h, 0, prec, cfg) == 0
+                y = p.apply_K(x, names[prec])
+                if prec == 0:
+                    assert np.abs(y - y_ref).max() <= 1e-13 * np.abs(bound).max(), cfg
+                else:
+                    assert np.all(np.abs(y - y_ref) <= tol[prec] * bound + 1e-300), (prec, cfg)
+                ncand += 1
+        op = 1 if pc == 'bj' else 2
+        for cfg in L.hdg_tuning_candidates(p.h, op, 0):
+            assert L.hdg_set_tuning(p.h, op, 0, cfg) == 0
+            z = p.apply_precond(o, x, 'fp64')
+            assert rel(z, z_ref) < 1e-10, (pc, cfg)
+            ncand += 1
+        assert ncand > 8
+        assert L.hdg_autotune(p.h, 3, 1) == 0
+        st, cfg, us, us0 = L.hdg_get_tuning(p.h, 0, 1)
+        assert st == 0 and 0 < us <= us0
+        assert np.all(np.abs(p.apply_K(x, 'fp32') - y_ref) <= tol[1] * bound + 1e-300)
+        assert rel(p.apply_precond(o, x, 'fp64'), z_ref) < 1e-10
+        p.close()
