@@ -294,6 +294,34 @@ long long hdg_launch_count(void);
  * results agree to rounding. */
 hdg_status hdg_set_kernel_variant(hdg_problem p, int variant);
 
+/* ---------------------------------------------------------- dense products
+ * Batched FP64 GEMM, the building block of the static condensation
+ * (Sec. 4.1, Eqs. w16-w22): C_b = alpha A_b B_b + beta C_b for
+ * b = 0..count-1, row-major M x K, K x N and M x N matrices (device
+ * pointers; leading dimensions and batch strides in elements).
+ *   mode 0: FP64 CUDA cores.
+ *   mode 1: BF16 tensor cores (tcgen05) with exact operand splitting: each
+ *           row of A and column of B in 56-bit fixed point relative to its
+ *           largest entry, as 8 digits of 7 bits; digit products summed
+ *           exactly in FP32 per digit weight; the result rounded once to FP64.
+ *           The error is within a small factor of FP64 rounding,
+ *           |err_ij| <= 2^-54 K max_k|A_ik| max_k|B_kj|.  Needs K <= 192 and
+ *           N >= 16 (HDG_ERR_ARG otherwise); HDG_ERR_NAN if an input is Inf
+ *           or NaN (the result is then not defined).
+ * Mode 1 takes (M + N) * count 16-bit words of stream-ordered scratch
+ * (cudaMallocAsync).  Synchronizes `stream` to read the error word it shares
+ * with other calls of this function in the process (do not call it
+ * concurrently).  The paper
+ * condenses on the CPU; this entry point has no counterpart there. */
+hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t lda, int64_t sA, const double* B,
+                        int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
+                        int64_t count, void* stream);
+
+/* Condensation products of this problem on the tensor cores (mode 1, the
+ * default, as hdg_gemm_f64 mode 1 where K <= 192 and N >= 16) or on the FP64
+ * cores (mode 0).  HDG_ERR_ARG for another mode. */
+hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
+
 /* ---------------------------------------------------------------- autotuner
  * Launch configurations of the block-row products (the face-block matvec of
  * Sec. 4.2, the block-Jacobi apply of Sec. 4.3 and the additive-Schwarz

@@ -67,6 +67,8 @@ _SIGS = {
     'hdg_set_graphs': (_I, [_V, _I]),
     'hdg_last_error': (ctypes.c_char_p, []),
     'hdg_autotune': (_I, [_V, _I, _I, _V]),
+    'hdg_gemm_f64': (_I, [_I, _I, _I, _I, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _I64, _D, _D, _I64, _V]),
+    'hdg_set_condense_mode': (_I, [_V, _I]),
     'hdg_get_tuning': (_I, [_V, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float),
                             ctypes.POINTER(ctypes.c_float)]),
     'hdg_tuning_candidates': (_I, [_V, _I, _I, ctypes.POINTER(_I), _I]),
@@ -251,3 +253,12 @@ def hdg_tuning_candidates(p, op, prec):
 def hdg_set_tuning(p, op, prec, cfg):
     c = (_I * 3)(*cfg)
     return load().hdg_set_tuning(p, op, prec, c)
+
+
+def hdg_gemm_f64(mode, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, beta, count, stream=None):
+    return load().hdg_gemm_f64(mode, M, N, K, ptr(A), lda, sA, ptr(B), ldb, sB, ptr(C), ldc, sC, float(alpha),
+                               float(beta), count, stream_ptr(stream))
+
+
+def hdg_set_condense_mode(p, mode):
+    return load().hdg_set_condense_mode(p, mode)

@@ -162,6 +162,9 @@ struct hdg_problem_s {
   int64_t n_mv[3] = {0, 0, 0};
   std::vector<int> ev_prec;
   int br_variant = 0;              // 1: bulk-copy staging for every block-row product
+  int condense_mode = 1;           // 1: condensation GEMMs on the tensor cores, 0: FP64 cores
+  uint16_t* d_oz = nullptr;        // row / column exponents of the tensor-core products
+  int64_t oz_cap = 0;
   // autotuned launch configurations [operation: K, BJ, ASM][precision]
   BrCfg tune[3][3];
   float tune_us[3][3] = {};        // measured time of the chosen configuration
@@ -401,6 +404,13 @@ void copy_in(double* dst, const double* src, int64_t per, int64_t count, bool sh
 // Condense elements [e0, e0+ec) whose inputs are device arrays laid out as in
 // hdg.h.  sh[i] = true when input i is one block shared by every element
 // (batch stride 0 in the products).
+// Condensation products: on the BF16 tensor cores with exact operand
+// splitting (FP64-accurate) where the shape allows, else on the FP64 cores.
+void gemm_c(hdg_problem p, const GemmDesc& d, cudaStream_t s) {
+  if (p->condense_mode == 1 && gemm_ozaki_scratch(d) <= p->oz_cap && gemm_ozaki(d, p->d_oz, p->d_err, s)) return;
+  gemm_f64(d, s);
+}
+
 void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, const double* Bd, const double* Cd,
                     const double* Dm, const double* Em, const double* Fm, const double* Gm, const double* Hm,
                     const double* Jm, const double* ru, const double* ruh, const bool* sh, cudaStream_t s) {
@@ -426,37 +436,37 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
   CK(cudaMemcpyAsync(Minv, Me, sizeof(double) * nM * PE * PE, cudaMemcpyDeviceToDevice, s));
   inverse_f64(Minv, PE, (int64_t)PE * PE, nM, p->d_err, s);
   // (M^e)^{-1} B_d, (M^e)^{-1} C_d
-  gemm_f64(gd(PE, PE, PE, Minv, PE, sMe, 0, Bd, PE, sBd, PE * PE, MinvB, PE, (int64_t)D * PE * PE, PE * PE, 1.0, 0.0,
+  gemm_c(p, gd(PE, PE, PE, Minv, PE, sMe, 0, Bd, PE, sBd, PE * PE, MinvB, PE, (int64_t)D * PE * PE, PE * PE, 1.0, 0.0,
               n, D), s);
-  gemm_f64(gd(PE, nlPF, PE, Minv, PE, sMe, 0, Cd, nlPF, sCd, (int64_t)PE * nlPF, MinvC, nlPF,
+  gemm_c(p, gd(PE, nlPF, PE, Minv, PE, sMe, 0, Cd, nlPF, sCd, (int64_t)PE * nlPF, MinvC, nlPF,
               (int64_t)D * PE * nlPF, (int64_t)PE * nlPF, 1.0, 0.0, n, D), s);
   // Ebar = E - D A^{-1} B, per component block b: D[:, (b,.,.)] * stack_d (M^e)^{-1}B_d   (Eq. w19)
   copy_in(Eb, Em, (int64_t)MPE * MPE, ec, sh[4], s);
-  gemm_f64(gd(MPE, PE, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Eb, MPE,
+  gemm_c(p, gd(MPE, PE, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Eb, MPE,
               (int64_t)MPE * MPE, PE, -1.0, 1.0, n, M), s);
   // Fbar = F - D A^{-1} C, output columns (l, b, j)
   copy_in(Fb, Fm, (int64_t)MPE * nlb, ec, sh[5], s);
-  gemm_f64(gd(MPE, nlPF, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Fb, nlb,
+  gemm_c(p, gd(MPE, nlPF, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Fb, nlb,
               (int64_t)MPE * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
   // Hbar = H - G A^{-1} B                                       (Eq. w21)
   copy_in(Hb, Hm, (int64_t)nlb * MPE, ec, sh[7], s);
-  gemm_f64(gd(nlb, PE, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Hb, MPE,
+  gemm_c(p, gd(nlb, PE, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Hb, MPE,
               (int64_t)nlb * MPE, PE, -1.0, 1.0, n, M), s);
   // Jbar = J - G A^{-1} C  (written into Kbar)
   copy_in(Kb, Jm, (int64_t)nlb * nlb, ec, sh[8], s);
-  gemm_f64(gd(nlb, nlPF, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Kb, nlb,
+  gemm_c(p, gd(nlb, nlPF, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Kb, nlb,
               (int64_t)nlb * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
   // Ebar^{-1}; X_F = Ebar^{-1} Fbar; X_r = Ebar^{-1} r_u
   inverse_f64(Eb, MPE, (int64_t)MPE * MPE, ec, p->d_err, s);
-  gemm_f64(gd(MPE, nlb, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlb, (int64_t)MPE * nlb, 0, XF, nlb,
+  gemm_c(p, gd(MPE, nlb, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlb, (int64_t)MPE * nlb, 0, XF, nlb,
               (int64_t)MPE * nlb, 0, 1.0, 0.0, n, 1), s);
-  gemm_f64(gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, sru, 0, Xr, R, (int64_t)MPE * R, 0, 1.0, 0.0, n, 1),
+  gemm_c(p, gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, sru, 0, Xr, R, (int64_t)MPE * R, 0, 1.0, 0.0, n, 1),
            s);
   // Kbar = Jbar - Hbar X_F ; rbar = r_uh - Hbar X_r              (Eq. w22)
-  gemm_f64(gd(nlb, nlb, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, XF, nlb, (int64_t)MPE * nlb, 0, Kb, nlb,
+  gemm_c(p, gd(nlb, nlb, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, XF, nlb, (int64_t)MPE * nlb, 0, Kb, nlb,
               (int64_t)nlb * nlb, 0, -1.0, 1.0, n, 1), s);
   copy_in(rb, ruh, (int64_t)nlb * R, ec, sh[10], s);
-  gemm_f64(gd(nlb, R, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, Xr, R, (int64_t)MPE * R, 0, rb, R, (int64_t)nlb * R, 0,
+  gemm_c(p, gd(nlb, R, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, Xr, R, (int64_t)MPE * R, 0, rb, R, (int64_t)nlb * R, 0,
               -1.0, 1.0, n, 1), s);
 }
 
@@ -1086,6 +1096,10 @@ hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_pr
     p->chunk = ch;
     p->d_stage = (double*)p->dalloc(sizeof(double) * ch * in_sizes(p).total);
     p->d_tmp = (double*)p->dalloc(sizeof(double) * ch * tmp_per_elem(p));
+    // exponents of the largest batched product of a chunk: nb1 <= max(D, M) items
+    // per element, M + N <= 2 * max(nlb, MPE, D * PE, nlPF)
+    p->oz_cap = ch * std::max(p->D, p->M) * 2 * std::max({p->nlb, p->MPE, p->D * p->PE, p->nlPF});
+    p->d_oz = (uint16_t*)p->dalloc(sizeof(uint16_t) * p->oz_cap);
     p->s64 = padded_stride<double>((int64_t)p->b * p->b);
     p->ld32 = ld_f32(p->b);
     p->ld16 = ld_bf16(p->b);
@@ -1714,6 +1728,14 @@ long long hdg_launch_count(void) { return hdg::g_launches.load(); }
 namespace {
 constexpr int64_t kNoAllocMaxEntries = 8ll * 1024 * 1024;   // n_dof * R <= 8,388,608 (32 MiB)
 static __device__ __align__(256) float g_noalloc_x32[kNoAllocMaxEntries];
+// error word of the stand-alone GEMM entry point
+static __device__ unsigned g_gemm_err;
+cudaError_t gemm_err_word(unsigned** out) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_gemm_err);
+  *out = static_cast<unsigned*>(ptr);
+  return e;
+}
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
@@ -1786,6 +1808,45 @@ hdg_status hdg_set_graphs(hdg_problem p, int enable) {
   if (!p) return HDG_ERR_ARG;
   p->use_graphs = enable != 0;
   return HDG_OK;
+}
+
+hdg_status hdg_set_condense_mode(hdg_problem p, int mode) {
+  if (!p || mode < 0 || mode > 1) return HDG_ERR_ARG;
+  p->condense_mode = mode;
+  return HDG_OK;
+}
+
+hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t lda, int64_t sA, const double* B,
+                        int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
+                        int64_t count, void* stream) {
+  if (mode < 0 || mode > 1 || M < 1 || N < 1 || K < 1 || count < 0 || !A || !B || !C) return HDG_ERR_ARG;
+  if (lda < K || ldb < N || ldc < N || count > (1ll << 31) - 1) return HDG_ERR_ARG;
+  if (mode == 1 && (K > 192 || N < 16)) return HDG_ERR_ARG;
+  if (count == 0) return HDG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    unsigned* err = nullptr;
+    CK(gemm_err_word(&err));
+    CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    GemmDesc d = gd(M, N, K, A, lda, sA, 0, B, ldb, sB, 0, C, ldc, sC, 0, alpha, beta, (int)count, 1);
+    if (mode == 1) {
+      void* scratch = nullptr;
+      CK(cudaMallocAsync(&scratch, sizeof(uint16_t) * gemm_ozaki_scratch(d), s));
+      gemm_ozaki(d, (uint16_t*)scratch, err, s);
+      CK(cudaFreeAsync(scratch, s));
+    } else {
+      gemm_f64(d, s);
+    }
+    CK(cudaGetLastError());
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h & ERRBIT_NAN) return HDG_ERR_NAN;
+    if (h & ERRBIT_TIMEOUT) return HDG_ERR_TIMEOUT;
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  }
 }
 
 hdg_status hdg_set_kernel_variant(hdg_problem p, int variant) {

@@ -23,6 +23,12 @@ struct GemmDesc {
   int nb0, nb1;
 };
 void gemm_f64(const GemmDesc& d, cudaStream_t s);
+// The same product on the BF16 tensor cores by exact operand splitting
+// (FP64-accurate).  Returns false (nothing launched) when K > 192 or N < 16.
+// scratch: gemm_ozaki_scratch(d) 16-bit words of device memory (the row and
+// column exponents), reused after the launches complete.
+int64_t gemm_ozaki_scratch(const GemmDesc& d);
+bool gemm_ozaki(const GemmDesc& d, uint16_t* scratch, unsigned* err, cudaStream_t s);
 
 // Batched in-place inverse (Gauss-Jordan, partial pivoting) of `count`
 // n x n FP64 matrices with batch stride `stride`.  Sets ERRBIT_SINGULAR in
