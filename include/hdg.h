@@ -251,11 +251,15 @@ hdg_status hdg_get_face_rows(hdg_problem p, int64_t f0, int64_t count, double* b
  * re[0], re[1].  *n receives the count. */
 hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n);
 
-/* Event timing of the block-matvec launches (hdg_solve, hdg_apply_K and the
- * polynomial steps) while enabled: hdg_set_timing(p, 1) clears and enables,
- * hdg_get_timing returns the summed device time (ms) and launch count of the
- * matvecs with blocks in precision `kind` (HDG_FP64, HDG_FP32, HDG_BF16).
- * The events are recorded on the caller's stream around each launch. */
+/* Event timing while enabled: hdg_set_timing(p, 1) clears and enables,
+ * hdg_get_timing returns the summed device time (ms) and launch count of
+ *   kind 0-2: the block-row matvec launches (hdg_solve, hdg_apply_K and the
+ *             polynomial steps) with blocks in precision HDG_FP64, HDG_FP32,
+ *             HDG_BF16 (the block-row kernel only, not the FP32 copy of x);
+ *   kind 3:   the tensor-core condensation products of hdg_condense (each
+ *             the exponent pass plus the product kernel).
+ * The events are recorded on the caller's stream around each launch;
+ * hdg_condense then synchronizes the stream to read them. */
 hdg_status hdg_set_timing(hdg_problem p, int enable);
 hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches);
 

@@ -158,8 +158,8 @@ struct hdg_problem_s {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  double t_mv_ms[3] = {0.0, 0.0, 0.0};
-  int64_t n_mv[3] = {0, 0, 0};
+  double t_mv_ms[4] = {0.0, 0.0, 0.0, 0.0};   // [0..2] matvec per precision, [3] tensor-core GEMMs
+  int64_t n_mv[4] = {0, 0, 0, 0};
   std::vector<int> ev_prec;
   int br_variant = 0;              // 1: bulk-copy staging for every block-row product
   int condense_mode = 1;           // 1: condensation GEMMs on the tensor cores, 0: FP64 cores
@@ -406,8 +406,33 @@ void copy_in(double* dst, const double* src, int64_t per, int64_t count, bool sh
 // (batch stride 0 in the products).
 // Condensation products: on the BF16 tensor cores with exact operand
 // splitting (FP64-accurate) where the shape allows, else on the FP64 cores.
+// Event pairs around timed launches (hdg_set_timing): kind 0-2 block-row
+// products per precision, 3 tensor-core condensation products.
+void timed_begin(hdg_problem p, cudaStream_t s) {
+  if (!p->timing) return;
+  if (p->ev_used + 2 > p->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      p->ev_pool.push_back(e);
+    }
+  }
+  CK(cudaEventRecord(p->ev_pool[p->ev_used], s));
+}
+void timed_end(hdg_problem p, cudaStream_t s, int kind) {
+  if (!p->timing) return;
+  CK(cudaEventRecord(p->ev_pool[p->ev_used + 1], s));
+  p->ev_used += 2;
+  p->ev_prec.push_back(kind);
+}
+
 void gemm_c(hdg_problem p, const GemmDesc& d, cudaStream_t s) {
-  if (p->condense_mode == 1 && gemm_ozaki_scratch(d) <= p->oz_cap && gemm_ozaki(d, p->d_oz, p->d_err, s)) return;
+  if (p->condense_mode == 1 && gemm_ozaki_scratch(d) <= p->oz_cap && d.K <= 192 && d.N >= 16) {
+    timed_begin(p, s);
+    gemm_ozaki(d, p->d_oz, p->d_err, s);
+    timed_end(p, s, 3);
+    return;
+  }
   gemm_f64(d, s);
 }
 
@@ -486,24 +511,8 @@ struct Ops {
   cudaStream_t s;
   int R;
 
-  void mv_timed_begin(cudaEvent_t* a) {
-    if (!p->timing) return;
-    if (p->ev_used + 2 > p->ev_pool.size()) {
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        p->ev_pool.push_back(e);
-      }
-    }
-    *a = p->ev_pool[p->ev_used];
-    CK(cudaEventRecord(*a, s));
-  }
-  void mv_timed_end(int prec) {
-    if (!p->timing) return;
-    CK(cudaEventRecord(p->ev_pool[p->ev_used + 1], s));
-    p->ev_used += 2;
-    p->ev_prec.push_back(prec);
-  }
+  void mv_timed_begin(cudaEvent_t*) { timed_begin(p, s); }
+  void mv_timed_end(int prec) { timed_end(p, s, prec); }
 
   // y = K x (prec storage), epilogue
   void K(int prec, const double* x, double* y, int epi, const double* rhs, const double* scale, const int* active) {
@@ -1231,6 +1240,7 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
         }
       }
     }
+    collect_timing(p, s);
     p->assembled = false;
     return HDG_OK;
   } catch (const CudaError& e) {
@@ -1694,7 +1704,7 @@ hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n) 
 hdg_status hdg_set_timing(hdg_problem p, int enable) {
   if (!p) return HDG_ERR_ARG;
   p->timing = enable != 0;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     p->t_mv_ms[i] = 0.0;
     p->n_mv[i] = 0;
   }
@@ -1704,7 +1714,7 @@ hdg_status hdg_set_timing(hdg_problem p, int enable) {
 }
 
 hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches) {
-  if (!p || kind < 0 || kind > 2) return HDG_ERR_ARG;
+  if (!p || kind < 0 || kind > 3) return HDG_ERR_ARG;
   if (total_ms) *total_ms = p->t_mv_ms[kind];
   if (launches) *launches = p->n_mv[kind];
   return HDG_OK;

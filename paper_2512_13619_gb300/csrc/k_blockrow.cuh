@@ -263,6 +263,8 @@ __global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
   using A = typename Acc<T>::type;
   if (!any_active(d.active, R)) return;
   const int bc = BC > 0 ? BC : d.bc;
+  // column stride: FP64 blocks are stored unpadded (ld == b_rows)
+  const int ldb = std::is_same<T, double>::value ? d.b_rows : d.ld;
   const int G = blockDim.x / d.b_rows;
   const int gu = threadIdx.x / d.b_rows;
   const int row = threadIdx.x - gu * d.b_rows;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
       if (BC > 0) {
         T kv[BC > 0 ? BC : 1];
 #pragma unroll
-        for (int c = 0; c < (BC > 0 ? BC : 1); ++c) kv[c] = __ldg(bs + (size_t)c * d.ld);
+        for (int c = 0; c < (BC > 0 ? BC : 1); ++c) kv[c] = __ldg(bs + (size_t)c * ldb);
 #pragma unroll
         for (int c = 0; c < (BC > 0 ? BC : 1); ++c)
 #pragma unroll
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
       } else {
 #pragma unroll 4
         for (int c = 0; c < bc; ++c) {
-          const A kv = cvt<A>(__ldg(bs + (size_t)c * d.ld));
+          const A kv = cvt<A>(__ldg(bs + (size_t)c * ldb));
 #pragma unroll
           for (int r = 0; r < R; ++r) acc[r] = fma(kv, load_x<A>(d, xb + c * R + r), acc[r]);
         }

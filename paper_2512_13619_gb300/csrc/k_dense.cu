@@ -79,6 +79,61 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
   }
 }
 
+// Products with few columns (N <= 8: the right-hand-side columns of
+// Eqs. w19 and w22): one warp per output row, lanes striding over K, the N
+// partial sums reduced with shuffles.
+template <int NN>
+__global__ void __launch_bounds__(256) gemm_f64_smalln_kernel(GemmDesc d) {
+  const int z = blockIdx.x;
+  const int b0 = z / d.nb1, b1 = z % d.nb1;
+  const double* A = d.A + b0 * d.sA0 + b1 * d.sA1;
+  const double* B = d.B + b0 * d.sB0 + b1 * d.sB1;
+  double* C = d.C + b0 * d.sC0 + b1 * d.sC1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = blockIdx.y * 8 + warp; r < d.M; r += gridDim.y * 8) {
+    double acc[NN];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[j] = 0.0;
+    const double* arow = A + (int64_t)r * d.lda;
+    for (int k = lane; k < d.K; k += 32) {
+      const double a = arow[k];
+      const double* brow = B + (int64_t)k * d.ldb;
+#pragma unroll
+      for (int j = 0; j < NN; ++j)
+        if (j < d.N) acc[j] = fma(a, brow[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[j] = warp_sum(acc[j]);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < NN; ++j) {
+        if (j >= d.N) continue;
+        const int64_t cc = (int64_t)(j / d.cg) * d.cgs + (j % d.cg);
+        double* p = C + (int64_t)r * d.ldc + cc;
+        *p = (d.beta == 0.0 ? 0.0 : d.beta * *p) + d.alpha * acc[j];
+      }
+    }
+  }
+}
+
+template <int NN>
+void gemm_smalln_launch(const GemmDesc& d, cudaStream_t s) {
+  const int64_t nb = (int64_t)d.nb0 * d.nb1;
+  const int gy = (d.M + 7) / 8 < 8 ? (d.M + 7) / 8 : 8;
+  const int64_t xmax = (2147483647 / d.nb1) * d.nb1;   // launches start at a whole batch row b0
+  for (int64_t z0 = 0; z0 < nb; z0 += xmax) {
+    GemmDesc e = d;
+    const int64_t nz = nb - z0 < xmax ? nb - z0 : xmax;
+    if (z0 > 0) {
+      e.nb0 = (int)(nz / d.nb1);
+      e.A = d.A + (z0 / d.nb1) * d.sA0;
+      e.B = d.B + (z0 / d.nb1) * d.sB0;
+      e.C = d.C + (z0 / d.nb1) * d.sC0;
+    }
+    count_launch(); gemm_f64_smalln_kernel<NN><<<dim3((unsigned)nz, (unsigned)gy), 256, 0, s>>>(e);
+  }
+}
+
 // tile factor (2, 3, 4 or 6) that pads n least, preferring the larger tile on ties
 int pick_tile(int n) {
   const int cand[4] = {6, 4, 3, 2};
@@ -208,6 +263,9 @@ size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0 || d.nb0 <= 0 || d.nb1 <= 0) return;
+  if (d.N <= 2) { gemm_smalln_launch<2>(d, s); return; }
+  if (d.N <= 4) { gemm_smalln_launch<4>(d, s); return; }
+  if (d.N <= 8) { gemm_smalln_launch<8>(d, s); return; }
   const int tm = pick_tile(d.M), tn = pick_tile(d.N);
   switch (tm) {
     case 2: gemm_tn<2>(d, tn, s); break;

@@ -26,14 +26,18 @@
 // 2^-55 K 2^{e_i} 2^{f_j} in absolute value, within a small factor of the
 // FP64 rounding of a dot product; the result is rounded once to FP64.
 //
-// One 256-thread CTA computes a 128 x NT output tile (NT <= 64) of one batch
-// item.  K is staged 32 columns at a time through two shared-memory stages:
-// all threads load FP64 operands, split them into digits and write the BF16
-// digit matrices in the UMMA no-swizzle K-major layout (8 x 16-byte core
-// matrices), then one thread issues the 72 MMAs of the stage
-// (M = 128, N = NT, K = 16) and commits them to the stage's mbarrier, so the
-// split of stage c+1 overlaps the MMAs of stage c.  The 8 accumulators use
-// 8 NT TMEM columns.
+// One CTA computes a 128 x NT output tile (NT <= 64) of one batch item with
+// nine warps.  K is staged 32 columns at a time through two shared-memory
+// stages.  Warps 0-7 load the FP64 operands (the next stage's loads are in
+// flight while the current stage is split), split them into digits and
+// write the BF16 digit matrices in the UMMA no-swizzle K-major layout (8 x
+// 16-byte core matrices), then arrive on the stage's `full` mbarrier.  Warp 8
+// allocates the TMEM accumulators (8 NT columns) and one of its lanes issues
+// the stage's 72 MMAs (M = 128, N = NT, K = 16) and commits them to the
+// stage's `empty` mbarrier, so splitting and MMAs overlap.  After the last
+// stage warps 0-7 read the accumulators and form the FP64 result with
+// integer arithmetic (one rounding), so the epilogue spends at most one FP64
+// addition per output (for C += alpha A B).
 #include <algorithm>
 
 #include "hdg_common.cuh"
@@ -48,12 +52,13 @@ constexpr int kAcc = kSlices;         // accumulators D_2 .. D_9
 constexpr int kBM = 128;              // UMMA M
 constexpr int kMaxNT = 64;
 constexpr int kKC = 32;               // K per stage
-constexpr int kThreads = 256;
+constexpr int kSplitThreads = 256;        // warps 0-7: split + epilogue
+constexpr int kThreads = kSplitThreads + 32;  // + warp 8: TMEM allocation, MMA issue
 constexpr int kMaxK = 192;            // exactness bound of D_2..D_6 (see above)
 constexpr int kSliceA = kBM * kKC * 2;       // bytes of one A digit matrix per stage (8 KB)
 constexpr int kSliceB = kMaxNT * kKC * 2;    // bytes of one B digit matrix per stage (4 KB)
 constexpr int kStage = kSlices * (kSliceA + kSliceB);
-constexpr int kSmem = 2 * kStage + 1024;
+constexpr int kSmem = 2 * kStage + 1024;   // stages + barriers
 
 // UMMA shared-memory descriptor, no swizzle, K-major: core matrices of
 // 8 rows x 16 bytes; LBO = byte distance of core matrices along K, SBO =
@@ -112,52 +117,74 @@ __device__ __forceinline__ uint64_t fixed56(double x, int e) {
   return m >> (-sh);
 }
 
-// x 2^sc in FP64 for an integer |x| < 2^53, exact, assembled from its bits;
-// ok = false when the result would leave the normal range.
-__device__ __forceinline__ double i2d_scaled(long long x, int sc, bool& ok) {
-  if (x == 0) return 0.0;
-  const unsigned long long u = (unsigned long long)(x < 0 ? -x : x);
-  const int p = 63 - __clzll((long long)u);
+// Splits 8 values (one core-matrix row of 8 K entries) into the 8 digit
+// matrices: 16 bytes per digit at dst + s * slice_bytes.  A digit d (7 bits)
+// becomes the float 2^23 + d (its bits or-ed into 2^23), and one FMA with
+// the value's sign gives +-d exactly; the upper halves of two floats are the
+// two BF16 values of a 32-bit word.
+__device__ __forceinline__ void split8(const double (&v)[8], int e, unsigned char* dst, int slice_bytes) {
+  uint32_t lo[8], hi[8];
+  float sg[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t F = fixed56(v[j], e);
+    lo[j] = (uint32_t)F;
+    hi[j] = (uint32_t)(F >> 32);
+    sg[j] = (__double_as_longlong(v[j]) < 0) ? -1.0f : 1.0f;
+  }
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t f[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = 2 * q + t;
+        uint32_t x;    // bits 7 (7 - s) .. + 6 of the 56-bit F in the low bits of x
+        if (s == 0) x = hi[j] >> 17;
+        else if (s == 1) x = hi[j] >> 10;
+        else if (s == 2) x = hi[j] >> 3;
+        else if (s == 3) x = __funnelshift_r(lo[j], hi[j], 28);
+        else x = lo[j] >> (7 * (7 - s));
+        const float big = __uint_as_float((x & 127u) | 0x4B000000u);          // 2^23 + d
+        f[t] = __float_as_uint(fmaf(big, sg[j], -8388608.0f * sg[j]));       // +-d
+      }
+      w[q] = __byte_perm(f[0], f[1], 0x7632);
+    }
+    *reinterpret_cast<uint4*>(dst + (size_t)s * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// (H 2^28 + L) 2^sc rounded once to FP64 (nearest, ties to even), from the
+// integers alone; ok = false when the result would leave the normal range.
+__device__ __forceinline__ double combine_hl(long long H, long long L, int sc, bool& ok) {
+  const __int128 X = ((__int128)H << 28) + (__int128)L;      // |X| < 2^76
+  if (X == 0) return 0.0;
+  const bool neg = X < 0;
+  const unsigned __int128 U = (unsigned __int128)(neg ? -X : X);
+  const unsigned long long uh = (unsigned long long)(U >> 64), ul = (unsigned long long)U;
+  int p = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);
+  unsigned long long mant;
+  if (p <= 52) {
+    mant = ul << (52 - p);
+  } else {
+    const int sh = p - 52;                                   // 1 .. 23
+    mant = (unsigned long long)(U >> sh);
+    const unsigned long long rem = ul & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++p;
+    }
+  }
   const int ef = p + 1023 + sc;
   if (ef < 1 || ef > 2046) {
     ok = false;
     return 0.0;
   }
-  const unsigned long long bits = ((unsigned long long)(x < 0) << 63) | ((unsigned long long)ef << 52) |
-                                  ((u << (52 - p)) & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
-}
-
-// digit value +-d (0 <= d <= 127) as BF16 bits
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t neg) {
-  const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;   // exactly d
-  return (__float_as_uint(f) >> 16) | neg;
-}
-
-// Splits 8 values (one core-matrix row of 8 K entries) into the 8 digit
-// matrices: 16 bytes per digit at dst + s * slice_bytes.
-__device__ __forceinline__ void split8(const double (&v)[8], int e, unsigned char* dst, int slice_bytes,
-                                       bool& bad) {
-  uint64_t F[8];
-  uint32_t neg[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    if (exp_field(v[j]) == 0x7FF) bad = true;
-    F[j] = fixed56(v[j], e);
-    neg[j] = (uint32_t)((uint64_t)__double_as_longlong(v[j]) >> 63) << 15;
-  }
-#pragma unroll
-  for (int s = 0; s < kSlices; ++s) {
-    const int sh = 7 * (kSlices - 1 - s);
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t d0 = (uint32_t)(F[2 * q] >> sh) & 127u;
-      const uint32_t d1 = (uint32_t)(F[2 * q + 1] >> sh) & 127u;
-      w[q] = digit_bf16(d0, d0 ? neg[2 * q] : 0u) | (digit_bf16(d1, d1 ? neg[2 * q + 1] : 0u) << 16);
-    }
-    *reinterpret_cast<uint4*>(dst + (size_t)s * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)ef << 52) |
+                                          (mant & ((1ull << 52) - 1))));
 }
 
 // byte offset of (row, k) in a digit matrix with kKC K entries per row:
@@ -196,7 +223,7 @@ __global__ void __launch_bounds__(256) ozaki_exponents_kernel(GemmDesc d, uint16
 }
 
 // FP64 operands of one stage in registers: 2 core rows of A (8 K entries
-// each) and 1 core row of B per thread.
+// each) and 1 core row of B per splitting thread.
 struct StageRegs {
   double a[2][8];
   double b[8];
@@ -206,13 +233,14 @@ __device__ __forceinline__ void load_stage(const GemmDesc& d, const double* A, c
                                            int NT, int k0, int tid, StageRegs& R) {
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const int u = tid + i * kThreads;
+    const int u = tid + i * kSplitThreads;
     const int r = u >> 2, h = u & 3;
     const int gr = row0 + r;
+    if (gr >= d.M) continue;                    // padding row: zero digits, never split
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = k0 + 8 * h + j;
-      R.a[i][j] = (gr < d.M && k < d.K) ? __ldg(A + (int64_t)gr * d.lda + k) : 0.0;
+      R.a[i][j] = (k < d.K) ? __ldg(A + (int64_t)gr * d.lda + k) : 0.0;
     }
   }
   {
@@ -226,14 +254,33 @@ __device__ __forceinline__ void load_stage(const GemmDesc& d, const double* A, c
   }
 }
 
+// The 72 MMAs of one stage: K = 32 as two steps of 16; digit pair (s, t)
+// into accumulator s + t.  Descriptors differ from the stage's base
+// descriptors only in the start-address field.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int NT,
+                                            bool first) {
+#pragma unroll
+  for (int kk = 0; kk < kKC / 16; ++kk) {
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+#pragma unroll
+      for (int t = 0; s + t < kSlices; ++t) {
+        const uint64_t ad = adesc + (uint64_t)((s * kSliceA + kk * 2 * (int)kLBO) >> 4);
+        const uint64_t bd = bdesc + (uint64_t)((t * kSliceB + kk * 2 * (int)kLBO) >> 4);
+        umma_bf16(tmem + (uint32_t)((s + t) * NT), ad, bd, idesc, (first && kk == 0 && s == 0) ? 0u : 1u);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int NT, const uint16_t* ea,
                                                                   const uint16_t* fb, unsigned* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stage_base = smem;
-  int* e_row = reinterpret_cast<int*>(smem + 2 * kStage);           // [128]
-  int* f_col = e_row + kBM;                                          // [64]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(f_col + kMaxNT);       // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * kStage);   // [2] count 256: stage split
+  uint64_t* empty = full + 2;                                        // [2] count 1: stage's MMAs done
+  uint64_t* done = empty + 2;                                        // [1] count 1: all MMAs done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -244,98 +291,108 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int
   double* C = d.C + b0 * d.sC0 + b1 * d.sC1;
   const int row0 = blockIdx.y * kBM, col0 = blockIdx.x * NT;
   const int ncols_alloc = NT <= 16 ? 128 : NT <= 32 ? 256 : 512;
+  const int nch = (d.K + kKC - 1) / kKC;
+  const bool splitter = warp < kSplitThreads / 32;
 
-  // first stage's operands in flight while the CTA sets up
   StageRegs R;
-  load_stage(d, A, B, row0, col0, NT, 0, tid, R);
-
+  int e_a[2] = {0, 0}, e_b = 0;
+  if (splitter) {
+    // first stage's operands and this thread's exponents in flight during set-up
+    load_stage(d, A, B, row0, col0, NT, 0, tid, R);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = (tid + i * kSplitThreads) >> 2;
+      e_a[i] = (row0 + r < d.M) ? (int)ea[(int64_t)z * d.M + row0 + r] : 0;
+    }
+    const int n = tid % kMaxNT;
+    e_b = (n < NT && col0 + n < d.N) ? (int)fb[(int64_t)z * d.N + col0 + n] : 0;
+  }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(&full[0], kSplitThreads);
+    mbar_init(&full[1], kSplitThreads);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    mbar_init(done, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == kSplitThreads / 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(ncols_alloc)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid < kBM) e_row[tid] = (row0 + tid < d.M) ? (int)ea[(int64_t)z * d.M + row0 + tid] : 0;
-  else if (tid < kBM + kMaxNT) {
-    const int n = tid - kBM;
-    f_col[n] = (n < NT && col0 + n < d.N) ? (int)fb[(int64_t)z * d.N + col0 + n] : 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  const int nch = (d.K + kKC - 1) / kKC;
-  bool bad = false;
-  int issued = 0;                       // stages whose MMAs were issued
-  for (int c = 0; c < nch; ++c) {
-    const int st = c & 1;
-    if (c >= 2) {
-      if (!mbar_wait_bounded(&bar[st], (unsigned)(((c - 2) >> 1) & 1))) *abort_flag = 1;
-      __syncthreads();
-      if (*abort_flag) break;
-    }
-    unsigned char* sA = stage_base + (size_t)st * kStage;
-    unsigned char* sB = sA + kSlices * kSliceA;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int u = tid + i * kThreads;
-      const int r = u >> 2, h = u & 3;
-      split8(R.a[i], e_row[r], sA + core_off(r, h), kSliceA, bad);
-    }
-    {
-      const int n = tid % kMaxNT, h = tid / kMaxNT;
-      if (n < NT) split8(R.b, f_col[n], sB + core_off(n, h), kSliceB, bad);
-    }
-    // next stage's operands in flight during the MMAs of this one
-    if (c + 1 < nch) load_stage(d, A, B, row0, col0, NT, (c + 1) * kKC, tid, R);
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t idesc = instr_desc(NT);
-      const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
-#pragma unroll 1
-      for (int kk = 0; kk < kKC / 16; ++kk) {
-#pragma unroll 1
-        for (int s = 0; s < kSlices; ++s) {
-          const uint64_t ad = smem_desc(aaddr + s * kSliceA + kk * 2 * kLBO, kLBO, kSBO);
-#pragma unroll 1
-          for (int t = 0; s + t < kSlices; ++t) {
-            const uint64_t bd = smem_desc(baddr + t * kSliceB + kk * 2 * kLBO, kLBO, kSBO);
-            const int dg = s + t;                       // digit weight index: D_{s+t+2}
-            const uint32_t acc = (c > 0 || kk > 0 || s > 0) ? 1u : 0u;
-            umma_bf16(tmem + (uint32_t)(dg * NT), ad, bd, idesc, acc);
-          }
-        }
+  if (splitter) {
+    // ---------------------------------------------------------- splitters
+    // digits of the padding rows (rows >= M) of both stages: zero, once
+    const int mvalid = min(kBM, d.M - row0);
+    if (mvalid < kBM) {
+      for (int u = tid; u < 2 * kSlices * kBM * (kKC / 8); u += kSplitThreads) {
+        const int rh = u % (kBM * (kKC / 8)), ps = u / (kBM * (kKC / 8));
+        const int r = rh >> 2, h = rh & 3;
+        if (r >= mvalid)
+          *reinterpret_cast<uint4*>(stage_base + (size_t)(ps / kSlices) * kStage + (ps % kSlices) * kSliceA +
+                                    core_off(r, h)) = make_uint4(0u, 0u, 0u, 0u);
       }
-      umma_commit(&bar[st]);
     }
-    issued = c + 1;
+    for (int c = 0; c < nch; ++c) {
+      const int st = c & 1;
+      if (c >= 2 && !mbar_wait_bounded(&empty[st], (unsigned)(((c - 2) >> 1) & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      unsigned char* sA = stage_base + (size_t)st * kStage;
+      unsigned char* sB = sA + kSlices * kSliceA;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int u = tid + i * kSplitThreads;
+        if ((u >> 2) < mvalid) split8(R.a[i], e_a[i], sA + core_off(u >> 2, u & 3), kSliceA);
+      }
+      {
+        const int n = tid % kMaxNT, h = tid / kMaxNT;
+        if (n < NT) split8(R.b, e_b, sB + core_off(n, h), kSliceB);
+      }
+      if (c + 1 < nch) load_stage(d, A, B, row0, col0, NT, (c + 1) * kKC, tid, R);   // in flight during the MMAs
+      fence_async_smem();
+      mbar_arrive(&full[st]);
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------- MMA issue
+    const uint32_t idesc = instr_desc(NT);
+    for (int c = 0; c < nch; ++c) {
+      const int st = c & 1;
+      if (!mbar_wait_bounded(&full[st], (unsigned)((c >> 1) & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      tc_fence_after();
+      const uint32_t aaddr = smem_u32(stage_base + (size_t)st * kStage);
+      const uint32_t baddr = aaddr + kSlices * kSliceA;
+      issue_stage(tmem, smem_desc(aaddr, kLBO, kSBO), smem_desc(baddr, kLBO, kSBO), idesc, NT, c == 0);
+      umma_commit(&empty[st]);
+    }
+    umma_commit(done);   // covers every MMA issued above (also after an abort)
   }
-  if (bad) atomicOr(err, ERRBIT_NAN);
-  // all MMAs done (the last commit covers every earlier MMA of the thread);
-  // after an abort this still waits, bounded, for the MMAs in flight
-  if (issued > 0) {
-    if (!mbar_wait_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1))) *abort_flag = 1;
-  }
-  __syncthreads();
+  // all issued MMAs complete before TMEM is read or freed
+  if (!mbar_wait_bounded(done, 0u)) *abort_flag = 1;
   tc_fence_after();
+  __syncthreads();
   if (*abort_flag) {
     if (tid == 0) atomicOr(err, ERRBIT_TIMEOUT);
-  } else {
+  } else if (splitter) {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows),
     // columns [half * NT / 2, (half + 1) * NT / 2) in groups of 8
     const int lg = warp & 3, half = warp >> 2;
     const int r = lg * 32 + lane;
     const int gr = row0 + r;
-    const int ea = e_row[r];
+    const int ea_r = (gr < d.M) ? (int)ea[(int64_t)z * d.M + gr] : 0;
     // alpha / beta cases: 0: C = AB, 1: C -= AB, 2: general
     const int ab = (d.alpha == 1.0 && d.beta == 0.0) ? 0 : (d.alpha == -1.0 && d.beta == 1.0) ? 1 : 2;
     for (int cb = half * (NT / 2); cb < (half + 1) * (NT / 2); cb += 8) {
@@ -359,15 +416,14 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int
         for (int j = 0; j < 8; ++j) {
           const int gc = col0 + cb + j;
           if (cb + j >= NT || gc >= d.N) continue;
-          const int fb = f_col[cb + j];
+          const int fbj = (int)fb[(int64_t)z * d.N + gc];
           double val = 0.0;
-          if (ea > 0 && fb > 0) {
-            // (H 2^28 + L) 2^E: both parts exact in FP64, one rounding in the sum
-            const int E = ea + fb - 2107;
+          if (ea_r > 0 && fbj > 0) {
+            // (H 2^28 + L) 2^E with E = ea + fb - 2107, one rounding
             bool ok = true;
-            val = i2d_scaled(H[j], E + 28, ok) + i2d_scaled(L[j], E, ok);
+            val = combine_hl(H[j], L[j], ea_r + fbj - 2107, ok);
             if (!ok) {   // outside the normal range: scale step by step
-              const int p1 = ea - 1054, p2 = fb - 1053;
+              const int p1 = ea_r - 1054, p2 = fbj - 1053;
               const double s1 = (p1 >= -1022) ? __longlong_as_double((long long)(p1 + 1023) << 52) : 0.0;
               const double s2 = (p2 >= -1022) ? __longlong_as_double((long long)(p2 + 1023) << 52) : 0.0;
               val = (fma((double)H[j], 268435456.0, (double)L[j]) * s1) * s2;
@@ -384,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == kSplitThreads / 32) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols_alloc) : "memory");
   }
 }
