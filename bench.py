@@ -47,7 +47,7 @@ def parse():
     ap.add_argument('--serving-requests', type=int, default=512,
                     help='requests of the serving stream timed beside the step (0: none)')
     ap.add_argument('--lanes', type=int, default=4, help='concurrent requests of the serving loop')
-    ap.add_argument('--serving-budget-gb', type=float, default=64.0)
+    ap.add_argument('--serving-budget-gb', type=float, default=160.0)
     ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
     ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
     ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40'], default='poisson16',

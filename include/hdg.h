@@ -311,9 +311,18 @@ hdg_status hdg_set_kernel_variant(hdg_problem p, int variant);
  *           The error is within a small factor of FP64 rounding,
  *           |err_ij| <= 2^-54 K max_k|A_ik| max_k|B_kj|.  Needs K <= 192 and
  *           N >= 16 (HDG_ERR_ARG otherwise); HDG_ERR_NAN if an input is Inf
- *           or NaN (the result is then not defined).
- * Mode 1 takes (M + N) * count 16-bit words of stream-ordered scratch
- * (cudaMallocAsync).  Synchronizes `stream` to read the error word it shares
+ *           or NaN (the result is then not defined).  The digits are
+ *           computed inside the product kernel for every output tile from the
+ *           FP64 operands ((M + N) * count 16-bit words of stream-ordered
+ *           scratch from cudaMallocAsync).
+ *   mode 2: as mode 1, with each operand split once into BF16 digit planes
+ *           in device memory (16 bytes per entry, twice the FP64 operand)
+ *           that the product kernel moves with bulk copies; the same
+ *           results, slower at the condensation shapes (the plane traffic
+ *           bounds it).
+ *   mode 3: as mode 1 with one persistent CTA per SM walking all output
+ *           tiles (accumulators double-buffered in TMEM for 32-column
+ *           tiles); the same results, slower at the condensation shapes.  Synchronizes `stream` to read the error word it shares
  * with other calls of this function in the process (do not call it
  * concurrently).  The paper
  * condenses on the CPU; this entry point has no counterpart there. */
@@ -322,8 +331,10 @@ hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t 
                         int64_t count, void* stream);
 
 /* Condensation products of this problem on the tensor cores (mode 1, the
- * default, as hdg_gemm_f64 mode 1 where K <= 192 and N >= 16) or on the FP64
- * cores (mode 0).  HDG_ERR_ARG for another mode. */
+ * default, 2 or 3, as hdg_gemm_f64 modes 1-3, where K <= 192 and N >= 16)
+ * or on the FP64 cores (mode 0).  Mode 2 keeps a digit-plane buffer of the
+ * largest product of a condensation chunk (grown on first use).
+ * HDG_ERR_ARG for another mode. */
 hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
 
 /* ---------------------------------------------------------------- autotuner

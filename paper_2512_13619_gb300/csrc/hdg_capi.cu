@@ -162,9 +162,14 @@ struct hdg_problem_s {
   int64_t n_mv[4] = {0, 0, 0, 0};
   std::vector<int> ev_prec;
   int br_variant = 0;              // 1: bulk-copy staging for every block-row product
-  int condense_mode = 1;           // 1: condensation GEMMs on the tensor cores, 0: FP64 cores
+  int condense_mode = 1;           // condensation GEMMs: 1 tensor cores (digits split per tile), 2 digit
+                                   // planes in device memory, 3 persistent CTAs, 0 FP64 cores
   uint16_t* d_oz = nullptr;        // row / column exponents of the tensor-core products
   int64_t oz_cap = 0;
+  unsigned char* d_planes = nullptr;   // digit planes of the operands (grown on demand)
+  int64_t planes_cap = 0;
+  uint16_t* d_pex = nullptr;
+  int64_t pex_cap = 0;
   // autotuned launch configurations [operation: K, BJ, ASM][precision]
   BrCfg tune[3][3];
   float tune_us[3][3] = {};        // measured time of the chosen configuration
@@ -427,9 +432,34 @@ void timed_end(hdg_problem p, cudaStream_t s, int kind) {
 }
 
 void gemm_c(hdg_problem p, const GemmDesc& d, cudaStream_t s) {
-  if (p->condense_mode == 1 && gemm_ozaki_scratch(d) <= p->oz_cap && d.K <= 192 && d.N >= 16) {
+  if (p->condense_mode == 2) {
+    int64_t exw = 0;
+    const int64_t need = gemm_planes_bytes(d, &exw);
+    if (need >= 0) {
+      if (need > p->planes_cap) {
+        p->dfree(p->d_planes, (size_t)p->planes_cap);
+        p->d_planes = nullptr;
+        p->planes_cap = 0;
+        p->d_planes = (unsigned char*)p->dalloc((size_t)need);
+        p->planes_cap = need;
+      }
+      if (exw > p->pex_cap) {
+        p->dfree(p->d_pex, sizeof(uint16_t) * (size_t)p->pex_cap);
+        p->d_pex = nullptr;
+        p->pex_cap = 0;
+        p->d_pex = (uint16_t*)p->dalloc(sizeof(uint16_t) * (size_t)exw);
+        p->pex_cap = exw;
+      }
+      timed_begin(p, s);
+      const bool ok = gemm_ozaki_planes(d, p->d_planes, p->planes_cap, p->d_pex, p->pex_cap, p->d_err, s);
+      timed_end(p, s, 3);
+      if (ok) return;
+    }
+  }
+  if (p->condense_mode >= 1 && gemm_ozaki_scratch(d) <= p->oz_cap && d.K <= 192 && d.N >= 16) {
     timed_begin(p, s);
-    gemm_ozaki(d, p->d_oz, p->d_err, s);
+    if (p->condense_mode == 3) gemm_ozaki_persist(d, p->d_oz, p->oz_cap, p->d_err, s);
+    else gemm_ozaki(d, p->d_oz, p->d_err, s);
     timed_end(p, s, 3);
     return;
   }
@@ -1821,7 +1851,7 @@ hdg_status hdg_set_graphs(hdg_problem p, int enable) {
 }
 
 hdg_status hdg_set_condense_mode(hdg_problem p, int mode) {
-  if (!p || mode < 0 || mode > 1) return HDG_ERR_ARG;
+  if (!p || mode < 0 || mode > 3) return HDG_ERR_ARG;
   p->condense_mode = mode;
   return HDG_OK;
 }
@@ -1829,9 +1859,9 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode) {
 hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t lda, int64_t sA, const double* B,
                         int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
                         int64_t count, void* stream) {
-  if (mode < 0 || mode > 1 || M < 1 || N < 1 || K < 1 || count < 0 || !A || !B || !C) return HDG_ERR_ARG;
+  if (mode < 0 || mode > 3 || M < 1 || N < 1 || K < 1 || count < 0 || !A || !B || !C) return HDG_ERR_ARG;
   if (lda < K || ldb < N || ldc < N || count > (1ll << 31) - 1) return HDG_ERR_ARG;
-  if (mode == 1 && (K > 192 || N < 16)) return HDG_ERR_ARG;
+  if (mode >= 1 && (K > 192 || N < 16)) return HDG_ERR_ARG;
   if (count == 0) return HDG_OK;
   cudaStream_t s = (cudaStream_t)stream;
   try {
@@ -1839,10 +1869,22 @@ hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t 
     CK(gemm_err_word(&err));
     CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
     GemmDesc d = gd(M, N, K, A, lda, sA, 0, B, ldb, sB, 0, C, ldc, sC, 0, alpha, beta, (int)count, 1);
-    if (mode == 1) {
+    if (mode == 2) {
+      int64_t exw = 0;
+      const int64_t need = gemm_planes_bytes(d, &exw);
+      void* planes = nullptr;
+      void* exs = nullptr;
+      CK(cudaMallocAsync(&planes, (size_t)need, s));
+      CK(cudaMallocAsync(&exs, sizeof(uint16_t) * (size_t)exw, s));
+      gemm_ozaki_planes(d, (unsigned char*)planes, need, (uint16_t*)exs, exw, err, s);
+      CK(cudaFreeAsync(planes, s));
+      CK(cudaFreeAsync(exs, s));
+    } else if (mode == 1 || mode == 3) {
       void* scratch = nullptr;
-      CK(cudaMallocAsync(&scratch, sizeof(uint16_t) * gemm_ozaki_scratch(d), s));
-      gemm_ozaki(d, (uint16_t*)scratch, err, s);
+      const int64_t words = gemm_ozaki_scratch(d);
+      CK(cudaMallocAsync(&scratch, sizeof(uint16_t) * words, s));
+      if (mode == 3) gemm_ozaki_persist(d, (uint16_t*)scratch, words, err, s);
+      else gemm_ozaki(d, (uint16_t*)scratch, err, s);
       CK(cudaFreeAsync(scratch, s));
     } else {
       gemm_f64(d, s);

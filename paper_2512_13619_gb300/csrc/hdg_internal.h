@@ -29,6 +29,17 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s);
 // column exponents), reused after the launches complete.
 int64_t gemm_ozaki_scratch(const GemmDesc& d);
 bool gemm_ozaki(const GemmDesc& d, uint16_t* scratch, unsigned* err, cudaStream_t s);
+// The same product with each operand split once into BF16 digit planes in
+// device memory (gemm_planes_bytes(d, &ex_words) plane bytes and ex_words
+// 16-bit words of scratch; -1 outside K <= 192, N >= 16), then bulk-copied
+// into the tensor-core product kernel.  False when the scratch is too small.
+int64_t gemm_planes_bytes(const GemmDesc& d, int64_t* ex_words);
+// Persistent variant of gemm_ozaki (one CTA per SM over all 128 x 32 tiles,
+// accumulators double-buffered in TMEM); scratch as gemm_ozaki_scratch.
+bool gemm_ozaki_persist(const GemmDesc& d, uint16_t* scratch, int64_t scratch_words, unsigned* err,
+                        cudaStream_t s);
+bool gemm_ozaki_planes(const GemmDesc& d, unsigned char* planes, int64_t planes_cap, uint16_t* ex, int64_t ex_cap,
+                       unsigned* err, cudaStream_t s);
 
 // Batched in-place inverse (Gauss-Jordan, partial pivoting) of `count`
 // n x n FP64 matrices with batch stride `stride`.  Sets ERRBIT_SINGULAR in

@@ -39,7 +39,7 @@ def _run(mode, A, B, C0, alpha, beta):
 
 
 @pytest.mark.parametrize('shape', SHAPES)
-@pytest.mark.parametrize('mode', [0, 1])
+@pytest.mark.parametrize('mode', [0, 1, 2, 3])
 def test_gemm_matches_fp64_product(shape, mode):
     """|C - (alpha A B + beta C0)| <= 2^-50 K |alpha| max_k|A_ik| max_k|B_kj|
     + 2^-50 (|beta C0| + |alpha| (|A||B|)): FP64-level accuracy (the
@@ -47,7 +47,7 @@ def test_gemm_matches_fp64_product(shape, mode):
     is bounded by K 2^-53 (|A||B|))."""
     need_gpu()
     M, N, K = shape
-    if mode == 1 and (K > 192 or N < 16):
+    if mode >= 1 and (K > 192 or N < 16):
         pytest.skip('outside the tensor-core shapes')
     A, B, C0 = _inputs(M, N, K, 3, M * 7919 + N * 31 + K)
     amax = np.abs(A).max(axis=2)[:, :, None]
@@ -65,7 +65,8 @@ def test_gemm_matches_fp64_product(shape, mode):
     print('shape', shape, 'mode', mode, 'max |err| / (K 2^-53 maxA maxB) =', worst)
 
 
-def test_gemm_tensor_exact_on_integers():
+@pytest.mark.parametrize('mode', [1, 2, 3])
+def test_gemm_tensor_exact_on_integers(mode):
     """Small integers are represented exactly by the digits, and their
     products and sums (< 2^53) are exact: the tensor-core result equals the
     integer product."""
@@ -74,46 +75,49 @@ def test_gemm_tensor_exact_on_integers():
     A = rng.integers(-1000, 1001, (2, 96, 192)).astype(float)
     B = rng.integers(-1000, 1001, (2, 192, 64)).astype(float)
     C0 = np.zeros((2, 96, 64))
-    st, C = _run(1, A, B, C0, 1.0, 0.0)
+    st, C = _run(mode, A, B, C0, 1.0, 0.0)
     assert st == 0
     assert np.array_equal(C, A @ B)
 
 
-def test_gemm_tensor_zero_rows_and_nan():
+@pytest.mark.parametrize('mode', [1, 2, 3])
+def test_gemm_tensor_zero_rows_and_nan(mode):
     """An all-zero row gives an exact zero row; an Inf/NaN input is reported
     (HDG_ERR_NAN); K > 192 or N < 16 is rejected on the tensor path."""
     need_gpu()
     from paper_2512_13619_gb300 import _lib as L
     A, B, C0 = _inputs(64, 32, 64, 1, 5)
     A[0, 7, :] = 0.0
-    st, C = _run(1, A, B, C0, 1.0, 0.0)
+    st, C = _run(mode, A, B, C0, 1.0, 0.0)
     assert st == 0 and np.all(C[0, 7] == 0.0)
     assert rel(C, A @ B) < 1e-14
     A[0, 3, 5] = np.nan
-    st, _ = _run(1, A, B, C0, 1.0, 0.0)
+    st, _ = _run(mode, A, B, C0, 1.0, 0.0)
     assert st == L.HDG_ERR_NAN
     A2, B2, C2 = _inputs(64, 32, 193, 1, 6)
-    st, _ = _run(1, A2, B2, C2, 1.0, 0.0)
+    st, _ = _run(mode, A2, B2, C2, 1.0, 0.0)
     assert st == L.HDG_ERR_ARG
     A3, B3, C3 = _inputs(64, 8, 64, 1, 7)
-    st, _ = _run(1, A3, B3, C3, 1.0, 0.0)
+    st, _ = _run(mode, A3, B3, C3, 1.0, 0.0)
     assert st == L.HDG_ERR_ARG
 
 
 def test_condensation_tensor_equals_fp64_cores():
-    """Condensation (Eqs. w16-w22) with the tensor-core products equals the
-    one on the FP64 cores to 1e-13 (both against the same inputs)."""
+    """Condensation (Eqs. w16-w22) with the tensor-core products (digits per
+    tile, or digit planes) equals the one on the FP64 cores to 1e-13 (all
+    against the same inputs)."""
     need_gpu()
     from hdg_inputs import workloads as W
     from paper_2512_13619_gb300 import driver, _lib as L
     w = W.hex_poisson(n=3, k=3)
     blk = w.blocks()
     out = []
-    for mode in (0, 1):
+    for mode in (0, 1, 2, 3):
         p = driver.Problem.from_workload(w)
         assert L.hdg_set_condense_mode(p.h, mode) == 0
         p.condense(blk)
         out.append(p.condensed())
         p.close()
-    assert rel(out[1][0], out[0][0]) < 1e-13
-    assert rel(out[1][1], out[0][1]) < 1e-13
+    for m in (1, 2, 3):
+        assert rel(out[m][0], out[0][0]) < 1e-13
+        assert rel(out[m][1], out[0][1]) < 1e-13
