@@ -67,6 +67,13 @@ def peaks():
         return {'hbm_gbs': 6800.0, 'bf16_tflops': 1900.0, '_fallback': True}
 
 
+# DRAM read + write of the tensor-core condensation products of one 16^3 Q3
+# condensation: ncu capture of the 8 launches of the same kernel on the 8^3
+# Q3 case (512 elements, 900.2 MB read + 96.6 MB written), scaled by the
+# element count (x 8).  Taken with the kernel as committed; to be set to None
+# when the kernel changes.
+OZAKI_DRAM_BYTES_PER_CONDENSATION = int((900.2e6 + 96.6e6) * 8)
+
 # FP64 ALU peak: 152 SMs x 2.07 GHz x 4 FP64 FLOP/clk/SM (nominal 1.25 TFLOP/s)
 FP64_ALU_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 
@@ -129,6 +136,19 @@ def dist_setup():
     rank = int(os.environ.get('RANK', '0'))
     local = int(os.environ.get('LOCAL_RANK', '0'))
     return ws, rank, local
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """The largest `value` over the ranks of the process group (the value
+    itself without one): every rank times its own replica, the job's time is
+    the slowest rank's.  NCCL reduces a device tensor, gloo a host tensor."""
+    if dist is None:
+        return float(value)
+    import torch
+    dev = device if dist.get_backend() == 'nccl' else 'cpu'
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def condense_flops(w):
@@ -231,10 +251,7 @@ def run_ours(args, ws, rank, local):
             ph['recover'] += ev[2].elapsed_time(ev[3]) / K
         tm = [L.hdg_get_timing(p.h, kind) for kind in range(3)]
         L.hdg_set_timing(p.h, 0)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return ms, ph, (n1 - n0) / K, tm
 
     o_fp64_10 = driver.opts(restart=50, rtol=1e-10, pc='bj', inner='fp64', max_iters=5000)
@@ -313,10 +330,7 @@ def run_ours(args, ws, rank, local):
             e2e_step()
         torch.cuda.synchronize(dev)
         e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e_ms, dist, dev)
         out_bytes = (uh_host.numel() + u_host.numel() + q_host.numel()) * 8
         e2e = {'value': round(e_ms, 3), 'unit': 'ms', 'h2d_bytes_per_step': int(in_bytes),
                'd2h_bytes_per_step': int(out_bytes)}
@@ -342,7 +356,9 @@ def run_ours(args, ws, rank, local):
     roof = {'kernel': 'gemm_ozaki_kernel (+ its exponent pass): FP64-accurate condensation products on the '
                       'BF16 tensor cores, 36 digit products per FP64 product',
             'bound': 'tensor', 'achieved': round(achieved, 2), 'peak': pk['bf16_tflops'],
-            'unit': 'TFLOP/s', 'frac': round(achieved / pk['bf16_tflops'], 4), 'traffic': None,
+            'unit': 'TFLOP/s', 'frac': round(achieved / pk['bf16_tflops'], 4),
+            'traffic': OZAKI_DRAM_BYTES_PER_CONDENSATION if (args.n, args.k) == (16, 3) else None,
+            'traffic_unit': 'DRAM bytes per condensation (all 32 launches)',
             'flops_per_step': int(tc_flops), 'ms_per_step': round(tc_ms_step, 3),
             'launches_per_step': tc_n // args.steps,
             'peak_source': 'MEASURED_PEAKS.json bf16_tflops (burst; the products are timed in their own loop)'
