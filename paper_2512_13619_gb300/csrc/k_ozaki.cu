@@ -118,39 +118,49 @@ __device__ __forceinline__ uint64_t fixed56(double x, int e) {
 }
 
 // Splits 8 values (one core-matrix row of 8 K entries) into the 8 digit
-// matrices: 16 bytes per digit at dst + s * slice_bytes.  A digit d (7 bits)
-// becomes the float 2^23 + d (its bits or-ed into 2^23), and one FMA with
-// the value's sign gives +-d exactly; the upper halves of two floats are the
-// two BF16 values of a 32-bit word.
+// matrices: 16 bytes per digit at dst + s * slice_bytes.  The digits d0, d1
+// (7 bits each) of two neighbouring values are placed in one 32-bit word as
+// the BF16 bit patterns of 128 + d (0x4300 | d, exact), and one packed BF16
+// FMA with the values' signs, (128 + d) s - 128 s = s d, gives both digits
+// exactly.
 __device__ __forceinline__ void split8(const double (&v)[8], int e, unsigned char* dst, int slice_bytes) {
   uint32_t lo[8], hi[8];
-  float sg[8];
+  __nv_bfloat162 sg[4], off[4];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint64_t F = fixed56(v[j], e);
     lo[j] = (uint32_t)F;
     hi[j] = (uint32_t)(F >> 32);
-    sg[j] = (__double_as_longlong(v[j]) < 0) ? -1.0f : 1.0f;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    // packed signs (+-1) and offsets (-+128) of values 2q, 2q+1 (bf16 bits)
+    const uint32_t s0 = (uint32_t)((unsigned long long)__double_as_longlong(v[2 * q]) >> 63);
+    const uint32_t s1 = (uint32_t)((unsigned long long)__double_as_longlong(v[2 * q + 1]) >> 63);
+    const uint32_t sb = 0x3F803F80u | (s0 << 15) | (s1 << 31);           // (+-1, +-1)
+    const uint32_t ob = 0xC300C300u ^ ((s0 << 15) | (s1 << 31));         // (-+128, -+128)
+    sg[q] = *reinterpret_cast<const __nv_bfloat162*>(&sb);
+    off[q] = *reinterpret_cast<const __nv_bfloat162*>(&ob);
   }
 #pragma unroll
   for (int s = 0; s < kSlices; ++s) {
     uint32_t w[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      uint32_t f[2];
+      uint32_t x[2];    // bits 7 (7 - s) .. + 6 of the 56-bit F in the low byte of x
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int j = 2 * q + t;
-        uint32_t x;    // bits 7 (7 - s) .. + 6 of the 56-bit F in the low bits of x
-        if (s == 0) x = hi[j] >> 17;
-        else if (s == 1) x = hi[j] >> 10;
-        else if (s == 2) x = hi[j] >> 3;
-        else if (s == 3) x = __funnelshift_r(lo[j], hi[j], 28);
-        else x = lo[j] >> (7 * (7 - s));
-        const float big = __uint_as_float((x & 127u) | 0x4B000000u);          // 2^23 + d
-        f[t] = __float_as_uint(fmaf(big, sg[j], -8388608.0f * sg[j]));       // +-d
+        if (s == 0) x[t] = hi[j] >> 17;
+        else if (s == 1) x[t] = hi[j] >> 10;
+        else if (s == 2) x[t] = hi[j] >> 3;
+        else if (s == 3) x[t] = __funnelshift_r(lo[j], hi[j], 28);
+        else x[t] = lo[j] >> (7 * (7 - s));
       }
-      w[q] = __byte_perm(f[0], f[1], 0x7632);
+      // low bytes of x[0], x[1] into bytes 0 and 2, 7-bit fields, 128 + d as BF16
+      const uint32_t pk = (__byte_perm(x[0], x[1], 0x4400) & 0x007F007Fu) | 0x43004300u;
+      const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162*>(&pk), sg[q], off[q]);
+      w[q] = *reinterpret_cast<const uint32_t*>(&r);
     }
     *reinterpret_cast<uint4*>(dst + (size_t)s * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
   }
