@@ -104,7 +104,12 @@ typedef struct {
  *               Krylov basis, Gram-Schmidt and Givens stay in FP64
  *  poly_prec    storage precision of K inside the polynomial smoother
  *  inner_rtol   relative tolerance of each inner solve in mixed mode
- *  max_outer    refinement-step cap in mixed mode */
+ *  max_outer    refinement-step cap in mixed mode; -1 selects the restarted
+ *               mixed mode instead: one restarted GMRES whose cycles (matvecs
+ *               and preconditioner) run on the inner_prec blocks while every
+ *               restart recomputes the true residual with the FP64 blocks,
+ *               so convergence is judged in FP64 and no inner solves are
+ *               nested */
 typedef struct {
   int restart;
   int max_iters;

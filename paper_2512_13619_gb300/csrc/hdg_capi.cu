@@ -1500,8 +1500,12 @@ hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* o, void* stream, hdg_
     p->ev_used = 0;
     hdg_solve_info inf{};
     hdg_status st = HDG_OK;
-    if (o->inner_prec == HDG_FP64) {
-      GmresResult g = gmres(p, *o, HDG_FP64, HDG_FP64, HDG_FP64, p->d_r, p->d_x, o->rtol, o->max_iters, 1, s);
+    if (o->inner_prec == HDG_FP64 || o->max_outer == -1) {
+      // plain FP64 GMRES; or (max_outer = -1) one restarted GMRES whose cycles
+      // run on the low-precision blocks and restart from the FP64 residual
+      const int kp = o->inner_prec;
+      const int pp = (kp != HDG_FP64 && o->poly_prec == HDG_BF16) ? HDG_BF16 : kp;
+      GmresResult g = gmres(p, *o, kp, kp, pp, p->d_r, p->d_x, o->rtol, o->max_iters, 1, s);
       inf.iters = g.iters;
       inf.restarts = g.restarts;
       inf.converged = g.converged ? 1 : 0;
