@@ -1195,6 +1195,9 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
     const int64_t tmp = PE * PE + MPE * MPE + MPE * nlb + nlb * MPE;
     const int64_t ch = std::max<int64_t>(1, std::min<int64_t>((1ll << 30) / ((in_total + tmp) * 8), NE));
     by += ch * (in_total + tmp) * 8 + (16ll << 20);               // + small per-call buffers
+    // exponents of the tensor-core products (16-bit, as hdg_problem_create sizes them)
+    const int64_t mx = std::max({nlb, MPE, D * PE, nl * (int64_t)mesh->PF});
+    by += ch * std::max<int64_t>(D, mesh->M) * 2 * mx * 2;
   }
   by += nfree * ms * b * b * (8 + 4);                             // K in FP64 + FP32
   if (opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16)) by += nfree * ms * b * b * 2;
