@@ -47,6 +47,8 @@ def parse():
     ap.add_argument('--serving-requests', type=int, default=512,
                     help='requests of the serving stream timed beside the step (0: none)')
     ap.add_argument('--lanes', type=int, default=4, help='concurrent requests of the serving loop')
+    ap.add_argument('--serving-mixed', choices=['refinement', 'restarted'], default='restarted',
+                    help='mixed-precision mode of the serving solves')
     ap.add_argument('--serving-budget-gb', type=float, default=160.0)
     ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
     ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
@@ -418,7 +420,8 @@ def serving_leg(args, local):
     from hdg_inputs import workloads as W
     from paper_2512_13619_gb300 import driver
     from paper_2512_13619_gb300.serving import HdgBackend, Server
-    o = driver.opts(restart=30, rtol=1e-8, pc='bj', inner='fp32', inner_rtol=1e-4, max_iters=20000)
+    o = driver.opts(restart=30, rtol=1e-8, pc='bj', inner='fp32', inner_rtol=1e-4, max_iters=20000,
+                    max_outer=-1 if args.serving_mixed == 'restarted' else 20)
 
     def inputs(shape, req):
         n, k = shape
@@ -453,7 +456,7 @@ def serving_leg(args, local):
         'evictions': st['evictions'] + st_cal['evictions'], 'max_in_flight': st['max_in_flight'],
         'budget_gb': args.serving_budget_gb, 'gmres_iters_mean': float(its.mean()), 'gmres_iters_max': int(its.max()),
         'max_rel_resid': rel, 'mesh_generation_s': round(t_mesh, 2),
-        'solve': 'FP32 blocks + FP64 refinement, BJ-GMRES(30) to 1e-8, CUDA graphs',
+        'solve': 'FP32 blocks, BJ-GMRES(30) to 1e-8, CUDA graphs, mixed mode: ' + args.serving_mixed,
         'latency': 'arrival to trace in host memory (includes element-block generation on the host)'}
 
 
