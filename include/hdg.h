@@ -335,6 +335,13 @@ hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t 
                         int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
                         int64_t count, void* stream);
 
+/* Elements per condensation chunk (default: as many as ~1 GiB of staging and
+ * temporaries hold, the most allowed).  With host inputs and several chunks
+ * the copies of chunk c+1 overlap the condensation of chunk c (two staging
+ * buffers, a copy stream ordered by events).  HDG_ERR_ARG for elems < 1 or
+ * above the default. */
+hdg_status hdg_set_condense_chunk(hdg_problem p, int64_t elems);
+
 /* Condensation products of this problem on the tensor cores (mode 1, the
  * default, 2 or 3, as hdg_gemm_f64 modes 1-3, where K <= 192 and N >= 16)
  * or on the FP64 cores (mode 0).  Mode 2 keeps a digit-plane buffer of the

@@ -69,6 +69,7 @@ _SIGS = {
     'hdg_autotune': (_I, [_V, _I, _I, _V]),
     'hdg_gemm_f64': (_I, [_I, _I, _I, _I, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _I64, _D, _D, _I64, _V]),
     'hdg_set_condense_mode': (_I, [_V, _I]),
+    'hdg_set_condense_chunk': (_I, [_V, _I64]),
     'hdg_get_tuning': (_I, [_V, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float),
                             ctypes.POINTER(ctypes.c_float)]),
     'hdg_tuning_candidates': (_I, [_V, _I, _I, ctypes.POINTER(_I), _I]),
@@ -262,3 +263,7 @@ def hdg_gemm_f64(mode, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, beta,
 
 def hdg_set_condense_mode(p, mode):
     return load().hdg_set_condense_mode(p, mode)
+
+
+def hdg_set_condense_chunk(p, elems):
+    return load().hdg_set_condense_chunk(p, int(elems))

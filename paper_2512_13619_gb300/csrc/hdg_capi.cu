@@ -90,7 +90,13 @@ struct hdg_problem_s {
   double* d_uhatD = nullptr;
   // staging / temporaries for condensation
   int64_t chunk = 0;
+  int64_t chunk_cap = 0;          // elements the staging and temporaries hold
   double* d_stage = nullptr;
+  // second staging buffer, copy stream and events: host blocks of chunk c+1
+  // are copied while chunk c is condensed
+  double* d_stage2 = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr}, ev_start = nullptr;
   double* d_tmp = nullptr;
 
   // assembled system
@@ -1133,6 +1139,7 @@ hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_pr
     int64_t ch = (int64_t)((1ll << 30) / (per * 8));
     ch = std::max<int64_t>(1, std::min<int64_t>(ch, p->NE));
     p->chunk = ch;
+    p->chunk_cap = ch;
     p->d_stage = (double*)p->dalloc(sizeof(double) * ch * in_sizes(p).total);
     p->d_tmp = (double*)p->dalloc(sizeof(double) * ch * tmp_per_elem(p));
     // exponents of the largest batched product of a chunk: nb1 <= max(D, M) items
@@ -1167,6 +1174,12 @@ hdg_status hdg_problem_destroy(hdg_problem p) {
     if (cg.g) cudaGraphDestroy(cg.g);
   }
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
+    if (p->ev_freed[i]) cudaEventDestroy(p->ev_freed[i]);
+  }
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
   if (p->h_flag) cudaFreeHost(p->h_flag);
   if (p->h_dbl) cudaFreeHost(p->h_dbl);
   if (p->h_int) cudaFreeHost(p->h_int);
@@ -1195,6 +1208,7 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
     const int64_t tmp = PE * PE + MPE * MPE + MPE * nlb + nlb * MPE;
     const int64_t ch = std::max<int64_t>(1, std::min<int64_t>((1ll << 30) / ((in_total + tmp) * 8), NE));
     by += ch * (in_total + tmp) * 8 + (16ll << 20);               // + small per-call buffers
+    if (NE > ch) by += ch * in_total * 8;                          // second staging buffer (host inputs)
     // exponents of the tensor-core products (16-bit, as hdg_problem_create sizes them)
     const int64_t mx = std::max({nlb, MPE, D * PE, nl * (int64_t)mesh->PF});
     by += ch * std::max<int64_t>(D, mesh->M) * 2 * mx * 2;
@@ -1248,23 +1262,46 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
       p->assembled = false;
       return HDG_OK;
     }
-    for (int64_t c0 = 0; c0 < count; c0 += p->chunk) {
+    // host blocks with several chunks: two staging buffers, the copies on a
+    // copy stream ordered against the condensation by events
+    const bool overlap = !on_device && count > p->chunk;
+    if (overlap) {
+      if (!p->d_stage2) p->d_stage2 = (double*)p->dalloc(sizeof(double) * p->chunk * in_sizes(p).total);
+      if (!p->copy_stream) CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+      for (int i = 0; i < 2; ++i) {
+        if (!p->ev_copied[i]) CK(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
+        if (!p->ev_freed[i]) CK(cudaEventCreateWithFlags(&p->ev_freed[i], cudaEventDisableTiming));
+      }
+      if (!p->ev_start) CK(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+      CK(cudaEventRecord(p->ev_start, s));                  // earlier work on the staging buffers
+      CK(cudaStreamWaitEvent(p->copy_stream, p->ev_start, 0));
+    }
+    int64_t ci = 0;
+    for (int64_t c0 = 0; c0 < count; c0 += p->chunk, ++ci) {
       const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
+      const int bsel = (int)(ci & 1);
       const double* dev[11];
-      double* st = p->d_stage;
+      double* st = (overlap && bsel) ? p->d_stage2 : p->d_stage;
+      cudaStream_t cs = overlap ? p->copy_stream : s;
+      if (overlap && ci >= 2) CK(cudaStreamWaitEvent(cs, p->ev_freed[bsel], 0));   // chunk ci-2 is done with it
       for (int i = 0; i < 11; ++i) {
         const double* base = blocks[i] + (sh[i] ? 0 : c0 * sz[i]);
         const int64_t ncopy = sh[i] ? 1 : ec;
         if (on_device) {
           dev[i] = base;
         } else {
-          CK(cudaMemcpyAsync(st, base, sizeof(double) * ncopy * sz[i], kind, s));
+          CK(cudaMemcpyAsync(st, base, sizeof(double) * ncopy * sz[i], kind, cs));
           dev[i] = st;
           st += ncopy * sz[i];
         }
       }
+      if (overlap) {
+        CK(cudaEventRecord(p->ev_copied[bsel], cs));
+        CK(cudaStreamWaitEvent(s, p->ev_copied[bsel], 0));
+      }
       condense_chunk(p, e0 + c0, ec, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], dev[7], dev[8], dev[9],
                      dev[10], sh, s);
+      if (overlap) CK(cudaEventRecord(p->ev_freed[bsel], s));
       CK(cudaGetLastError());
       for (int64_t e = e0 + c0; e < e0 + c0 + ec; ++e) {
         if (!p->condensed[e]) {
@@ -1854,6 +1891,17 @@ const char* hdg_last_error(void) { return g_last_error; }
 hdg_status hdg_set_graphs(hdg_problem p, int enable) {
   if (!p) return HDG_ERR_ARG;
   p->use_graphs = enable != 0;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_condense_chunk(hdg_problem p, int64_t elems) {
+  if (!p || elems < 1) return HDG_ERR_ARG;
+  if (elems > p->chunk_cap) return HDG_ERR_ARG;
+  if (p->d_stage2) {
+    p->dfree(p->d_stage2, 0);   // sized for the old chunk
+    p->d_stage2 = nullptr;
+  }
+  p->chunk = elems;
   return HDG_OK;
 }
 

@@ -121,3 +121,27 @@ def test_condensation_tensor_equals_fp64_cores():
     for m in (1, 2, 3):
         assert rel(out[m][0], out[0][0]) < 1e-13
         assert rel(out[m][1], out[0][1]) < 1e-13
+
+
+def test_condensation_chunks_from_host_overlap_copies():
+    """Host inputs condensed in many small chunks (the copies of chunk c+1
+    overlap the condensation of chunk c through two staging buffers) give
+    bitwise the results of one chunk."""
+    need_gpu()
+    import torch
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w = W.hex_poisson(n=3, k=3)
+    blk = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in w.blocks().items()
+           if k in driver.BLOCK_NAMES}
+    out = []
+    for chunk in (None, 2, 5):
+        p = driver.Problem.from_workload(w)
+        if chunk:
+            assert L.hdg_set_condense_chunk(p.h, chunk) == 0
+        assert L.hdg_condense(p.h, 0, w.n_elem, *[blk[k] for k in driver.BLOCK_NAMES], 0, None) == 0
+        out.append(p.condensed())
+        assert L.hdg_set_condense_chunk(p.h, 0) == L.HDG_ERR_ARG
+        p.close()
+    for m in (1, 2):
+        assert np.array_equal(out[m][0], out[0][0]) and np.array_equal(out[m][1], out[0][1])
