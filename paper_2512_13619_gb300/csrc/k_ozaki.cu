@@ -205,8 +205,12 @@ __device__ __forceinline__ int core_off(int row, int kgrp) { return (row >> 3) *
 
 // Per batch item: the largest exponent field of every row of A and of every
 // column of B (over all of K), as 16-bit integers; flags Inf / NaN inputs.
+// Rows of A: one warp per row, lanes along K (coalesced).  Columns of B:
+// threads along the columns (coalesced), four K ranges per column merged in
+// shared memory.
 __global__ void __launch_bounds__(256) ozaki_exponents_kernel(GemmDesc d, uint16_t* ea, uint16_t* fb,
                                                               unsigned* err) {
+  __shared__ int colmax[256];
   const int z = blockIdx.x;
   const int b0 = z / d.nb1, b1 = z % d.nb1;
   const double* A = d.A + b0 * d.sA0 + b1 * d.sA1;
@@ -217,17 +221,28 @@ __global__ void __launch_bounds__(256) ozaki_exponents_kernel(GemmDesc d, uint16
     int m = 0;
     const double* row = A + (int64_t)r * d.lda;
 #pragma unroll 8
-    for (int k = lane; k < d.K; k += 32) m = max(m, exp_field(row[k]));
+    for (int k = lane; k < d.K; k += 32) m = max(m, exp_field(__ldg(row + k)));
     bad |= (m == 0x7FF);
     m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
     if (lane == 0) ea[(int64_t)z * d.M + r] = (uint16_t)m;
   }
-  for (int n = threadIdx.x; n < d.N; n += 256) {
+  // columns in blocks of 64: thread (n, q) scans rows k = q, q + 4, ...
+  for (int n0 = 0; n0 < d.N; n0 += 64) {
+    const int n = n0 + (threadIdx.x & 63), q = threadIdx.x >> 6;
     int m = 0;
+    if (n < d.N) {
 #pragma unroll 8
-    for (int k = 0; k < d.K; ++k) m = max(m, exp_field(B[(int64_t)k * d.ldb + n]));
-    bad |= (m == 0x7FF);
-    fb[(int64_t)z * d.N + n] = (uint16_t)m;
+      for (int k = q; k < d.K; k += 4) m = max(m, exp_field(__ldg(B + (int64_t)k * d.ldb + n)));
+    }
+    colmax[threadIdx.x] = m;
+    __syncthreads();
+    if (q == 0 && n < d.N) {
+      const int c = threadIdx.x;
+      m = max(max(colmax[c], colmax[c + 64]), max(colmax[c + 128], colmax[c + 192]));
+      bad |= (m == 0x7FF);
+      fb[(int64_t)z * d.N + n] = (uint16_t)m;
+    }
+    __syncthreads();
   }
   if (bad) atomicOr(err, ERRBIT_NAN);
 }
