@@ -314,18 +314,20 @@ hdg_status hdg_set_kernel_variant(hdg_problem p, int variant);
  *           largest entry, as 8 digits of 7 bits; digit products summed
  *           exactly in FP32 per digit weight; the result rounded once to FP64.
  *           The error is within a small factor of FP64 rounding,
- *           |err_ij| <= 2^-54 K max_k|A_ik| max_k|B_kj|.  Needs K <= 192 and
+ *           |err_ij| <= 2^-54 K max_k|A_ik| max_k|B_kj| for K <= 192 (the
+ *           exactness bound of the accumulators); larger K runs in slices of
+ *           at most 192, each rounded to FP64 and accumulated into C.  Needs
  *           N >= 16 (HDG_ERR_ARG otherwise); HDG_ERR_NAN if an input is Inf
  *           or NaN (the result is then not defined).  The digits are
  *           computed inside the product kernel for every output tile from the
  *           FP64 operands ((M + N) * count 16-bit words of stream-ordered
  *           scratch from cudaMallocAsync).
- *   mode 2: as mode 1, with each operand split once into BF16 digit planes
+ *   mode 2: as mode 1 (K <= 192), with each operand split once into BF16 digit planes
  *           in device memory (16 bytes per entry, twice the FP64 operand)
  *           that the product kernel moves with bulk copies; the same
  *           results, slower at the condensation shapes (the plane traffic
  *           bounds it).
- *   mode 3: as mode 1 with one persistent CTA per SM walking all output
+ *   mode 3: as mode 1 (K <= 192) with one persistent CTA per SM walking all output
  *           tiles (accumulators double-buffered in TMEM for 32-column
  *           tiles); the same results, slower at the condensation shapes.  Synchronizes `stream` to read the error word it shares
  * with other calls of this function in the process (do not call it

@@ -462,7 +462,8 @@ void gemm_c(hdg_problem p, const GemmDesc& d, cudaStream_t s) {
       if (ok) return;
     }
   }
-  if (p->condense_mode >= 1 && gemm_ozaki_scratch(d) <= p->oz_cap && d.K <= 192 && d.N >= 16) {
+  if (p->condense_mode >= 1 && gemm_ozaki_scratch(d) <= p->oz_cap && d.N >= 16 &&
+      (d.K <= 192 || p->condense_mode == 1)) {
     timed_begin(p, s);
     if (p->condense_mode == 3) gemm_ozaki_persist(d, p->d_oz, p->oz_cap, p->d_err, s);
     else gemm_ozaki(d, p->d_oz, p->d_err, s);
@@ -1916,7 +1917,7 @@ hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t 
                         int64_t count, void* stream) {
   if (mode < 0 || mode > 3 || M < 1 || N < 1 || K < 1 || count < 0 || !A || !B || !C) return HDG_ERR_ARG;
   if (lda < K || ldb < N || ldc < N || count > (1ll << 31) - 1) return HDG_ERR_ARG;
-  if (mode >= 1 && (K > 192 || N < 16)) return HDG_ERR_ARG;
+  if (mode >= 1 && (N < 16 || (mode >= 2 && K > 192))) return HDG_ERR_ARG;
   if (count == 0) return HDG_OK;
   cudaStream_t s = (cudaStream_t)stream;
   try {

@@ -24,7 +24,8 @@ struct GemmDesc {
 };
 void gemm_f64(const GemmDesc& d, cudaStream_t s);
 // The same product on the BF16 tensor cores by exact operand splitting
-// (FP64-accurate).  Returns false (nothing launched) when K > 192 or N < 16.
+// (FP64-accurate); K > 192 runs in slices of at most 192 accumulated into C.
+// Returns false (nothing launched) when N < 16.
 // scratch: gemm_ozaki_scratch(d) 16-bit words of device memory (the row and
 // column exponents), reused after the launches complete.
 int64_t gemm_ozaki_scratch(const GemmDesc& d);

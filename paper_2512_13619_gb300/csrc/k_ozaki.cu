@@ -1031,7 +1031,20 @@ int64_t gemm_ozaki_scratch(const GemmDesc& d) {
 }
 
 bool gemm_ozaki(const GemmDesc& d, uint16_t* scratch, unsigned* err, cudaStream_t s) {
-  if (d.K > kMaxK || d.N < 16 || d.M <= 0 || d.K <= 0 || !scratch) return false;
+  if (d.N < 16 || d.M <= 0 || d.K <= 0 || !scratch) return false;
+  if (d.K > kMaxK) {
+    // K in slices of at most 192 (the exactness bound of the accumulators),
+    // each rounded to FP64 and accumulated into C
+    for (int k0 = 0; k0 < d.K; k0 += kMaxK) {
+      GemmDesc e = d;
+      e.K = d.K - k0 < kMaxK ? d.K - k0 : kMaxK;
+      e.A = d.A + k0;                      // columns k0.. of A
+      e.B = d.B + (int64_t)k0 * d.ldb;     // rows k0.. of B
+      if (k0 > 0) e.beta = 1.0;
+      gemm_ozaki(e, scratch, err, s);
+    }
+    return true;
+  }
   static_assert(kSmem <= 227 * 1024, "shared memory");
   cudaFuncSetAttribute(gemm_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   const int ntile = (d.N + kMaxNT - 1) / kMaxNT;

@@ -21,6 +21,7 @@ SMALL = {
     'cdr_M5_R4': lambda: W.hex_cdr(n=2, k=1, R=4),
     'elast_pert_k2_R8': lambda: W.hex_elasticity(n=2, k=2, R=8),
     'cdr_k2_R4': lambda: W.hex_cdr(n=2, k=2, R=4),     # b = 45: face rows span several staging chunks
+    'hex_q4': lambda: W.hex_poisson(n=2, k=4),          # K = 375 > 192: tensor-core products in K slices
 }
 
 
