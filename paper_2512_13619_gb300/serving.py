@@ -175,6 +175,23 @@ class Server:
             'max_in_flight': self.max_in_flight, 'resident_bytes': self.used_bytes,
         }
 
+    def warm(self, shapes, per_shape=1):
+        """Create `per_shape` idle slots for each shape before requests arrive
+        (a server that knows its meshes), as far as the budget allows; returns
+        the number created.  Slots are created in the order given."""
+        made = 0
+        for _ in range(per_shape):
+            for sh in shapes:
+                need = self.backend.slot_bytes(sh)
+                if self.used_bytes + need > self.mem_budget:
+                    continue
+                sl = Slot(sh, self.backend.create_slot(sh, 0), need)
+                self.slots.append(sl)
+                self.used_bytes += need
+                self.creations += 1
+                made += 1
+        return made
+
     def close(self):
         for sl in self.slots:
             if sl.handle is not None:

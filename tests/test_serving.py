@@ -120,3 +120,13 @@ def test_server_runs_twice_statistics_per_run():
     st2 = srv.run([{'id': 1, 'shape': 'a'}, {'id': 2, 'shape': 'a'}], [0.0, 0.0])
     assert st1['completed'] == 1 and st2['completed'] == 2
     assert st2['slot_creations'] <= 2 and srv.results[2] == 4
+
+
+def test_warm_creates_slots_within_budget_and_requests_reuse_them():
+    be = FakeBackend({'a': 40, 'b': 30, 'c': 50})
+    srv = Server(be, lanes=2, mem_budget=100)
+    made = srv.warm(['a', 'b', 'c'])
+    assert made == 2 and srv.used_bytes == 70          # 'c' does not fit beside 'a' and 'b'
+    st = srv.run([{'id': 0, 'shape': 'a'}, {'id': 1, 'shape': 'b'}], [0.0, 0.0])
+    assert st['completed'] == 2 and st['slot_creations'] == 2     # only the warm slots
+    assert srv.results[0] == 0 and srv.results[1] == 2
