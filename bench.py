@@ -54,10 +54,14 @@ def parse():
     ap.add_argument('--serving-budget-gb', type=float, default=160.0)
     ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
     ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
-    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40'], default='poisson16',
+    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40', 'beam'], default='poisson16',
                     help='poisson16: the step above; elasticity32 / cdr40: solver and kernel measurements '
                          'on the 32^3 perturbed Q2 elasticity (8 RHS) and 40^3 Q2 5-component CDR (4 RHS) '
-                         'problems, one JSON line')
+                         'problems; beam: the cantilever beam runs of Sec. 6.2 (BJ, BJ-PP(10), ASM, '
+                         'ASM-PP(10), GMRES(50) to 1e-6) over k at N_E = 320 and over N_E at k = 3; '
+                         'one JSON line')
+    ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
+                    help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
     ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
                     help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
                          'one FP32 hdg_apply_K call (matvec) or one solve (solve-*), for profilers; no JSON')
@@ -590,6 +594,83 @@ def run_config(args, local):
     return out
 
 
+def run_beam(args, local):
+    """Sec. 6.2 cantilever beam (0,5) x (0,1) x (0,1), lambda = mu = 1,
+    clamped at x = 0, uniform traction at x = 5: per mesh and degree, the
+    condensation, the preconditioner set-up and GMRES(50) with classical
+    Gram-Schmidt to a relative residual of 1e-6 (FP64), with BJ, BJ-PP(10),
+    ASM and ASM-PP(10), timed with CUDA events; the polynomial variants also
+    with the restarted mixed path (FP32 cycles, FP64 residual at restarts)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    names = driver.BLOCK_NAMES
+    maxit = max(args.max_iters, 20000)
+
+    def ev_time(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    rows = []
+    for case in args.beam_cases.split(','):
+        n, k = (int(v) for v in case.split(':'))
+        w = W.hex_beam(n=n, k=k)
+        hb, strides = W.shared_blocks(w)
+        dblk = [torch.from_numpy(hb[x]).to(dev) for x in names]
+        p = driver.Problem.from_workload(w, local)
+
+        def condense():
+            driver.check(L.hdg_condense_strided(p.h, 0, w.n_elem, dblk, strides, 1, st), 'condense')
+        condense()
+        ms_cond = ev_time(condense)
+        driver.check(L.hdg_set_dirichlet(p.h, w.uhat_dirichlet(), 0, st), 'dirichlet')
+        v0 = torch.from_numpy(w.random_vector(11)).to(dev)
+        row = {'N_E': w.n_elem, 'k': k, 'n_dof': p.n_dof, 'condense_ms': round(ms_cond, 3), 'solves': {}}
+        for label, pc, poly in (('BJ', 'bj', None), ('BJ-PP(10)', 'bj', 'gmres'), ('ASM', 'asm', None),
+                                ('ASM-PP(10)', 'asm', 'gmres')):
+            for tag in (('fp64', 'mixed_restarted') if poly else ('fp64',)):
+                o = driver.opts(restart=50, rtol=1e-6, orth='cgs', pc=pc, poly=poly, degree=10 if poly else 0,
+                                inner='fp64' if tag == 'fp64' else 'fp32',
+                                poly_prec='fp64' if tag == 'fp64' else 'fp32', max_iters=maxit,
+                                max_outer=-1 if tag != 'fp64' else 20)
+                ms_setup = ev_time(lambda: (driver.check(L.hdg_assemble(p.h, o, st), 'assemble'),
+                                            driver.check(L.hdg_setup_precond(p.h, o, v0 if poly else None, st),
+                                                         'setup')))
+                info = L.hdg_solve_info()
+                stt = L.hdg_solve(p.h, o, st, info)          # builds the cycle graphs
+                ms = ev_time(lambda: L.hdg_solve(p.h, o, st, info)) if stt == 0 else float('nan')
+                print('beam N_E=%d k=%d %s %s: %s, %d iterations, %.2f ms' % (
+                    w.n_elem, k, label, tag, L.hdg_status_str(stt), info.iters, ms), file=sys.stderr, flush=True)
+                row['solves'][label + ('' if tag == 'fp64' else ' mixed')] = {
+                    'gmres': info.iters, 'setup_ms': round(ms_setup, 3), 'solve_ms': round(ms, 3),
+                    't_comp_s': round((ms_cond + ms_setup + ms) / 1e3, 4), 'rel_resid': info.rel_resid,
+                    'status': L.hdg_status_str(stt)}
+        # mean tip deflection of the last solution: <g, uhat> over the loaded
+        # face (unit area, t = (0, 0, -1)), from the element face loads r_uh
+        # (identical face parametrisation from both sides on this mesh)
+        tr = p.trace()[:, :, 0]
+        ruh = hb['ruh'][:, :, 0].reshape(w.n_elem, w.n_lfe, -1)
+        row['tip_deflection'] = round(float(np.einsum('elj,elj->', ruh, tr[w.mesh.elem_face])), 4)
+        rows.append(row)
+        p.close()
+        del dblk
+        torch.cuda.empty_cache()
+    return {'workload': 'HDG linear elasticity cantilever beam (0,5)x(0,1)^2, lambda = mu = 1, Q^k hexahedra, '
+                        'clamped x = 0, traction (0,0,-1) at x = 5; GMRES(50) CGS to 1e-6',
+            'data': 'synthetic', 'max_iters': maxit, 'cases': rows}
+
+
 def oracle_step(w, blk):
     """One step of the workload with the FP64 oracle (condense, assemble,
     block-Jacobi, GMRES(50) to 1e-8, recover).  Returns (ms, iterations)."""
@@ -695,6 +776,8 @@ def main():
         return
     if args.impl == 'reference':
         out = run_reference(args, ws, rank)
+    elif args.workload == 'beam':
+        out = run_beam(args, local)
     elif args.workload != 'poisson16':
         out = run_config(args, local)
     else:

@@ -274,9 +274,35 @@ def load_vector_from_nodal(mats, fnodal):
     return ru.reshape(ru.shape[0], -1)
 
 
+def neumann_face_load(mesh, ref, perm, elems, neumann, g, M):
+    """r_uh rows of Neumann faces: the trace equation of a boundary face that
+    is not Dirichlet states <Fhat.n, mu> = <g, mu>, g the prescribed outward
+    normal flux (g = -kappa du/dn for F = -kappa grad u; g = -t for
+    F = -sigma, t the applied traction).  g(x, n) -> (..., M) at face
+    quadrature points x with unit outward normals n.  Returns (E, nl*M*PF) in
+    the (l, a, j) row order of H and J; zero rows on the other faces."""
+    nl, PF = ref.n_lfe, ref.PF
+    E = len(elems)
+    out = np.zeros((E, nl, M, PF))
+    for l in range(nl):
+        sel = neumann[mesh.elem_face[elems, l]].astype(bool)
+        if not np.any(sel):
+            continue
+        es = elems[sel]
+        xf, Jf, detf, Jinvf = geometry(mesh, es, ref.face_ref_pts[l])
+        nv = detf[:, :, None] * np.einsum('eqba,b->eqa', Jinvf, ref.face_normal_ref[l])
+        dA = np.linalg.norm(nv, axis=2)
+        w = ref.face_wts[None, :] * dA
+        psi = np.transpose(ref.face_psi[:, perm[es, l, :]], (1, 0, 2))
+        gx = g(xf, nv / dA[:, :, None])                                   # (E', nfq, M)
+        out[sel, l] = np.einsum('eq,eqa,eqj->eaj', w, gx, psi)
+    return out.reshape(E, nl * M * PF)
+
+
 def dirichlet_face_values(mesh, ref, perm, u_exact, M):
     """L2 projection of u_exact onto the face space of every boundary face
-    (b_hat = uhat - u_D on Dirichlet faces).  Returns (NF, M*PF)."""
+    (b_hat = uhat - u_D on Dirichlet faces).  Returns (NF, M*PF); only the
+    rows of Dirichlet faces are used."""
     NF = mesh.n_face
     out = np.zeros((NF, M * ref.PF))
     bf = np.nonzero(mesh.face_boundary)[0]

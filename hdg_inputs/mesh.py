@@ -81,22 +81,34 @@ def hex_mesh(n, perturb=0.0, seed=None):
     """n^3 hexahedra on [0,1]^3.  With perturb > 0, every interior vertex moves
     by perturb * h * r * s, s a uniform random unit vector and r ~ U[0,1]
     (seeded); boundary vertices stay fixed."""
-    xs = np.linspace(0.0, 1.0, n + 1)
-    h = 1.0 / n
-    verts = np.array([[xs[i], xs[j], xs[l]] for l in range(n + 1) for j in range(n + 1) for i in range(n + 1)])
+    return box_hex_mesh((n, n, n), (1.0, 1.0, 1.0), perturb, seed)
+
+
+def box_hex_mesh(counts, lengths, perturb=0.0, seed=None):
+    """nx x ny x nz hexahedra on (0,Lx) x (0,Ly) x (0,Lz), e.g. the
+    (0,5) x (0,1) x (0,1) cantilever beam of Sec. 6.2 with 10x2x2 .. 40x8x8
+    elements.  Vertex and element ids run x fastest; perturb as in hex_mesh,
+    relative to the smallest cell width."""
+    nx, ny, nz = counts
+    lx, ly, lz = lengths
+    axes = [np.linspace(0.0, L, c + 1) for c, L in zip(counts, lengths)]
+    verts = np.array([[axes[0][i], axes[1][j], axes[2][l]]
+                      for l in range(nz + 1) for j in range(ny + 1) for i in range(nx + 1)])
     if perturb > 0.0:
+        h = min(L / c for c, L in zip(counts, lengths))
         rng = np.random.default_rng(seed)
         nv = verts.shape[0]
         s = rng.normal(size=(nv, 3))
         s /= np.linalg.norm(s, axis=1, keepdims=True)
         r = rng.uniform(0.0, 1.0, size=(nv, 1))
-        interior = np.all((verts > 1e-12) & (verts < 1 - 1e-12), axis=1)
+        top = np.array([lx, ly, lz])
+        interior = np.all((verts > 1e-12) & (verts < top - 1e-12), axis=1)
         verts = verts + (perturb * h * r * s) * interior[:, None]
-    vid = lambda i, j, l: (l * (n + 1) + j) * (n + 1) + i
+    vid = lambda i, j, l: (l * (ny + 1) + j) * (nx + 1) + i
     elems = []
-    for l in range(n):
-        for j in range(n):
-            for i in range(n):
+    for l in range(nz):
+        for j in range(ny):
+            for i in range(nx):
                 elems.append([vid(i + di, j + dj, l + dl) for dl in (0, 1) for dj in (0, 1) for di in (0, 1)])
     elems = np.array(elems, np.int64)
     ef, fe, fb = _build_faces([hex_face_vertices(l) for l in range(6)], elems)

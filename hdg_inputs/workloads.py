@@ -14,7 +14,12 @@
                                                              (n=40, k=2, R=4)
   hex_convdiff    : one serving request: n^3 hexahedra, Q^k, kappa, unit beta,
                     f = 1, tau = 1 + kappa
-All faces on the domain boundary are Dirichlet faces.
+  hex_beam        : cantilever beam (0,5) x (0,1) x (0,1) with 5n x n x n
+                    hexahedra (Sec. 6.2: n = 2, 4, 6, 8 gives N_E = 40, 320,
+                    1080, 2560), Q^k, lambda = mu = 1, tau = 1; clamped
+                    (u = 0) at x = 0, uniform traction t = (0, 0, -1) at
+                    x = 5, the other faces traction-free; no body force
+Except for hex_beam, all faces on the domain boundary are Dirichlet faces.
 """
 from dataclasses import dataclass
 import numpy as np
@@ -31,12 +36,14 @@ class Workload:
     perm: np.ndarray
     phys: object
     R: int
-    rhs_kind: str                 # 'function' or 'nodal'
+    rhs_kind: str                 # 'function', 'nodal' or 'none' (no body force)
     f_exact: object = None        # callable x -> (..., M)
     u_exact: object = None        # callable x -> (..., M)
     q_exact: object = None        # callable x -> (..., M, D)
     rhs_seeds: tuple = ()
     k: int = 1
+    dirichlet: np.ndarray = None  # (NF,) uint8 Dirichlet faces; None = every boundary face
+    neumann_flux: object = None   # g(x, n) -> (..., M): outward flux on the other boundary faces
 
     # sizes
     @property
@@ -62,7 +69,14 @@ class Workload:
 
     @property
     def face_dirichlet(self):
+        if self.dirichlet is not None:
+            return np.asarray(self.dirichlet, np.uint8)
         return self.mesh.face_boundary.astype(np.uint8)
+
+    @property
+    def face_neumann(self):
+        """Boundary faces that are not Dirichlet faces (prescribed flux)."""
+        return (self.mesh.face_boundary.astype(bool) & ~self.face_dirichlet.astype(bool)).astype(np.uint8)
 
     @property
     def n_free(self):
@@ -79,7 +93,9 @@ class Workload:
         mats = blk.element_matrices(self.mesh, self.ref, self.perm, elems)
         out = blk.hdg_blocks(mats, self.phys)
         E = len(elems)
-        if self.rhs_kind == 'function':
+        if self.rhs_kind == 'none':
+            ru = np.zeros((E, self.M * self.PE, self.R))
+        elif self.rhs_kind == 'function':
             ru = blk.load_vector_from_function(mats, self.ref, self.f_exact, self.M)[:, :, None]
             ru = np.repeat(ru, self.R, axis=2)
         else:
@@ -91,6 +107,10 @@ class Workload:
             ru = np.stack(cols, axis=2)
         out['ru'] = np.ascontiguousarray(ru)
         out['ruh'] = np.zeros((E, self.n_lfe * self.M * self.PF, self.R))
+        if self.neumann_flux is not None and self.face_neumann.any():
+            gN = blk.neumann_face_load(self.mesh, self.ref, self.perm, elems, self.face_neumann,
+                                       self.neumann_flux, self.M)
+            out['ruh'] += gN[:, :, None]
         out['_mats'] = mats
         return out
 
@@ -174,6 +194,32 @@ def hex_convdiff(n, k, kappa, beta, R=1):
     return Workload('hex_convdiff', m, ref, blk.face_permutations(m, ref), phys, R, 'function', one, k=k)
 
 
+def boundary_faces_at(mesh, axis, value, tol=1e-12):
+    """(NF,) uint8: boundary faces whose vertices all have x_axis = value."""
+    from .basis import hex_face_vertices
+    out = np.zeros(mesh.n_face, np.uint8)
+    for f in np.nonzero(mesh.face_boundary)[0]:
+        e, l = mesh.face_elem[f, 0], mesh.face_elem[f, 1]
+        xs = mesh.verts[mesh.elems[e, hex_face_vertices(l)], axis]
+        out[f] = np.all(np.abs(xs - value) < tol)
+    return out
+
+
+def hex_beam(n=4, k=2, lam=1.0, mu=1.0, traction=(0.0, 0.0, -1.0), length=5.0, tau=1.0):
+    """Sec. 6.2: the clamped face x = 0 is the only Dirichlet boundary; the
+    loaded end x = length carries the traction t, i.e. the outward flux of
+    F = -sigma there is g = -t; the four side faces are traction-free."""
+    m = meshmod.box_hex_mesh((5 * n, n, n), (length, 1.0, 1.0))
+    ref = blk.reference_element(m, k)
+    t = np.asarray(traction, float)
+
+    def g(x, nrm):
+        at_end = (np.abs(x[..., 0] - length) < 1e-9)[..., None]
+        return np.where(at_end, -t, 0.0)
+    return Workload('hex_beam', m, ref, blk.face_permutations(m, ref), blk.elasticity(3, lam, mu, tau), 1,
+                    'none', k=k, dirichlet=boundary_faces_at(m, 0, 0.0), neumann_flux=g)
+
+
 def serving_requests(n_requests=512, seed=4, n_range=(8, 24), k_range=(1, 3)):
     """Request parameters of the serving stream: kappa log-uniform in
     [1e-3, 1], a uniform random unit velocity, n and k uniform integers."""
@@ -241,7 +287,7 @@ def shared_blocks(w):
     X = m.verts[m.elems]
     assert np.allclose(X - X[:, :1], X[:1] - X[:1, :1], atol=1e-13), "elements are not translates"
     assert np.all(w.perm == np.arange(w.PF)), "face permutations differ between elements"
-    assert w.rhs_kind == 'nodal'
+    assert w.rhs_kind in ('nodal', 'none')
     b0 = w.blocks(0, 1)
     mats = b0.pop('_mats')
     cols = []
@@ -249,8 +295,13 @@ def shared_blocks(w):
         fn = np.random.default_rng(s).standard_normal((w.n_elem, w.M, w.PE))
         cols.append(np.einsum('ij,eaj->eai', mats['Me'][0], fn).reshape(w.n_elem, -1))
     out = {k: np.ascontiguousarray(v) for k, v in b0.items()}
-    out['ru'] = np.ascontiguousarray(np.stack(cols, axis=2))
+    out['ru'] = (np.ascontiguousarray(np.stack(cols, axis=2)) if cols
+                 else np.zeros((w.n_elem, w.M * w.PE, w.R)))
     out['ruh'] = np.zeros((w.n_elem, w.n_lfe * w.M * w.PF, w.R))
+    if w.neumann_flux is not None and w.face_neumann.any():
+        # the face loads differ between elements (only boundary faces carry them)
+        out['ruh'] += blk.neumann_face_load(m, w.ref, w.perm, np.arange(w.n_elem), w.face_neumann,
+                                            w.neumann_flux, w.M)[:, :, None]
     names = ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J', 'ru', 'ruh')
     strides = [0] * 9 + [out['ru'][0].size, out['ruh'][0].size]
     return {k: out[k] for k in names}, strides

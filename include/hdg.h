@@ -209,9 +209,13 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
  * polynomial preconditioner one Arnoldi(P) cycle (MGS) with A = M^{-1} K from
  * the start vector `v0` (device, n_dof doubles), harmonic Ritz values and
  * Leja order (Sec. 4.7) or Chebyshev bounds.  v0 may be NULL when
- * opts->poly == HDG_POLY_NONE.  Errors: HDG_ERR_SINGULAR, HDG_ERR_ARG (also
- * for ASM when n_lfe*M*PF > 169: the element matrices are inverted in shared
- * memory). */
+ * opts->poly == HDG_POLY_NONE.  Errors: HDG_ERR_SINGULAR, HDG_ERR_ARG.
+ * Inverses (BJ blocks, ASM patches, and Ebar and M^e in the condensation)
+ * of order <= 169 run as Gauss-Jordan with partial pivoting in one CTA's
+ * shared memory; larger ones split into 2 x 2 blocks (leading block and its
+ * Schur complement, recursively), which needs a nonsingular leading block
+ * (SPD matrices, or a positive definite symmetric part, as for the HDG
+ * local and patch matrices). */
 hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* opts, const double* v0, void* stream);
 
 /* Restarted left-preconditioned GMRES(m) on K x = r for all R right-hand

@@ -176,6 +176,8 @@ struct hdg_problem_s {
   int64_t planes_cap = 0;
   uint16_t* d_pex = nullptr;
   int64_t pex_cap = 0;
+  double* d_invs = nullptr;        // scratch of the block inverses of matrices beyond one CTA's shared memory
+  int64_t invs_cap = 0;            // (doubles, grown on demand)
   // autotuned launch configurations [operation: K, BJ, ASM][precision]
   BrCfg tune[3][3];
   float tune_us[3][3] = {};        // measured time of the chosen configuration
@@ -473,6 +475,77 @@ void gemm_c(hdg_problem p, const GemmDesc& d, cudaStream_t s) {
   gemm_f64(d, s);
 }
 
+// Scratch (doubles per matrix) of inverse_any for an n x n matrix.
+int64_t inverse_scratch(int n) {
+  if (n <= inverse_max_n()) return 0;
+  const int n1 = (n + 1) / 2;
+  return (int64_t)n * n + inverse_scratch(n1);
+}
+
+// Batched in-place inverse of `count` n x n matrices (batch stride `stride`)
+// of any size.  Up to one CTA's shared memory: Gauss-Jordan with partial
+// pivoting (inverse_f64).  Beyond: the 2 x 2 block form with the leading
+// block A11 (n1 = ceil(n/2)) and its Schur complement S = A22 - A21 A11^{-1}
+// A12, both inverted recursively,
+//   A^{-1} = [A11^{-1} + T S^{-1} U,  -T S^{-1};  -S^{-1} U,  S^{-1}],
+//   T = A11^{-1} A12,  U = A21 A11^{-1},
+// with the products on the condensation's GEMM path.  Pivoting stays within
+// the leaves, so the split needs a nonsingular leading block: true for SPD
+// matrices and for matrices whose symmetric part is positive definite, which
+// covers the local HDG matrices Ebar (Eq. w19) and the ASM patch matrices
+// (Sec. 4.6) of the discretisations here.  A zero leaf pivot sets
+// ERRBIT_SINGULAR.
+void inverse_any(hdg_problem p, double* A, int n, int64_t stride, int64_t count, cudaStream_t s,
+                 int64_t scratch_off = 0) {
+  if (n <= 0 || count <= 0) return;
+  if (n <= inverse_max_n()) {
+    inverse_f64(A, n, stride, count, p->d_err, s);
+    return;
+  }
+  const int64_t need = inverse_scratch(n);
+  if (scratch_off == 0) {
+    // matrices per pass: scratch of at most 1 GiB (at least one matrix)
+    const int64_t per_pass = std::max<int64_t>(1, std::min<int64_t>(count, (1ll << 27) / need));
+    if (per_pass * need > p->invs_cap) {
+      p->dfree(p->d_invs, sizeof(double) * (size_t)p->invs_cap);
+      p->d_invs = nullptr;
+      p->invs_cap = 0;
+      p->d_invs = (double*)p->dalloc(sizeof(double) * (size_t)(per_pass * need));
+      p->invs_cap = per_pass * need;
+    }
+    if (count > per_pass) {
+      for (int64_t c0 = 0; c0 < count; c0 += per_pass)
+        inverse_any(p, A + c0 * stride, n, stride, std::min(per_pass, count - c0), s, 0);
+      return;
+    }
+  }
+  const int n1 = (n + 1) / 2, n2 = n - n1;
+  const int c = (int)count;
+  const int64_t nn = (int64_t)n * n;
+  double* L = p->d_invs + scratch_off;        // this level: count x n^2
+  double* Ai = L;                             // n1 x n1
+  double* T = Ai + (int64_t)n1 * n1;          // n1 x n2
+  double* U = T + (int64_t)n1 * n2;           // n2 x n1
+  double* Sc = U + (int64_t)n2 * n1;          // n2 x n2
+  const int64_t deeper = scratch_off + count * nn;
+  double* A11 = A;
+  double* A12 = A + n1;
+  double* A21 = A + (int64_t)n1 * n;
+  double* A22 = A21 + n1;
+  copy_block_f64(Ai, n1, nn, A11, n, stride, n1, n1, count, s);
+  inverse_any(p, Ai, n1, nn, count, s, deeper);
+  gemm_c(p, gd(n1, n2, n1, Ai, n1, nn, 0, A12, n, stride, 0, T, n2, nn, 0, 1.0, 0.0, c, 1), s);
+  gemm_c(p, gd(n2, n1, n1, A21, n, stride, 0, Ai, n1, nn, 0, U, n1, nn, 0, 1.0, 0.0, c, 1), s);
+  gemm_c(p, gd(n2, n2, n1, A21, n, stride, 0, T, n2, nn, 0, A22, n, stride, 0, -1.0, 1.0, c, 1), s);
+  copy_block_f64(Sc, n2, nn, A22, n, stride, n2, n2, count, s);
+  inverse_any(p, Sc, n2, nn, count, s, deeper);
+  gemm_c(p, gd(n1, n2, n2, T, n2, nn, 0, Sc, n2, nn, 0, A12, n, stride, 0, -1.0, 0.0, c, 1), s);
+  gemm_c(p, gd(n2, n1, n2, Sc, n2, nn, 0, U, n1, nn, 0, A21, n, stride, 0, -1.0, 0.0, c, 1), s);
+  copy_block_f64(A11, n, stride, Ai, n1, nn, n1, n1, count, s);
+  gemm_c(p, gd(n1, n1, n2, A12, n, stride, 0, U, n1, nn, 0, A11, n, stride, 0, -1.0, 1.0, c, 1), s);
+  copy_block_f64(A22, n, stride, Sc, n2, nn, n2, n2, count, s);
+}
+
 void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, const double* Bd, const double* Cd,
                     const double* Dm, const double* Em, const double* Fm, const double* Gm, const double* Hm,
                     const double* Jm, const double* ru, const double* ruh, const bool* sh, cudaStream_t s) {
@@ -496,7 +569,7 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
   // (M^e)^{-1}  (Eq. w16); a shared mass matrix is inverted once
   const int64_t nM = sh[0] ? 1 : ec;
   CK(cudaMemcpyAsync(Minv, Me, sizeof(double) * nM * PE * PE, cudaMemcpyDeviceToDevice, s));
-  inverse_f64(Minv, PE, (int64_t)PE * PE, nM, p->d_err, s);
+  inverse_any(p, Minv, PE, (int64_t)PE * PE, nM, s);
   // (M^e)^{-1} B_d, (M^e)^{-1} C_d
   gemm_c(p, gd(PE, PE, PE, Minv, PE, sMe, 0, Bd, PE, sBd, PE * PE, MinvB, PE, (int64_t)D * PE * PE, PE * PE, 1.0, 0.0,
               n, D), s);
@@ -519,7 +592,7 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
   gemm_c(p, gd(nlb, nlPF, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Kb, nlb,
               (int64_t)nlb * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
   // Ebar^{-1}; X_F = Ebar^{-1} Fbar; X_r = Ebar^{-1} r_u
-  inverse_f64(Eb, MPE, (int64_t)MPE * MPE, ec, p->d_err, s);
+  inverse_any(p, Eb, MPE, (int64_t)MPE * MPE, ec, s);
   gemm_c(p, gd(MPE, nlb, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlb, (int64_t)MPE * nlb, 0, XF, nlb,
               (int64_t)MPE * nlb, 0, 1.0, 0.0, n, 1), s);
   gemm_c(p, gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, sru, 0, Xr, R, (int64_t)MPE * R, 0, 1.0, 0.0, n, 1),
@@ -1218,6 +1291,11 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
   if (opts && (opts->poly_prec == HDG_BF16 || opts->inner_prec == HDG_BF16)) by += nfree * ms * b * b * 2;
   by += nfree * b * b * (8 + 4 + 8);                              // BJ
   if (opts && opts->pc == HDG_PC_ASM) by += NE * nlb * nlb * (8 + 8 + 4);
+  {  // scratch of the block inverses beyond one CTA's shared memory (Ebar, ASM patches)
+    const int nbig = (int)std::max<int64_t>(MPE, (opts && opts->pc == HDG_PC_ASM) ? nlb : 0);
+    const int64_t need = inverse_scratch(nbig);
+    if (need > 0) by += std::max<int64_t>(1, std::min<int64_t>(NE, (1ll << 27) / need)) * need * 8;
+  }
   const int m = opts ? opts->restart : 50;
   by += (int64_t)(m + 12) * nfree * b * R * 8;
   by += NE * nlb * R * 8;
@@ -1414,7 +1492,7 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       if (!p->d_bjtmp) p->d_bjtmp = (double*)p->dalloc(sizeof(double) * p->nfree * b * b);
       double* tmp = p->d_bjtmp;
       extract_diag(p->K64, p->s64, p->d_rowptr, b, p->nfree, tmp, s);
-      inverse_f64(tmp, b, (int64_t)b * b, p->nfree, p->d_err, s);
+      inverse_any(p, tmp, b, (int64_t)b * b, p->nfree, s);
       p->bs64 = padded_stride<double>((int64_t)b * b);
       p->bs32 = (int64_t)p->ld32 * b;
       p->bs16 = (int64_t)p->ld16 * b;
@@ -1432,12 +1510,11 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       if (st != HDG_OK) return st;
     } else if (o->pc == HDG_PC_ASM) {
       const int nlb = p->nlb;
-      if (nlb > inverse_max_n()) return HDG_ERR_ARG;
       if (!p->d_asmP) p->d_asmP = (double*)p->dalloc(sizeof(double) * p->NE * nlb * nlb);
       double* P = p->d_asmP;
       asm_build(p->d_Kbar, nlb, b, p->nl, p->NE, p->d_asm_lf, p->d_asm_cnt, p->d_asm_face_free, p->K64, p->s64,
                 p->d_rowptr, P, s);
-      inverse_f64(P, nlb, (int64_t)nlb * nlb, p->NE, p->d_err, s);
+      inverse_any(p, P, nlb, (int64_t)nlb * nlb, p->NE, s);
       p->as_s64 = padded_stride<double>((int64_t)nlb * b);
       p->as_ld32 = ld_f32(nlb);
       p->as_ld16 = ld_bf16(nlb);

@@ -47,6 +47,9 @@ bool gemm_ozaki_planes(const GemmDesc& d, unsigned char* planes, int64_t planes_
 // *err on a zero pivot.  Returns false if n is too large for one CTA.
 bool inverse_f64(double* A, int n, int64_t stride, int64_t count, unsigned* err, cudaStream_t s);
 int inverse_max_n();
+// Batched copy of a rows x cols submatrix between row-major FP64 arrays.
+void copy_block_f64(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss, int rows,
+                    int cols, int64_t count, cudaStream_t s);
 
 // --------------------------------------------------------------- block rows
 // out[u][row][r] = epilogue( sum_{s < cnt[u]} sum_{c < bc}

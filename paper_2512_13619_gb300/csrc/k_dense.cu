@@ -259,7 +259,30 @@ __global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int 
 
 size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)n * 4 + 16; }
 
+// dst[c][i][j] = src[c][i][j] for i < rows, j < cols (row-major, leading
+// dimensions ldd / lds, batch strides sd / ss); one CTA row per (c, i).
+__global__ void copy_block_kernel(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss,
+                                  int rows, int cols) {
+  const int64_t c = blockIdx.y;
+  const int i = blockIdx.x;
+  const double* a = src + c * ss + (int64_t)i * lds;
+  double* o = dst + c * sd + (int64_t)i * ldd;
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) o[j] = a[j];
+}
+
 }  // namespace
+
+void copy_block_f64(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss, int rows,
+                    int cols, int64_t count, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0 || count <= 0) return;
+  const int threads = cols >= 128 ? 128 : (cols >= 64 ? 64 : 32);
+  for (int64_t c0 = 0; c0 < count; c0 += 65535) {
+    const int64_t c = count - c0 < 65535 ? count - c0 : 65535;
+    count_launch();
+    copy_block_kernel<<<dim3((unsigned)rows, (unsigned)c), threads, 0, s>>>(dst + c0 * sd, ldd, sd, src + c0 * ss,
+                                                                          lds, ss, rows, cols);
+  }
+}
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0 || d.nb0 <= 0 || d.nb1 <= 0) return;

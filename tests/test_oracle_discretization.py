@@ -152,3 +152,77 @@ def test_structural_counts_golden():
     b = s.bsz
     pat = (abs(s.K) > 0).toarray().reshape(s.K.shape[0] // b, b, -1, b).any(axis=(1, 3))
     assert int(pat.sum()) == gold['cases']['tri_poisson_8_k2']['n_nonzero_blocks']
+
+
+# ------------------------------------------------- Neumann (traction) faces
+def _box_workload(phys, k, u, qf, f, g, M, perturb):
+    """(0,2) x (0,1) x (0,1), 4 x 2 x 2 hexahedra (interior vertices moved by
+    up to perturb * h: the mapped Q^k space then still holds the linear
+    fields, not the quadratic ones); Dirichlet faces at x = 0 only,
+    prescribed outward flux g on the five other sides."""
+    from hdg_inputs import mesh as meshmod
+    m = meshmod.box_hex_mesh((4, 2, 2), (2.0, 1.0, 1.0), perturb=perturb, seed=8)
+    ref = blk.reference_element(m, k, k + 4)
+    return W.Workload('box', m, ref, blk.face_permutations(m, ref), phys, 1, 'function', f, u, qf, k=k,
+                      dirichlet=W.boundary_faces_at(m, 0, 0.0), neumann_flux=g)
+
+
+def test_neumann_patch_poisson_exact():
+    """A quadratic u with Dirichlet data on one face and its outward flux
+    g = -grad u . n on the other five is reproduced exactly by Q^2 (HDG
+    consistency with flux boundary conditions)."""
+    w0 = _patch(W.hex_poisson(n=2, k=2), 2)
+    g = lambda x, n: -np.einsum('...d,...d->...', w0.q_exact(x)[..., 0, :], n)[..., None]
+    w = _box_workload(blk.poisson(3), 2, w0.u_exact, w0.q_exact, w0.f_exact, g, 1, 0.0)
+    assert w.face_neumann.sum() == 2 * 2 + 2 * (4 * 2) + 2 * (4 * 2) and w.face_dirichlet.sum() == 2 * 2
+    _, _, _, (eu, eq) = _solve_errors(w)
+    assert eu < 1e-11 and eq < 1e-10
+
+
+@pytest.mark.parametrize('k', [1, 2])
+def test_neumann_patch_elasticity_exact(k):
+    """Linear elasticity (lambda = 0.7, mu = 1.3) with u_a = c_a + G_ab x_b
+    (+ Q_abc x_b x_c for k = 2): body force f = -div sigma (constant), traction
+    data g = -sigma n on five sides, Dirichlet data on x = 0; Q^k reproduces u
+    and q = grad u exactly (k = 1 on a perturbed mesh)."""
+    lam, mu = 0.7, 1.3
+    rng = np.random.default_rng(12)
+    c0 = rng.standard_normal(3)
+    G = rng.standard_normal((3, 3))
+    Q = rng.standard_normal((3, 3, 3)) * (k >= 2)
+    Q = 0.5 * (Q + np.transpose(Q, (0, 2, 1)))              # symmetric in the two x indices
+
+    def u(x):
+        return c0 + x @ G.T + np.einsum('abc,...b,...c->...a', Q, x, x)
+
+    def qf(x):                                               # q[a, d] = du_a/dx_d
+        return G + 2.0 * np.einsum('adc,...c->...ad', Q, x)
+
+    def sigma(x):
+        q = qf(x)
+        tr = np.einsum('...aa->...', q)
+        return lam * tr[..., None, None] * np.eye(3) + mu * (q + np.swapaxes(q, -1, -2))
+
+    # div sigma_a = lam d_a(tr q) + mu (lap u_a + d_a div u) = 2 lam Q_bba + mu (2 Q_add + 2 Q_dad)
+    divs = 2 * lam * np.einsum('bba->a', Q) + mu * (2 * np.einsum('add->a', Q) + 2 * np.einsum('dad->a', Q))
+    f = lambda x: np.broadcast_to(-divs, x.shape[:-1] + (3,)).copy()
+    g = lambda x, n: -np.einsum('...ad,...d->...a', sigma(x), n)
+    w = _box_workload(blk.elasticity(3, lam, mu, 1.0), k, u, qf, f, g, 3, 0.15 if k == 1 else 0.0)
+    _, _, _, (eu, eq) = _solve_errors(w)
+    assert eu < 1e-10 and eq < 1e-9
+
+
+def test_beam_tip_deflection_timoshenko():
+    """Sec. 6.2 beam, 20 x 4 x 4 hexahedra, Q^2, lambda = mu = 1: the mean
+    tip deflection under unit traction t = (0, 0, -1) equals the compliance
+    r . uhat = <g, uhat> and agrees within 2% with Timoshenko beam theory,
+    delta = F L^3 / (3 E I) + F L / (kappa G A) = 200 + 6 (E = mu (3 lam +
+    2 mu) / (lam + mu) = 2.5, I = 1/12, G = mu = 1, kappa = 5/6, A = 1)."""
+    w = W.hex_beam(n=4, k=2)
+    assert w.face_dirichlet.sum() == 16 and w.n_elem == 320
+    s = OracleSystem(w)
+    uh = s.direct()
+    compliance = float(np.ravel(s.r) @ np.ravel(uh))
+    delta = 125.0 / (3 * 2.5 / 12.0) + 5.0 / (5.0 / 6.0)
+    assert compliance < 0.0                                  # deflects along the traction
+    assert abs(-compliance - delta) < 0.02 * delta
