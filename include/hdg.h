@@ -180,6 +180,44 @@ hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count,
                         const double* G, const double* H, const double* J,
                         const double* ru, const double* ruh, int on_device, void* stream);
 
+/* Physics of a linear HDG system (Eq. HDG): flux F_{a,d} = sum_{b,c}
+ * Cq[a][d][b][c] q_{b,c} + sum_b Cu[a][d][b] u_b, source -sum_b Rr[a][b] u_b,
+ * stabilisation S = tau I; q = grad u.  Host arrays, M components, D = 3:
+ * Cq M*3*M*3, Cu M*3*M (NULL: zero), Rr M*M (NULL: zero). */
+typedef struct {
+  const double* Cq;
+  const double* Cu;
+  const double* Rr;
+  double tau;
+} hdg_physics;
+
+/* Static condensation of hexahedral Q^k elements whose blocks are generated
+ * on the device (the element integrals of Sec. 4.1 as batched products of
+ * basis tables with quadrature weights, M = Phi W, then the blocks of
+ * Eq. matrixform), chunk by chunk, without the blocks ever leaving the GPU.
+ * Requires dim 3, N_lfe 6, P_E = (k+1)^3, P_F = (k+1)^2.  Reference element:
+ * Q^k on Gauss-Lobatto-Legendre nodes (x fastest), an nquad^3 Gauss rule
+ * (nquad^2 on faces), local face l fixing reference coordinate l/2 at -1
+ * (l even) or +1 (l odd) with parameters the other two coordinates in
+ * increasing order; trilinear geometry.
+ *   verts      count x 8 x 3: vertex v at reference corner (+-1 by bits 0,1,2 of v)
+ *   face_perm  count x 6 x P_F int32: the local face-node index of face l
+ *              that carries the face's global node j
+ *   ru, ruh    as hdg_condense (load vectors; count x M*P_E x R and
+ *              count x N_lfe*M*P_F x R)
+ * verts, face_perm, ru, ruh are host or device per on_device.  Errors:
+ * HDG_ERR_ARG (shapes, nquad outside 1..12, a face_perm entry outside
+ * 0..P_F-1), HDG_ERR_SINGULAR (a degenerate element), as hdg_condense. */
+hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad, const double* verts,
+                            const int32_t* face_perm, const hdg_physics* phys, const double* ru,
+                            const double* ruh, int on_device, void* stream);
+
+/* The generated blocks themselves (tests, callers that keep them): out[9]
+ * are device buffers for Me, Bd, Cd, D, E, F, G, H, J of `count` elements in
+ * hdg_condense's layout.  Inputs as hdg_condense_hex. */
+hdg_status hdg_hex_blocks(hdg_problem p, int64_t count, int nquad, const double* verts, const int32_t* face_perm,
+                          const hdg_physics* phys, double* const* out, int on_device, void* stream);
+
 /* hdg_condense with per-input element strides.  blocks[11] are the inputs in
  * the order Me, Bd, Cd, D, E, F, G, H, J, ru, ruh; elem_stride[i] (doubles)
  * is either the input's size per element (one block per element, as in

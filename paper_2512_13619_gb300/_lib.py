@@ -27,6 +27,10 @@ class hdg_mesh(ctypes.Structure):
                 ('elem_face', ctypes.c_void_p), ('face_elem', ctypes.c_void_p), ('face_dirichlet', ctypes.c_void_p)]
 
 
+class hdg_physics(ctypes.Structure):
+    _fields_ = [('Cq', ctypes.c_void_p), ('Cu', ctypes.c_void_p), ('Rr', ctypes.c_void_p), ('tau', ctypes.c_double)]
+
+
 class hdg_solver_opts(ctypes.Structure):
     _fields_ = [('restart', ctypes.c_int), ('max_iters', ctypes.c_int), ('rtol', ctypes.c_double),
                 ('orth', ctypes.c_int), ('pc', ctypes.c_int), ('poly', ctypes.c_int), ('poly_degree', ctypes.c_int),
@@ -74,6 +78,8 @@ _SIGS = {
                             ctypes.POINTER(ctypes.c_float)]),
     'hdg_tuning_candidates': (_I, [_V, _I, _I, ctypes.POINTER(_I), _I]),
     'hdg_set_tuning': (_I, [_V, _I, _I, ctypes.POINTER(_I)]),
+    'hdg_condense_hex': (_I, [_V, _I64, _I64, _I, _P, _P, ctypes.POINTER(hdg_physics), _P, _P, _I, _V]),
+    'hdg_hex_blocks': (_I, [_V, _I64, _I, _P, _P, ctypes.POINTER(hdg_physics), ctypes.POINTER(_P), _I, _V]),
 }
 
 _lib = None
@@ -150,6 +156,26 @@ def hdg_condense_strided(p, e0, count, blocks, elem_stride, on_device, stream=No
     arr = (_P * 11)(*[ptr(a) for a in blocks])
     st = (_I64 * 11)(*[int(x) for x in elem_stride]) if elem_stride is not None else None
     return load().hdg_condense_strided(p, e0, count, arr, st, int(on_device), stream_ptr(stream))
+
+
+def physics(Cq, Cu=None, Rr=None, tau=1.0):
+    """hdg_physics over host float64 arrays (returned with the arrays, which
+    must outlive the call)."""
+    import numpy as np
+    keep = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in (Cq, Cu, Rr)]
+    ph = hdg_physics(*[ptr(a) for a in keep], float(tau))
+    return ph, keep
+
+
+def hdg_condense_hex(p, e0, count, nquad, verts, face_perm, phys, ru, ruh, on_device, stream=None):
+    return load().hdg_condense_hex(p, e0, count, nquad, ptr(verts), ptr(face_perm), ctypes.byref(phys), ptr(ru),
+                                   ptr(ruh), int(on_device), stream_ptr(stream))
+
+
+def hdg_hex_blocks(p, count, nquad, verts, face_perm, phys, out, on_device, stream=None):
+    arr = (_P * 9)(*[ptr(a) for a in out])
+    return load().hdg_hex_blocks(p, count, nquad, ptr(verts), ptr(face_perm), ctypes.byref(phys), arr,
+                                 int(on_device), stream_ptr(stream))
 
 
 def hdg_set_dirichlet(p, uhat_dirichlet, on_device, stream=None):

@@ -178,6 +178,16 @@ struct hdg_problem_s {
   int64_t pex_cap = 0;
   double* d_invs = nullptr;        // scratch of the block inverses of matrices beyond one CTA's shared memory
   int64_t invs_cap = 0;            // (doubles, grown on demand)
+  // element-matrix generation of hexahedra: device tables for (hex_k, hex_nq), scratch, inputs
+  int hex_k = -1, hex_nq = -1;
+  HexTables hex_tab;
+  double* d_hextab = nullptr;
+  int64_t hextab_cap = 0;
+  double* d_gen = nullptr;
+  int64_t gen_cap = 0;
+  unsigned char* d_genin = nullptr;
+  int64_t genin_cap = 0;
+  double* d_phys = nullptr;
   // autotuned launch configurations [operation: K, BJ, ASM][precision]
   BrCfg tune[3][3];
   float tune_us[3][3] = {};        // measured time of the chosen configuration
@@ -1403,6 +1413,231 @@ hdg_status hdg_condense(hdg_problem p, int64_t e0, int64_t count, const double* 
                         void* stream) {
   const double* blocks[11] = {Me, Bd, Cd, Dm, Em, Fm, Gm, Hm, Jm, ru, ruh};
   return hdg_condense_strided(p, e0, count, blocks, nullptr, on_device, stream);
+}
+
+// ----------------------------------------------- generated hexahedral blocks
+}  // extern "C"
+namespace {
+
+template <typename T>
+T* grow(hdg_problem p, T*& buf, int64_t& cap, int64_t need) {
+  if (need > cap) {
+    p->dfree(buf, sizeof(T) * (size_t)cap);
+    buf = nullptr;
+    cap = 0;
+    buf = (T*)p->dalloc(sizeof(T) * (size_t)need);
+    cap = need;
+  }
+  return buf;
+}
+
+struct HexDev {
+  const double *phi, *dphi, *wq, *dN, *fphi, *fdN, *psi, *wf, *phiT, *fphiT;
+};
+
+// Validates the shapes, builds and uploads the reference tables for
+// (k, nquad) when they change, and uploads the physics.
+hdg_status hex_prepare(hdg_problem p, int nquad, const hdg_physics* ph, HexDev* dev, cudaStream_t s) {
+  if (!ph || !ph->Cq || nquad < 1 || nquad > 12) return HDG_ERR_ARG;
+  if (p->D != 3 || p->nl != 6) return HDG_ERR_ARG;
+  int n1 = 1;
+  while (n1 * n1 * n1 < p->PE) ++n1;
+  if (n1 * n1 * n1 != p->PE || n1 * n1 != p->PF || n1 < 2) return HDG_ERR_ARG;
+  const int k = n1 - 1;
+  if (p->hex_k != k || p->hex_nq != nquad) {
+    p->hex_tab = build_hex_tables(k, nquad);
+    const HexTables& T = p->hex_tab;
+    const std::vector<double>* parts[10] = {&T.phi, &T.dphi, &T.wq, &T.dN, &T.fphi, &T.fdN, &T.psi, &T.wf,
+                                            &T.phiT, &T.fphiT};
+    int64_t tot = 0;
+    for (auto* v : parts) tot += (int64_t)v->size();
+    grow(p, p->d_hextab, p->hextab_cap, tot);
+    int64_t off = 0;
+    for (auto* v : parts) {
+      CK(cudaMemcpyAsync(p->d_hextab + off, v->data(), sizeof(double) * v->size(), cudaMemcpyHostToDevice, s));
+      off += (int64_t)v->size();
+    }
+    CK(cudaStreamSynchronize(s));          // the host tables may change with the next call
+    p->hex_k = k;
+    p->hex_nq = nquad;
+  }
+  const HexTables& T = p->hex_tab;
+  const double* base = p->d_hextab;
+  const double** outs[10] = {&dev->phi, &dev->dphi, &dev->wq, &dev->dN, &dev->fphi, &dev->fdN, &dev->psi,
+                             &dev->wf, &dev->phiT, &dev->fphiT};
+  const std::vector<double>* parts[10] = {&T.phi, &T.dphi, &T.wq, &T.dN, &T.fphi, &T.fdN, &T.psi, &T.wf,
+                                          &T.phiT, &T.fphiT};
+  for (int i = 0; i < 10; ++i) {
+    *outs[i] = base;
+    base += parts[i]->size();
+  }
+  // physics: Cq, Cu, Rr
+  const int M = p->M;
+  std::vector<double> h((size_t)M * 9 * M + (size_t)M * 3 * M + (size_t)M * M, 0.0);
+  std::copy(ph->Cq, ph->Cq + (size_t)M * 9 * M, h.begin());
+  if (ph->Cu) std::copy(ph->Cu, ph->Cu + (size_t)M * 3 * M, h.begin() + (size_t)M * 9 * M);
+  if (ph->Rr) std::copy(ph->Rr, ph->Rr + (size_t)M * M, h.begin() + (size_t)M * 12 * M);
+  if (!p->d_phys) p->d_phys = (double*)p->dalloc(sizeof(double) * (size_t)25 * 13);   // M <= 5
+  if (M > 5) return HDG_ERR_ARG;
+  CK(cudaMemcpyAsync(p->d_phys, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return HDG_OK;
+}
+
+// Generates the blocks of `ec` elements into out[0..8] (Me, Bd, Cd, D..J;
+// element strides = the condensation input sizes).
+void hex_generate_chunk(hdg_problem p, const HexDev& dev, int64_t ec, const double* verts, const int32_t* perm,
+                        const hdg_physics* ph, double* const* out, cudaStream_t s) {
+  const HexTables& T = p->hex_tab;
+  const int PE = T.PE, PF = T.PF, nq = T.nq, nfq = T.nfq, F4 = 4 * PF;
+  double* g = grow(p, p->d_gen, p->gen_cap, ec * hex_gen_scratch(T));
+  HexGenDesc d;
+  d.count = ec;
+  d.M = p->M;
+  d.PE = PE;
+  d.PF = PF;
+  d.nq = nq;
+  d.nfq = nfq;
+  d.verts = verts;
+  d.perm = perm;
+  d.phi = dev.phi; d.dphi = dev.dphi; d.wq = dev.wq; d.dN = dev.dN;
+  d.fphi = dev.fphi; d.fdN = dev.fdN; d.psi = dev.psi; d.wf = dev.wf;
+  d.AW = g;                 g += ec * (int64_t)nq * PE;
+  d.GT = g;                 g += ec * (int64_t)3 * PE * nq;
+  d.BWN = g;                g += ec * (int64_t)6 * nfq * F4;
+  d.PW = g;                 g += ec * (int64_t)6 * nfq * PE;
+  d.PsiT = g;               g += ec * (int64_t)6 * PF * nfq;
+  d.Mf = g;                 g += ec * (int64_t)PE * PE;
+  d.EF4 = g;                g += ec * (int64_t)6 * PE * F4;
+  d.FF4 = g;
+  d.Cq = p->d_phys;
+  d.Cu = p->d_phys + (size_t)p->M * 9 * p->M;
+  d.Rr = p->d_phys + (size_t)p->M * 12 * p->M;
+  d.tau = ph->tau;
+  d.Me = out[0];
+  d.Sd = out[1];
+  d.Cd = out[2]; d.Dm = out[3]; d.Em = out[4]; d.Fm = out[5]; d.Gm = out[6]; d.Hm = out[7]; d.Jm = out[8];
+  d.err = p->d_err;
+  const int n = (int)ec;
+  hex_geometry(d, s);
+  // M^e = Phi^T (W Phi);  B_d = G_d^T (W Phi);  Mf = sum over faces Phi_f^T (W Phi_f)
+  gemm_c(p, gd(PE, PE, nq, dev.phiT, nq, 0, 0, d.AW, PE, (int64_t)nq * PE, 0, out[0], PE, (int64_t)PE * PE, 0, 1.0,
+              0.0, n, 1), s);
+  gemm_c(p, gd(PE, PE, nq, d.GT, nq, (int64_t)3 * PE * nq, (int64_t)PE * nq, d.AW, PE, (int64_t)nq * PE, 0, out[1],
+              PE, (int64_t)3 * PE * PE, (int64_t)PE * PE, 1.0, 0.0, n, 3), s);
+  gemm_c(p, gd(PE, PE, 6 * nfq, dev.fphiT, 6 * nfq, 0, 0, d.PW, PE, (int64_t)6 * nfq * PE, 0, d.Mf, PE,
+              (int64_t)PE * PE, 0, 1.0, 0.0, n, 1), s);
+  // per face: [EF | EFN_d] = Phi_f^T [W psi | W n_d psi],  [FF | FFN_d] = psi^T [W psi | W n_d psi]
+  gemm_c(p, gd(PE, F4, nfq, dev.fphiT, 6 * nfq, 0, nfq, d.BWN, F4, (int64_t)6 * nfq * F4, (int64_t)nfq * F4, d.EF4,
+              F4, (int64_t)6 * PE * F4, (int64_t)PE * F4, 1.0, 0.0, n, 6), s);
+  gemm_c(p, gd(PF, F4, nfq, d.PsiT, nfq, (int64_t)6 * PF * nfq, (int64_t)PF * nfq, d.BWN, F4, (int64_t)6 * nfq * F4,
+              (int64_t)nfq * F4, d.FF4, F4, (int64_t)6 * PF * F4, (int64_t)PF * F4, 1.0, 0.0, n, 6), s);
+  hex_expand(d, s);
+}
+
+// device copies of this chunk's vertices and face permutations
+void hex_inputs(hdg_problem p, int64_t c0, int64_t ec, const double* verts, const int32_t* perm, int on_device,
+                const double** dv, const int32_t** dp, cudaStream_t s) {
+  const int64_t nv = ec * 24, np = ec * 6 * (int64_t)p->PF;
+  if (on_device) {
+    *dv = verts + c0 * 24;
+    *dp = perm + c0 * 6 * (int64_t)p->PF;
+    return;
+  }
+  unsigned char* b = grow(p, p->d_genin, p->genin_cap, (int64_t)(sizeof(double) * nv + sizeof(int32_t) * np));
+  CK(cudaMemcpyAsync(b, verts + c0 * 24, sizeof(double) * nv, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b + sizeof(double) * nv, perm + c0 * 6 * (int64_t)p->PF, sizeof(int32_t) * np,
+                     cudaMemcpyHostToDevice, s));
+  *dv = (const double*)b;
+  *dp = (const int32_t*)(b + sizeof(double) * nv);
+}
+
+}  // namespace
+extern "C" {
+
+hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad, const double* verts,
+                            const int32_t* face_perm, const hdg_physics* phys, const double* ru, const double* ruh,
+                            int on_device, void* stream) {
+  if (!p || !verts || !face_perm || !ru || !ruh) return HDG_ERR_ARG;
+  if (e0 < 0 || count < 0 || e0 + count > p->NE) return HDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    HexDev dev;
+    hdg_status st = hex_prepare(p, nquad, phys, &dev, s);
+    if (st != HDG_OK) return st;
+    const InSizes z = in_sizes(p);
+    const int64_t sz[11] = {z.Me, z.Bd, z.Cd, z.D, z.E, z.F, z.G, z.H, z.J, z.ru, z.ruh};
+    const bool sh[11] = {false, false, false, false, false, false, false, false, false, false, false};
+    for (int64_t c0 = 0; c0 < count; c0 += p->chunk) {
+      const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
+      double* stg = p->d_stage;
+      double* out[11];
+      for (int i = 0; i < 11; ++i) {
+        out[i] = stg;
+        stg += ec * sz[i];
+      }
+      const double* dv;
+      const int32_t* dp;
+      hex_inputs(p, c0, ec, verts, face_perm, on_device, &dv, &dp, s);
+      hex_generate_chunk(p, dev, ec, dv, dp, phys, out, s);
+      const double* dru = ru + c0 * sz[9];
+      const double* druh = ruh + c0 * sz[10];
+      if (!on_device) {
+        CK(cudaMemcpyAsync(out[9], dru, sizeof(double) * ec * sz[9], cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(out[10], druh, sizeof(double) * ec * sz[10], cudaMemcpyHostToDevice, s));
+        dru = out[9];
+        druh = out[10];
+      }
+      condense_chunk(p, e0 + c0, ec, out[0], out[1], out[2], out[3], out[4], out[5], out[6], out[7], out[8], dru,
+                     druh, sh, s);
+      CK(cudaGetLastError());
+      for (int64_t e = e0 + c0; e < e0 + c0 + ec; ++e) {
+        if (!p->condensed[e]) {
+          p->condensed[e] = 1;
+          p->n_condensed++;
+        }
+      }
+    }
+    collect_timing(p, s);
+    p->assembled = false;
+    return HDG_OK;
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_hex_blocks(hdg_problem p, int64_t count, int nquad, const double* verts, const int32_t* face_perm,
+                          const hdg_physics* phys, double* const* out, int on_device, void* stream) {
+  if (!p || !verts || !face_perm || !out || count < 0) return HDG_ERR_ARG;
+  for (int i = 0; i < 9; ++i)
+    if (!out[i]) return HDG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    DeviceGuard dg(p->device);
+    HexDev dev;
+    hdg_status st = hex_prepare(p, nquad, phys, &dev, s);
+    if (st != HDG_OK) return st;
+    const InSizes z = in_sizes(p);
+    const int64_t sz[9] = {z.Me, z.Bd, z.Cd, z.D, z.E, z.F, z.G, z.H, z.J};
+    for (int64_t c0 = 0; c0 < count; c0 += p->chunk) {
+      const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
+      double* o[9];
+      for (int i = 0; i < 9; ++i) o[i] = out[i] + c0 * sz[i];
+      const double* dv;
+      const int32_t* dp;
+      hex_inputs(p, c0, ec, verts, face_perm, on_device, &dv, &dp, s);
+      hex_generate_chunk(p, dev, ec, dv, dp, phys, o, s);
+      CK(cudaGetLastError());
+    }
+    return check_err(p, s);
+  } catch (const CudaError& e) {
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
 }
 
 hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhatD, int on_device, void* stream) {

@@ -47,6 +47,48 @@ bool gemm_ozaki_planes(const GemmDesc& d, unsigned char* planes, int64_t planes_
 // *err on a zero pivot.  Returns false if n is too large for one CTA.
 bool inverse_f64(double* A, int n, int64_t stride, int64_t count, unsigned* err, cudaStream_t s);
 int inverse_max_n();
+// ------------------------------------------- hexahedral element matrices
+// Reference tables of Q^k on the cube with an n^3 / n^2 Gauss rule (host).
+struct HexTables {
+  int k = 0, n1 = 0, PE = 0, PF = 0, nq1 = 0, nq = 0, nfq = 0;
+  std::vector<double> phiT;    // PE x nq
+  std::vector<double> phi;     // nq x PE
+  std::vector<double> dphi;    // nq x PE x 3 (reference gradients)
+  std::vector<double> wq;      // nq
+  std::vector<double> dN;      // nq x 8 x 3 trilinear shape derivatives
+  std::vector<double> fphiT;   // PE x (6 nfq): phi at face points, column l nfq + q
+  std::vector<double> fphi;    // (6 nfq) x PE
+  std::vector<double> fdN;     // (6 nfq) x 8 x 3
+  std::vector<double> psi;     // nfq x PF face basis
+  std::vector<double> wf;      // nfq face weights
+};
+HexTables build_hex_tables(int k, int nquad);
+// per-element scratch (doubles) of the generation steps
+int64_t hex_gen_scratch(const HexTables& T);
+// device pointers of one generation chunk (count elements)
+struct HexGenDesc {
+  int64_t count;
+  int M, PE, PF, nq, nfq;
+  const double* verts;         // count x 8 x 3
+  const int32_t* perm;         // count x 6 x PF
+  // device copies of the tables
+  const double *phi, *dphi, *wq, *dN, *fphi, *fdN, *psi, *wf;
+  // scratch (per element, see hex_gen_scratch)
+  double *AW, *GT, *BWN, *PW, *PsiT, *Mf, *EF4, *FF4;
+  // physics (device): Cq M x 3 x M x 3, Cu M x 3 x M, Rr M x M
+  const double *Cq, *Cu, *Rr;
+  double tau;
+  // outputs (row-major per element, the condensation's input layout)
+  const double* Me;            // written by the mass product
+  const double* Sd;            // = Bd, written by the gradient products
+  double *Cd, *Dm, *Em, *Fm, *Gm, *Hm, *Jm;
+  unsigned* err;
+};
+// AW, GT, BWN, PW, PsiT from the vertices (two kernels)
+void hex_geometry(const HexGenDesc& d, cudaStream_t s);
+// Cd, D, E, F, G, H, J from Me, Sd, Mf, EF4, FF4 and the physics (seven kernels)
+void hex_expand(const HexGenDesc& d, cudaStream_t s);
+
 // Batched copy of a rows x cols submatrix between row-major FP64 arrays.
 void copy_block_f64(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss, int rows,
                     int cols, int64_t count, cudaStream_t s);

@@ -1,0 +1,467 @@
+// Element matrices of hexahedral Q^k HDG elements on the device: the step
+// before the static condensation (Welter & Nguyen, Sec. 4.1 writes the
+// element integrals as products of basis tables with quadrature weights,
+// M = Phi W, and Eq. matrixform assembles the blocks D..J from them).
+//
+// Conventions (shared with the host-side input generator, so that both
+// produce the same blocks for the same mesh):
+//  - reference cube [-1,1]^3; Q^k Lagrange basis on Gauss-Lobatto-Legendre
+//    nodes, node (i, j, l) at index i + (k+1) (j + (k+1) l), x fastest;
+//  - volume rule: n^3 Gauss-Legendre points, x fastest; face rule: n^2;
+//  - local face l = 2 axis + side fixes reference coordinate `axis` at
+//    -1 (side 0) or +1 (side 1); its parameters (s, t) are the two other
+//    coordinates in increasing axis order; face basis Q^k on GLL nodes in
+//    (s, t), node (i, j) at index i + (k+1) j;
+//  - trilinear geometry from 8 vertices, vertex v at reference corner
+//    ((v & 1 ? 1 : -1), (v & 2 ? 1 : -1), (v & 4 ? 1 : -1));
+//  - face_perm[e][l][j] = the local face-node index of element e's face l
+//    that carries the face's global node j.
+#include <cmath>
+#include <vector>
+
+#include "hdg_common.cuh"
+#include "hdg_internal.h"
+
+namespace hdg {
+
+// ------------------------------------------------------------ 1D tables
+namespace {
+
+// Legendre P_n and P_n' at x by the three-term recurrence.
+void legendre(int n, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int m = 1; m < n; ++m) {
+    const double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  *dP = n * (x * p1 - p0) / (x * x - 1.0);     // interior points only
+}
+
+// n-point Gauss-Legendre rule: roots of P_n by Newton's method from the
+// asymptotic guesses cos(pi (i + 3/4) / (n + 1/2)); w = 2 / ((1 - x^2) P_n'^2).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double P, dP;
+    for (int it = 0; it < 100; ++it) {
+      legendre(n, t, &P, &dP);
+      const double dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    legendre(n, t, &P, &dP);
+    x[n - 1 - i] = t;                          // ascending
+    w[n - 1 - i] = 2.0 / ((1.0 - t * t) * dP * dP);
+  }
+}
+
+// k+1 Gauss-Lobatto-Legendre nodes: -1, the roots of P_k', +1.  Newton on
+// P_k' with P_k'' = (2 x P_k' - k (k+1) P_k) / (1 - x^2), from the
+// Chebyshev-Lobatto points.
+std::vector<double> gll_nodes(int k) {
+  std::vector<double> g(k + 1);
+  if (k == 0) {
+    g[0] = 0.0;
+    return g;
+  }
+  g[0] = -1.0;
+  g[k] = 1.0;
+  for (int i = 1; i < k; ++i) {
+    double t = -std::cos(M_PI * i / k);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(k, t, &P, &dP);
+      const double d2 = (2.0 * t * dP - k * (k + 1.0) * P) / (1.0 - t * t);
+      const double dt = dP / d2;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    g[i] = t;
+  }
+  return g;
+}
+
+// Lagrange polynomials through `nodes` and their derivatives at t (product form).
+void lagrange(const std::vector<double>& nodes, double t, double* phi, double* dphi) {
+  const int n = (int)nodes.size();
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0, d = 0.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == j) continue;
+      const double den = nodes[j] - nodes[m];
+      d = d * (t - nodes[m]) / den + v / den;    // product rule, one factor at a time
+      v *= (t - nodes[m]) / den;
+    }
+    phi[j] = v;
+    dphi[j] = d;
+  }
+}
+
+// Q^k values and reference gradients at a point of the cube.
+void hex_basis_at(const std::vector<double>& g, const double xi[3], double* phi, double* dphi /* PE x 3 */) {
+  const int n1 = (int)g.size();
+  std::vector<double> p[3], dp[3];
+  for (int a = 0; a < 3; ++a) {
+    p[a].resize(n1);
+    dp[a].resize(n1);
+    lagrange(g, xi[a], p[a].data(), dp[a].data());
+  }
+  for (int l = 0; l < n1; ++l)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        const int idx = (l * n1 + j) * n1 + i;
+        phi[idx] = p[0][i] * p[1][j] * p[2][l];
+        if (dphi) {
+          dphi[idx * 3 + 0] = dp[0][i] * p[1][j] * p[2][l];
+          dphi[idx * 3 + 1] = p[0][i] * dp[1][j] * p[2][l];
+          dphi[idx * 3 + 2] = p[0][i] * p[1][j] * dp[2][l];
+        }
+      }
+}
+
+// derivatives of the 8 trilinear shape functions at xi: dN[v*3 + b]
+void trilinear_dN(const double xi[3], double* dN) {
+  for (int v = 0; v < 8; ++v) {
+    const double s[3] = {(v & 1) ? 1.0 : -1.0, (v & 2) ? 1.0 : -1.0, (v & 4) ? 1.0 : -1.0};
+    for (int b = 0; b < 3; ++b) {
+      double f = s[b] / 8.0;
+      for (int c = 0; c < 3; ++c)
+        if (c != b) f *= 1.0 + xi[c] * s[c];
+      dN[v * 3 + b] = f;
+    }
+  }
+}
+
+void face_point(int l, double s, double t, double xi[3]) {
+  const int ax = l / 2;
+  const int a0 = ax == 0 ? 1 : 0, a1 = ax == 2 ? 1 : 2;
+  xi[ax] = (l & 1) ? 1.0 : -1.0;
+  xi[a0] = s;
+  xi[a1] = t;
+}
+
+}  // namespace
+
+HexTables build_hex_tables(int k, int nquad) {
+  HexTables T;
+  T.k = k;
+  T.n1 = k + 1;
+  T.PE = T.n1 * T.n1 * T.n1;
+  T.PF = T.n1 * T.n1;
+  T.nq1 = nquad;
+  T.nq = nquad * nquad * nquad;
+  T.nfq = nquad * nquad;
+  const std::vector<double> g = gll_nodes(k);
+  std::vector<double> x, w;
+  gauss_legendre(nquad, x, w);
+  const int PE = T.PE, PF = T.PF, nq = T.nq, nfq = T.nfq, n = nquad;
+  T.phiT.assign((size_t)PE * nq, 0.0);
+  T.phi.assign((size_t)nq * PE, 0.0);
+  T.dphi.assign((size_t)nq * PE * 3, 0.0);
+  T.wq.assign(nq, 0.0);
+  T.dN.assign((size_t)nq * 24, 0.0);
+  for (int l = 0; l < n; ++l)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const int q = (l * n + j) * n + i;
+        const double xi[3] = {x[i], x[j], x[l]};
+        hex_basis_at(g, xi, &T.phi[(size_t)q * PE], &T.dphi[(size_t)q * PE * 3]);
+        T.wq[q] = w[i] * w[j] * w[l];
+        trilinear_dN(xi, &T.dN[(size_t)q * 24]);
+        for (int a = 0; a < PE; ++a) T.phiT[(size_t)a * nq + q] = T.phi[(size_t)q * PE + a];
+      }
+  // faces: phi at the face points (PE x 6 nfq, column l nfq + q), trilinear
+  // derivatives there, face basis psi (nfq x PF) and face weights
+  T.fphiT.assign((size_t)PE * 6 * nfq, 0.0);
+  T.fphi.assign((size_t)6 * nfq * PE, 0.0);
+  T.fdN.assign((size_t)6 * nfq * 24, 0.0);
+  T.psi.assign((size_t)nfq * PF, 0.0);
+  T.wf.assign(nfq, 0.0);
+  std::vector<double> ps(T.n1), pt(T.n1), dum(T.n1);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const int q = j * n + i;
+      T.wf[q] = w[i] * w[j];
+      lagrange(g, x[i], ps.data(), dum.data());
+      lagrange(g, x[j], pt.data(), dum.data());
+      for (int b = 0; b < T.n1; ++b)
+        for (int a = 0; a < T.n1; ++a) T.psi[(size_t)q * PF + b * T.n1 + a] = ps[a] * pt[b];
+      for (int l = 0; l < 6; ++l) {
+        double xi[3];
+        face_point(l, x[i], x[j], xi);
+        double* ph = &T.fphi[((size_t)l * nfq + q) * PE];
+        hex_basis_at(g, xi, ph, nullptr);
+        for (int a = 0; a < PE; ++a) T.fphiT[(size_t)a * 6 * nfq + l * nfq + q] = ph[a];
+        trilinear_dN(xi, &T.fdN[((size_t)l * nfq + q) * 24]);
+      }
+    }
+  return T;
+}
+
+int64_t hex_gen_scratch(const HexTables& T) {
+  const int64_t PE = T.PE, PF = T.PF, nq = T.nq, nfq = T.nfq;
+  return nq * PE            // AW: w |det J| phi
+         + 3 * PE * nq      // GT: physical gradients, transposed
+         + 6 * nfq * 4 * PF // BWN: w psi, w n_d psi per face
+         + 6 * nfq * PE     // PW: w phi at face points
+         + 6 * PF * nfq     // PsiT: permuted face basis, transposed
+         + PE * PE          // Mf
+         + 6 * PE * 4 * PF  // EF4: [EF | EFN_0 | EFN_1 | EFN_2] per face
+         + 6 * PF * 4 * PF; // FF4: [FF | FFN_0 | FFN_1 | FFN_2] per face
+}
+
+namespace {
+
+__device__ __forceinline__ void jac_at(const double* X8, const double* dN, double J[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int v = 0; v < 8; ++v) s += dN[v * 3 + b] * X8[v * 3 + a];
+      J[a][b] = s;
+    }
+}
+
+// adjugate (transpose of the cofactor matrix) and determinant of J
+__device__ __forceinline__ double adj3(const double J[3][3], double A[3][3]) {
+  A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+}
+
+// One CTA per element: per volume point q the Jacobian, |det|, J^{-1};
+// then AW[q][i] = w_q |det J_q| phi_i(x_q) and GT[d][i][q] = (grad phi_i)_d.
+__global__ void hex_vol_geom_kernel(HexGenDesc d) {
+  extern __shared__ double sm[];
+  double* X8 = sm;                 // 24
+  double* geo = sm + 24;           // nq x 10: wJ, Jinv (3 x 3, [b][a] = dxi_b/dx_a)
+  const int64_t e = blockIdx.x;
+  const int nq = d.nq, PE = d.PE;
+  for (int i = threadIdx.x; i < 24; i += blockDim.x) X8[i] = d.verts[e * 24 + i];
+  __syncthreads();
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double J[3][3], A[3][3];
+    jac_at(X8, d.dN + (int64_t)q * 24, J);
+    const double det = adj3(J, A);
+    if (!(det != 0.0) || !isfinite(det)) atomicOr(d.err, ERRBIT_SINGULAR);
+    const double inv = 1.0 / det;
+    double* gq = geo + q * 10;
+    gq[0] = d.wq[q] * fabs(det);
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) gq[1 + b * 3 + a] = A[b][a] * inv;
+  }
+  __syncthreads();
+  double* AW = d.AW + e * (int64_t)nq * PE;
+  double* GT = d.GT + e * (int64_t)3 * PE * nq;
+  for (int idx = threadIdx.x; idx < nq * PE; idx += blockDim.x) {
+    const int q = idx / PE, i = idx - q * PE;
+    const double* gq = geo + q * 10;
+    AW[idx] = gq[0] * d.phi[idx];
+    const double* dp = d.dphi + (int64_t)idx * 3;
+    for (int a = 0; a < 3; ++a)
+      GT[((int64_t)a * PE + i) * nq + q] = dp[0] * gq[1 + a] + dp[1] * gq[4 + a] + dp[2] * gq[7 + a];
+  }
+}
+
+// One CTA per element: per face point the cofactor normal nv = adj(J)^T e_l,
+// dA = |nv|, n = nv / dA, w = w_q dA; then the weighted face tables.
+__global__ void hex_face_geom_kernel(HexGenDesc d) {
+  extern __shared__ double sm[];
+  double* X8 = sm;                 // 24
+  double* geo = sm + 24;           // 6 nfq x 4: w, n
+  const int64_t e = blockIdx.x;
+  const int nfq = d.nfq, PE = d.PE, PF = d.PF, F4 = 4 * PF;
+  for (int i = threadIdx.x; i < 24; i += blockDim.x) X8[i] = d.verts[e * 24 + i];
+  __syncthreads();
+  for (int lq = threadIdx.x; lq < 6 * nfq; lq += blockDim.x) {
+    const int l = lq / nfq, q = lq - l * nfq;
+    double J[3][3], A[3][3];
+    jac_at(X8, d.fdN + (int64_t)lq * 24, J);
+    adj3(J, A);
+    const int ax = l / 2;
+    const double sgn = (l & 1) ? 1.0 : -1.0;
+    double nv[3];
+    for (int a = 0; a < 3; ++a) nv[a] = sgn * A[ax][a];
+    const double dA = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    if (!(dA > 0.0) || !isfinite(dA)) atomicOr(d.err, ERRBIT_SINGULAR);
+    double* gq = geo + lq * 4;
+    gq[0] = d.wf[q] * dA;
+    for (int a = 0; a < 3; ++a) gq[1 + a] = nv[a] / dA;
+  }
+  __syncthreads();
+  const int32_t* perm = d.perm + e * (int64_t)6 * PF;
+  double* BWN = d.BWN + e * (int64_t)6 * nfq * F4;
+  double* PW = d.PW + e * (int64_t)6 * nfq * PE;
+  double* PsiT = d.PsiT + e * (int64_t)6 * PF * nfq;
+  for (int idx = threadIdx.x; idx < 6 * nfq * PF; idx += blockDim.x) {
+    const int lq = idx / PF, j = idx - lq * PF;
+    const int l = lq / nfq, q = lq - l * nfq;
+    const int pj = perm[l * PF + j];
+    const double ps = (pj >= 0 && pj < PF) ? d.psi[(int64_t)q * PF + pj] : 0.0;
+    if (pj < 0 || pj >= PF) atomicOr(d.err, ERRBIT_ARG);
+    const double* gq = geo + lq * 4;
+    double* row = BWN + (int64_t)lq * F4;
+    row[j] = gq[0] * ps;
+    row[PF + j] = gq[0] * gq[1] * ps;
+    row[2 * PF + j] = gq[0] * gq[2] * ps;
+    row[3 * PF + j] = gq[0] * gq[3] * ps;
+    PsiT[((int64_t)l * PF + j) * nfq + q] = ps;
+  }
+  for (int idx = threadIdx.x; idx < 6 * nfq * PE; idx += blockDim.x) {
+    const int lq = idx / PE;
+    PW[idx] = geo[lq * 4] * d.fphi[idx];
+  }
+}
+
+// The blocks of Eq. matrixform from the element integrals and the physics
+// tensors, one output entry per thread (grid-stride), written in the
+// row-major per-element layout of the condensation inputs:
+//   Cd[d][i][l PF + j]   = -EFN[l,d][i,j]
+//   D[(a,i),(b,c,k)]     = sum_d Cq[a,d,b,c] Sd[d][k][i]
+//   E[(a,i),(b,j)]       = -sum_d Cu[a,d,b] Sd[d][i][j] + tau d_ab Mf[i][j] + Rr[a,b] Me[i][j]
+//   F[(a,i),(l,b,j)]     = sum_d Cu[a,d,b] EFN[l,d][i,j] - tau d_ab EF[l][i,j]
+//   G[(l,a,j),(b,c,k)]   = sum_d Cq[a,d,b,c] EFN[l,d][k,j]
+//   H[(l,a,j),(b,k)]     = tau d_ab EF[l][k,j]
+//   J[(l,a,j),(l',b,k)]  = d_ll' (sum_d Cu[a,d,b] FFN[l,d][k,j] - tau d_ab FF[l][k,j])
+template <int WHICH>
+__global__ void hex_expand_kernel(HexGenDesc d) {
+  const int M = d.M, PE = d.PE, PF = d.PF, F4 = 4 * PF;
+  const int MPE = M * PE, MDPE = 3 * MPE, nlb = 6 * M * PF;
+  int64_t per;
+  switch (WHICH) {
+    case 0: per = (int64_t)3 * PE * 6 * PF; break;
+    case 1: per = (int64_t)MPE * MDPE; break;
+    case 2: per = (int64_t)MPE * MPE; break;
+    case 3: per = (int64_t)MPE * nlb; break;
+    case 4: per = (int64_t)nlb * MDPE; break;
+    case 5: per = (int64_t)nlb * MPE; break;
+    default: per = (int64_t)nlb * nlb; break;
+  }
+  const int64_t total = per * d.count;
+  const double tau = d.tau;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / per;
+    const int64_t o = t - e * per;
+    const double* Me = d.Me + e * (int64_t)PE * PE;
+    const double* Sd = d.Sd + e * (int64_t)3 * PE * PE;
+    const double* Mf = d.Mf + e * (int64_t)PE * PE;
+    const double* EF4 = d.EF4 + e * (int64_t)6 * PE * F4;
+    const double* FF4 = d.FF4 + e * (int64_t)6 * PF * F4;
+    double v = 0.0;
+    if (WHICH == 0) {                                           // Cd
+      const int dd = (int)(o / (PE * 6 * PF));
+      const int rem = (int)(o - (int64_t)dd * PE * 6 * PF);
+      const int i = rem / (6 * PF), c = rem - i * 6 * PF;
+      const int l = c / PF, j = c - l * PF;
+      v = -EF4[((int64_t)l * PE + i) * F4 + (1 + dd) * PF + j];
+      d.Cd[e * per + o] = v;
+    } else if (WHICH == 1) {                                    // D
+      const int row = (int)(o / MDPE), col = (int)(o - (int64_t)row * MDPE);
+      const int a = row / PE, i = row - a * PE;
+      const int bc = col / PE, k = col - bc * PE;
+      const int b = bc / 3, c = bc - b * 3;
+      for (int dd = 0; dd < 3; ++dd) v += d.Cq[((a * 3 + dd) * M + b) * 3 + c] * Sd[((int64_t)dd * PE + k) * PE + i];
+      d.Dm[e * per + o] = v;
+    } else if (WHICH == 2) {                                    // E
+      const int row = (int)(o / MPE), col = (int)(o - (int64_t)row * MPE);
+      const int a = row / PE, i = row - a * PE;
+      const int b = col / PE, j = col - b * PE;
+      for (int dd = 0; dd < 3; ++dd) v -= d.Cu[(a * 3 + dd) * M + b] * Sd[((int64_t)dd * PE + i) * PE + j];
+      if (a == b) v += tau * Mf[i * PE + j];
+      v += d.Rr[a * M + b] * Me[i * PE + j];
+      d.Em[e * per + o] = v;
+    } else if (WHICH == 3) {                                    // F
+      const int row = (int)(o / nlb), col = (int)(o - (int64_t)row * nlb);
+      const int a = row / PE, i = row - a * PE;
+      const int lb = col / PF, j = col - lb * PF;
+      const int l = lb / M, b = lb - l * M;
+      const double* ef = EF4 + ((int64_t)l * PE + i) * F4;
+      for (int dd = 0; dd < 3; ++dd) v += d.Cu[(a * 3 + dd) * M + b] * ef[(1 + dd) * PF + j];
+      if (a == b) v -= tau * ef[j];
+      d.Fm[e * per + o] = v;
+    } else if (WHICH == 4) {                                    // G
+      const int row = (int)(o / MDPE), col = (int)(o - (int64_t)row * MDPE);
+      const int la = row / PF, j = row - la * PF;
+      const int l = la / M, a = la - l * M;
+      const int bc = col / PE, k = col - bc * PE;
+      const int b = bc / 3, c = bc - b * 3;
+      const double* ef = EF4 + ((int64_t)l * PE + k) * F4;
+      for (int dd = 0; dd < 3; ++dd) v += d.Cq[((a * 3 + dd) * M + b) * 3 + c] * ef[(1 + dd) * PF + j];
+      d.Gm[e * per + o] = v;
+    } else if (WHICH == 5) {                                    // H
+      const int row = (int)(o / MPE), col = (int)(o - (int64_t)row * MPE);
+      const int la = row / PF, j = row - la * PF;
+      const int l = la / M, a = la - l * M;
+      const int b = col / PE, k = col - b * PE;
+      if (a == b) v = tau * EF4[((int64_t)l * PE + k) * F4 + j];
+      d.Hm[e * per + o] = v;
+    } else {                                                    // J
+      const int row = (int)(o / nlb), col = (int)(o - (int64_t)row * nlb);
+      const int la = row / PF, j = row - la * PF;
+      const int l = la / M, a = la - l * M;
+      const int lb = col / PF, k = col - lb * PF;
+      const int l2 = lb / M, b = lb - l2 * M;
+      if (l == l2) {
+        const double* ff = FF4 + ((int64_t)l * PF + k) * F4;
+        for (int dd = 0; dd < 3; ++dd) v += d.Cu[(a * 3 + dd) * M + b] * ff[(1 + dd) * PF + j];
+        if (a == b) v -= tau * ff[j];
+      }
+      d.Jm[e * per + o] = v;
+    }
+  }
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+template <int W>
+void launch_expand(const HexGenDesc& d, cudaStream_t s) {
+  count_launch();
+  hex_expand_kernel<W><<<sm_count() * 8, 256, 0, s>>>(d);
+}
+
+}  // namespace
+
+void hex_geometry(const HexGenDesc& d, cudaStream_t s) {
+  if (d.count <= 0) return;
+  const size_t sv = sizeof(double) * (24 + (size_t)d.nq * 10);
+  const size_t sf = sizeof(double) * (24 + (size_t)6 * d.nfq * 4);
+  cudaFuncSetAttribute(hex_vol_geom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(hex_face_geom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  count_launch();
+  hex_vol_geom_kernel<<<(unsigned)d.count, 256, sv, s>>>(d);
+  count_launch();
+  hex_face_geom_kernel<<<(unsigned)d.count, 256, sf, s>>>(d);
+}
+
+void hex_expand(const HexGenDesc& d, cudaStream_t s) {
+  if (d.count <= 0) return;
+  launch_expand<0>(d, s);
+  launch_expand<1>(d, s);
+  launch_expand<2>(d, s);
+  launch_expand<3>(d, s);
+  launch_expand<4>(d, s);
+  launch_expand<5>(d, s);
+  launch_expand<6>(d, s);
+}
+
+}  // namespace hdg

@@ -38,6 +38,18 @@ def opts(restart=50, max_iters=1000, rtol=1e-10, orth='cgs', pc='bj', poly=None,
 BLOCK_NAMES = ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J', 'ru', 'ruh')
 
 
+def hex_geometry_inputs(w, e0=0, count=None):
+    """(verts (count, 8, 3), face_perm (count, 6, P_F) int32, nquad) of a
+    hexahedral workload, the geometry inputs of hdg_condense_hex."""
+    count = w.n_elem - e0 if count is None else count
+    m = w.mesh
+    verts = np.ascontiguousarray(m.verts[m.elems[e0:e0 + count]], dtype=np.float64)
+    perm = np.ascontiguousarray(w.perm[e0:e0 + count], dtype=np.int32)
+    nquad = int(round(len(w.ref.vol_wts) ** (1.0 / 3.0)))
+    assert nquad ** 3 == len(w.ref.vol_wts)
+    return verts, perm, nquad
+
+
 class Problem:
     def __init__(self, dim, n_lfe, M, PE, PF, elem_face, face_elem, face_dirichlet, nrhs=1, device=0):
         self._ef = np.ascontiguousarray(elem_face, dtype=np.int32)
@@ -79,6 +91,18 @@ class Problem:
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
         count = arrs[0].shape[0]
         check(L.hdg_condense(self.h, e0, count, *arrs, on_device, stream), 'hdg_condense')
+
+    def condense_hex(self, w, e0=0, count=None, stream=None):
+        """Generate the element blocks of a hexahedral workload on the device
+        and condense them (hdg_condense_hex); host inputs: the vertices, the
+        face permutations, the physics tensors and the load vectors."""
+        count = w.n_elem - e0 if count is None else count
+        verts, perm, nquad = hex_geometry_inputs(w, e0, count)
+        ph, keep = L.physics(w.phys.Cq, w.phys.Cu, w.phys.Rr, w.phys.tau)
+        b = w.blocks(e0, e0 + count)
+        ru = np.ascontiguousarray(b['ru'], dtype=np.float64)
+        ruh = np.ascontiguousarray(b['ruh'], dtype=np.float64)
+        check(L.hdg_condense_hex(self.h, e0, count, nquad, verts, perm, ph, ru, ruh, 0, stream), 'hdg_condense_hex')
 
     def set_dirichlet(self, uhatD, on_device=False, stream=None):
         if not on_device:
