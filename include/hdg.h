@@ -403,11 +403,13 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
  * prec: HDG_FP64 / HDG_FP32 / HDG_BF16 block storage.
  * A configuration is three ints {kind, sp, cps}: kind 0 = heuristic default
  * (vectorised 16-byte loads for FP32/BF16 blocks whose rows divide into
- * 16-byte groups, else one thread per row), 1 = shared-memory staging with
- * bulk copies, 2 = one thread per output row, 3 = 16-byte loads of 4 (FP32)
- * or 8 (BF16) rows per thread with the slots of a row split over sp adjacent
- * lanes (sp in {1,2,4,8}); cps = CTAs per SM of the grid-stride launch
- * (0 = heuristic).  Every configuration computes the same sums; they differ
+ * 16-byte groups; FP64 rows split over slot parts when one thread per row
+ * would fill less than 2048 threads per SM; else one thread per row), 1 =
+ * shared-memory staging with bulk copies, 2 = one thread per output row, 3 =
+ * 16-byte loads of 4 (FP32) or 8 (BF16) rows per thread with the slots of a
+ * row split over sp adjacent lanes (sp in {1,2,4,8}), 4 = FP64 rows with the
+ * slots split over sp adjacent lanes (sp in {2,4,8}) and a shuffle
+ * reduction; cps = CTAs per SM of the grid-stride launch (0 = heuristic).  Every configuration computes the same sums; they differ
  * in summation order only. */
 
 /* Time every candidate configuration of every operation the problem can run

@@ -120,10 +120,12 @@ struct BlockRowDesc {
 };
 // Launch configuration of a block-row product.  kind: BR_DEFAULT (heuristic:
 // vectorised loads for FP32/BF16 where the rows allow, else one thread per
-// row), BR_TMA (bulk-copy staging), BR_DIRECT (one thread per row), BR_VEC
-// (VR rows per thread, 16-byte loads, sp slot parts).  cps: CTAs per SM of the
-// grid-stride launch (0 = heuristic).
-enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3 };
+// row; FP64 rows split over slot parts when one thread per row would leave
+// the SMs mostly idle), BR_TMA (bulk-copy staging), BR_DIRECT (one thread per
+// row), BR_VEC (VR rows per thread, 16-byte loads, sp slot parts), BR_SPLIT
+// (sp threads per row, each summing every sp-th slot, shuffle reduction).
+// cps: CTAs per SM of the grid-stride launch (0 = heuristic).
+enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4 };
 struct BrCfg {
   int kind = BR_DEFAULT, sp = 0, cps = 0;
 };

@@ -305,6 +305,60 @@ __global__ void __launch_bounds__(512) blockrow_direct_kernel(BlockRowDesc d) {
   }
 }
 
+// Rows split over SP slot parts: thread t serves part t % SP of row
+// (t / SP) % b_rows of unit t / (SP b_rows) in its group; part p sums slots
+// p, p + SP, ...; the SP partial sums of a row sit in SP adjacent lanes of one
+// warp and are added by shuffles (every lane takes part, so idle lanes carry
+// zeros).  For small meshes, where one thread per row leaves most of the SMs'
+// warp slots empty.
+template <typename T, int R, int BC, int SP>
+__global__ void __launch_bounds__(512) blockrow_split_kernel(BlockRowDesc d) {
+  using A = typename Acc<T>::type;
+  if (!any_active(d.active, R)) return;
+  const int bc = BC > 0 ? BC : d.bc;
+  const int ldb = std::is_same<T, double>::value ? d.b_rows : d.ld;
+  const int per_unit = d.b_rows * SP;
+  const int G = blockDim.x / per_unit;
+  const int part = threadIdx.x % SP;
+  const int rr = threadIdx.x / SP;
+  const int gu = rr / d.b_rows;
+  const int row = rr - gu * d.b_rows;
+  const T* blk = static_cast<const T*>(d.blk);
+  const int64_t ngroups = (d.n_units + G - 1) / G;
+  // every CTA runs the same number of group iterations, so the shuffles see full warps
+  for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x) {
+    const int64_t grp = g0 + blockIdx.x;
+    const int64_t u = grp * G + gu;
+    const bool live = grp < ngroups && gu < G && u < d.n_units;
+    A acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = (A)0;
+    if (live) {
+      const int n = d.cnt[u];
+      const int64_t rp = d.rowptr[u];
+      const int32_t* nbr = d.nbr + u * d.max_slots;
+      for (int s = part; s < n; s += SP) {
+        const int64_t xb = (int64_t)nbr[s] * bc * R;
+        const T* bs = blk + (rp + s) * d.blk_stride + row;
+#pragma unroll 4
+        for (int c = 0; c < bc; ++c) {
+          const A kv = cvt<A>(__ldg(bs + (size_t)c * ldb));
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] = fma(kv, load_x<A>(d, xb + c * R + r), acc[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = SP / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (live && part == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) epi_store(d, u, row, r, (double)acc[r]);
+    }
+  }
+}
+
 // FP32/BF16 blocks: each thread owns VR consecutive rows of a unit, so one
 // 16-byte load brings VR rows of a column (column-major blocks, rows
 // contiguous).  Requires ld % VR == 0 (the FP32/BF16 copies pad every column
@@ -526,11 +580,50 @@ bool bc_compiled(int bc) {
   return bc == 3 || bc == 4 || bc == 9 || bc == 16 || bc == 20 || bc == 27 || bc == 45;
 }
 
+// Slot parts for an FP64 product under the heuristic: the largest SP <= 8
+// (and <= the slots per unit, SP b_rows <= 512) with at most 2048 threads per
+// SM in all; 1 when one thread per row already fills that.
+int split_parts(const BlockRowDesc& d) {
+  const int64_t threads = d.n_units * (int64_t)d.b_rows;
+  int sp = 1;
+  while (sp < 8 && 2 * sp <= d.max_slots && 2 * sp * d.b_rows <= 512 &&
+         threads * 2 * sp <= (int64_t)num_sms() * 2048)
+    sp *= 2;
+  return sp;
+}
+
+template <typename T, int R, int BC, int SP>
+void launch_split_sp(const BlockRowDesc& d, int cps, cudaStream_t s) {
+  const int per_unit = d.b_rows * SP;
+  const int NT = pick_nt_direct(per_unit);
+  const int G = NT / per_unit;
+  const int64_t ngroups = (d.n_units + G - 1) / G;
+  int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * (cps > 0 ? cps : 8));
+  if (grid < 1) grid = 1;
+  count_launch(); blockrow_split_kernel<T, R, BC, SP><<<(unsigned)grid, NT, 0, s>>>(d);
+}
+
+template <typename T, int R, int BC>
+void launch_split(const BlockRowDesc& d, int sp, int cps, cudaStream_t s) {
+  switch (sp) {
+    case 2: launch_split_sp<T, R, BC, 2>(d, cps, s); break;
+    case 4: launch_split_sp<T, R, BC, 4>(d, cps, s); break;
+    default: launch_split_sp<T, R, BC, 8>(d, cps, s); break;
+  }
+}
+
 template <typename T, int R, int BC>
 void launch_direct_bc(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
   if constexpr (!std::is_same<T, double>::value && BC > 0) {
     if ((cfg.kind == BR_DEFAULT || cfg.kind == BR_VEC) && vec_ok<T>(d)) {
       launch_vec<T, R, BC>(d, cfg.sp, cfg.cps, s);
+      return;
+    }
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    const int sp = cfg.kind == BR_SPLIT ? cfg.sp : (cfg.kind == BR_DEFAULT ? split_parts(d) : 1);
+    if (sp > 1 && sp * d.b_rows <= 512) {
+      launch_split<T, R, 0>(d, sp, cfg.cps, s);     // the column count stays a run-time value
       return;
     }
   }
@@ -583,7 +676,11 @@ int candidates_T(const BlockRowDesc& d, BrCfg* out, int cap) {
     }
   };
   for (int cps : {4, 8, 16}) add(BR_DIRECT, 0, cps);
-  if constexpr (!std::is_same<T, double>::value) {
+  if constexpr (std::is_same<T, double>::value) {
+    for (int sp : {2, 4, 8})
+      if (sp <= d.max_slots && sp * d.b_rows <= 512)
+        for (int cps : {8, 16}) add(BR_SPLIT, sp, cps);
+  } else {
     if (vec_ok<T>(d) && bc_compiled(d.bc)) {
       for (int sp : {1, 2, 4, 8})
         if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)

@@ -328,8 +328,7 @@ def test_every_tuning_candidate_matches_oracle(name):
     nterm = (2 * w.n_lfe - 1) * s.bsz
     tol = {0: None, 1: U32 + (nterm + 1) * U32, 2: U16 + (nterm + 1) * U32}
     names = {0: 'fp64', 1: 'fp32', 2: 'bf16'}
-    # ASM inverts n_lfe*b square element matrices in shared memory (n <= 169)
-    for pc in ('bj', 'asm') if w.n_lfe * w.M * w.PF <= 169 else ('bj',):
+    for pc in ('bj', 'asm'):
         o = driver.opts(pc=pc, poly_prec='bf16')
         p = _problem(w, o)
         p.assemble(o)
