@@ -54,12 +54,15 @@ def parse():
     ap.add_argument('--serving-budget-gb', type=float, default=160.0)
     ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
     ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
-    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40', 'beam'], default='poisson16',
+    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40', 'beam', 'tets'], default='poisson16',
                     help='poisson16: the step above; elasticity32 / cdr40: solver and kernel measurements '
                          'on the 32^3 perturbed Q2 elasticity (8 RHS) and 40^3 Q2 5-component CDR (4 RHS) '
                          'problems; beam: the cantilever beam runs of Sec. 6.2 (BJ, BJ-PP(10), ASM, '
                          'ASM-PP(10), GMRES(50) to 1e-6) over k at N_E = 320 and over N_E at k = 3; '
+                         'tets: the tetrahedral Poisson runs of Sec. 6.1 (BJ-PP(10/20), ASM-PP(10/20)) on a '
+                         'synthetic obstacle mesh of 6 n^3 Kuhn tetrahedra (--mesh-n, default 26: 104,160); '
                          'one JSON line')
+    ap.add_argument('--tet-ks', default='1,2,3,4', help='polynomial degrees of --workload tets')
     ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
                     help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
     ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
@@ -692,6 +695,74 @@ def run_beam(args, local):
             'data': 'synthetic', 'max_iters': maxit, 'cases': rows}
 
 
+def run_tets(args, local):
+    """Sec. 6.1 three-dimensional Poisson runs, synthetic stand-in: Laplace on
+    (-1,1)^3 minus a central cube (u = 0 there, outward flux n_x on the box),
+    Kuhn tetrahedra, P^k; BJ-PP(10), BJ-PP(20), ASM-PP(10), ASM-PP(20) with
+    GMRES(50)-CGS to 1e-6 in FP64, set-up and solve timed with CUDA events."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    n = args.mesh_n or 26
+    names9 = driver.BLOCK_NAMES[:9]
+
+    def ev_time(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    rows = []
+    for k in [int(v) for v in args.tet_ks.split(',')]:
+        t_gen = time.perf_counter()
+        w = W.tet_obstacle(n=n, k=k)
+        rb, cls, ruh = W.class_blocks(w)
+        t_gen = time.perf_counter() - t_gen
+        p = driver.Problem.from_workload(w, local)
+        t0 = time.perf_counter()
+        ch = 8192
+        for c0 in range(0, w.n_elem, ch):
+            c1 = min(w.n_elem, c0 + ch)
+            b = {x: np.ascontiguousarray(rb[x][cls[c0:c1]]) for x in names9}
+            b['ru'] = np.zeros((c1 - c0, w.M * w.PE, 1))
+            b['ruh'] = np.ascontiguousarray(ruh[c0:c1])
+            p.condense(b, c0)
+        torch.cuda.synchronize(dev)
+        t_cond = time.perf_counter() - t0
+        driver.check(L.hdg_set_dirichlet(p.h, w.uhat_dirichlet(), 0, st), 'dirichlet')
+        v0 = torch.from_numpy(w.random_vector(11)).to(dev)
+        row = {'N_E': w.n_elem, 'k': k, 'n_dof': p.n_dof, 'input_generation_s': round(t_gen, 1),
+               'condense_from_host_s': round(t_cond, 2), 'solves': {}}
+        for label, pc, deg in (('BJ-PP(10)', 'bj', 10), ('BJ-PP(20)', 'bj', 20), ('ASM-PP(10)', 'asm', 10),
+                               ('ASM-PP(20)', 'asm', 20)):
+            o = driver.opts(restart=50, rtol=1e-6, orth='cgs', pc=pc, poly='gmres', degree=deg,
+                            poly_prec='fp64', max_iters=max(args.max_iters, 3000))
+            ms_setup = ev_time(lambda: (driver.check(L.hdg_assemble(p.h, o, st), 'assemble'),
+                                        driver.check(L.hdg_setup_precond(p.h, o, v0, st), 'setup')))
+            info = L.hdg_solve_info()
+            stt = L.hdg_solve(p.h, o, st, info)
+            ms = ev_time(lambda: L.hdg_solve(p.h, o, st, info)) if stt == 0 else float('nan')
+            print('tets N_E=%d k=%d %s: %s, %d iterations, %.2f ms' % (w.n_elem, k, label, L.hdg_status_str(stt),
+                                                                     info.iters, ms), file=sys.stderr, flush=True)
+            row['solves'][label] = {'gmres': info.iters, 'setup_ms': round(ms_setup, 3), 'solve_ms': round(ms, 3),
+                                    'rel_resid': info.rel_resid, 'status': L.hdg_status_str(stt)}
+        rows.append(row)
+        p.close()
+        torch.cuda.empty_cache()
+    return {'workload': 'HDG Poisson (Laplace) on (-1,1)^3 minus a central cube of half-width 0.25, Kuhn '
+                        'tetrahedra, P^k; u = 0 on the obstacle, outward flux n_x on the box; GMRES(50) CGS to 1e-6',
+            'data': 'synthetic', 'cases': rows}
+
+
 def oracle_step(w, blk):
     """One step of the workload with the FP64 oracle (condense, assemble,
     block-Jacobi, GMRES(50) to 1e-8, recover).  Returns (ms, iterations)."""
@@ -799,6 +870,8 @@ def main():
         out = run_reference(args, ws, rank)
     elif args.workload == 'beam':
         out = run_beam(args, local)
+    elif args.workload == 'tets':
+        out = run_tets(args, local)
     elif args.workload != 'poisson16':
         out = run_config(args, local)
     else:

@@ -1,9 +1,10 @@
 """Lagrange bases and Gauss quadrature on the reference elements.
 
 Reference interval [-1, 1]; reference square/cube [-1, 1]^d; reference
-triangle with vertices (0,0), (1,0), (0,1).  Hexahedra use the tensor space
-Q^k with Gauss-Lobatto-Legendre (GLL) nodes, triangles the complete space P^k
-with equispaced nodes (Welter & Nguyen, Sec. 2.1 defines P^k on simplices;
+triangle with vertices (0,0), (1,0), (0,1); reference tetrahedron with
+vertices (0,0,0), (1,0,0), (0,1,0), (0,0,1).  Hexahedra use the tensor space
+Q^k with Gauss-Lobatto-Legendre (GLL) nodes, triangles and tetrahedra the
+complete space P^k with equispaced nodes (Welter & Nguyen, Sec. 2.1 defines P^k on simplices;
 the hexahedral workloads need tensor Q^k to reach 16 / 9 dofs per face).
 """
 import numpy as np
@@ -188,3 +189,77 @@ def tri_edge_points(l, t):
     a, b = TRI_EDGES[l]
     t = np.asarray(t)[:, None]
     return (1 - t) / 2 * TRI_VERTS[a] + (1 + t) / 2 * TRI_VERTS[b]
+
+
+# ------------------------------------------------------------- tetrahedra
+TET_VERTS = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+# Local face l is opposite vertex l; its corners (A, B, C) in this order
+# parametrise it as A + s (B - A) + t (C - A) over the reference triangle.
+TET_FACES = [(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)]
+
+
+def tet_nodes(k):
+    """Equispaced P^k nodes on the reference tetrahedron, x fastest."""
+    return np.array([[i / k, j / k, l / k] for l in range(k + 1) for j in range(k + 1 - l)
+                     for i in range(k + 1 - l - j)])
+
+
+def _tet_monomials(k):
+    return [(a, b, c) for c in range(k + 1) for b in range(k + 1 - c) for a in range(k + 1 - b - c)]
+
+
+def tet_basis(k, pts):
+    """phi (n, P_E) and reference gradients (n, P_E, 3) of nodal P^k on the
+    reference tetrahedron (monomials about the centroid, inverted Vandermonde)."""
+    mons = _tet_monomials(k)
+    c = np.full(3, 0.25)
+    X = tet_nodes(k) - c
+    V = np.array([[x[0] ** a * x[1] ** b * x[2] ** cc for (a, b, cc) in mons] for x in X])
+    Cinv = np.linalg.inv(V)
+    P = np.asarray(pts, float) - c
+    px, py, pz = P[:, 0], P[:, 1], P[:, 2]
+
+    def pw(v, e):
+        return v ** e if e > 0 else np.ones_like(v)
+
+    def dpw(v, e):
+        return e * v ** (e - 1) if e > 0 else np.zeros_like(v)
+    Vt = np.stack([pw(px, a) * pw(py, b) * pw(pz, cc) for (a, b, cc) in mons], axis=1)
+    dx = np.stack([dpw(px, a) * pw(py, b) * pw(pz, cc) for (a, b, cc) in mons], axis=1)
+    dy = np.stack([pw(px, a) * dpw(py, b) * pw(pz, cc) for (a, b, cc) in mons], axis=1)
+    dz = np.stack([pw(px, a) * pw(py, b) * dpw(pz, cc) for (a, b, cc) in mons], axis=1)
+    return Vt @ Cinv, np.stack([dx @ Cinv, dy @ Cinv, dz @ Cinv], axis=-1)
+
+
+def tet_rule(n):
+    """Collapsed (Duffy) Gauss rule with n^3 points on the reference
+    tetrahedron: x = u, y = v (1 - u), z = w (1 - u)(1 - v), weight
+    (1 - u)^2 (1 - v)."""
+    x, w = gauss_legendre(n)
+    u = (x + 1) / 2
+    wu = w / 2
+    pts, wts = [], []
+    for i in range(n):
+        for j in range(n):
+            for l in range(n):
+                a, b, c = u[i], u[j], u[l]
+                pts.append([a, b * (1 - a), c * (1 - a) * (1 - b)])
+                wts.append(wu[i] * wu[j] * wu[l] * (1 - a) ** 2 * (1 - b))
+    return np.array(pts), np.array(wts)
+
+
+def tet_face_points(l, st):
+    """Map reference-triangle points st (n, 2) onto local face l."""
+    A, Bv, C = (TET_VERTS[v] for v in TET_FACES[l])
+    st = np.asarray(st, float)
+    return A[None, :] + st[:, :1] * (Bv - A)[None, :] + st[:, 1:2] * (C - A)[None, :]
+
+
+def tet_face_normal(l):
+    """Outward normal of local face l scaled by its area element in (s, t):
+    (B - A) x (C - A), oriented away from the opposite vertex."""
+    A, Bv, C = (TET_VERTS[v] for v in TET_FACES[l])
+    n = np.cross(Bv - A, C - A)
+    if np.dot(n, TET_VERTS[l] - A) > 0:
+        n = -n
+    return n

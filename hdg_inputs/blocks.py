@@ -135,9 +135,29 @@ def ref_tri(k, nquad):
                       t[:, None], wt, fpts, fphi, None, fn, psi, node_t[:, None], fnode)
 
 
+def ref_tet(k, nquad):
+    pts, wts = B.tet_rule(nquad)
+    phi, dphi = B.tet_basis(k, pts)
+    st, ws = B.tri_rule(nquad)
+    node_st = B.tri_nodes(k)
+    fpts, fphi, fn, fnode = [], [], [], []
+    for l in range(4):
+        P = B.tet_face_points(l, st)
+        fpts.append(P)
+        fphi.append(B.tet_basis(k, P)[0])
+        fn.append(B.tet_face_normal(l))
+        fnode.append(B.tet_face_points(l, node_st))
+    psi, _ = B.tri_basis(k, st)
+    PE = (k + 1) * (k + 2) * (k + 3) // 6
+    return RefElement('tet', k, 3, 4, PE, (k + 1) * (k + 2) // 2, pts, wts, phi, dphi, st, ws,
+                      fpts, fphi, None, fn, psi, node_st, fnode)
+
+
 def reference_element(mesh, k, nquad=None):
     if mesh.kind == 'hex':
         return ref_hex(k, nquad or (k + 2))
+    if mesh.kind == 'tet':
+        return ref_tet(k, nquad or (k + 2))
     return ref_tri(k, nquad or (k + 3))
 
 
@@ -148,6 +168,12 @@ def geometry(mesh, elems, ref_pts):
     if mesh.kind == 'hex':
         X8 = mesh.verts[mesh.elems[elems]]
         x, Jac = B.trilinear(X8, ref_pts)
+    elif mesh.kind == 'tet':
+        X4 = mesh.verts[mesh.elems[elems]]                     # (E, 4, 3)
+        v0 = X4[:, 0, :]
+        Jm = np.stack([X4[:, 1, :] - v0, X4[:, 2, :] - v0, X4[:, 3, :] - v0], axis=2)
+        x = v0[:, None, :] + np.einsum('eab,nb->ena', Jm, ref_pts)
+        Jac = np.broadcast_to(Jm[:, None], (len(elems), ref_pts.shape[0], 3, 3)).copy()
     else:
         X3 = mesh.verts[mesh.elems[elems]]                     # (E, 3, 2)
         v0 = X3[:, 0, :]

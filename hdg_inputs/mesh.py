@@ -10,7 +10,7 @@ face-based assembly and for the ASM update (Welter & Nguyen, Sec. 4.2, 4.6).
 from dataclasses import dataclass
 import numpy as np
 
-from .basis import hex_face_vertices, TRI_EDGES
+from .basis import hex_face_vertices, TRI_EDGES, TET_FACES
 
 
 @dataclass
@@ -113,3 +113,43 @@ def box_hex_mesh(counts, lengths, perturb=0.0, seed=None):
     elems = np.array(elems, np.int64)
     ef, fe, fb = _build_faces([hex_face_vertices(l) for l in range(6)], elems)
     return Mesh(3, 'hex', verts, elems, ef, fe, fb)
+
+
+def tet_mesh(n, lo=0.0, hi=1.0, hole=0.0):
+    """Kuhn subdivision of the n^3 cubes of (lo, hi)^3 into six tetrahedra each
+    (the paths from the cube's lowest to its highest corner through the
+    orderings of the three axes; every cube is split the same way, so the mesh
+    is conforming).  Cubes whose centres lie within `hole` of the box centre
+    in every coordinate are left out (an obstacle with reentrant edges and
+    corners).  Every tetrahedron is positively oriented."""
+    xs = np.linspace(lo, hi, n + 1)
+    verts = np.array([[xs[i], xs[j], xs[l]] for l in range(n + 1) for j in range(n + 1) for i in range(n + 1)])
+    vid = lambda i, j, l: (l * (n + 1) + j) * (n + 1) + i
+    mid = 0.5 * (lo + hi)
+    h = (hi - lo) / n
+    orders = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    elems = []
+    for l in range(n):
+        for j in range(n):
+            for i in range(n):
+                c = np.array([lo + (i + 0.5) * h, lo + (j + 0.5) * h, lo + (l + 0.5) * h])
+                if hole > 0.0 and np.all(np.abs(c - mid) < hole):
+                    continue
+                for od in orders:
+                    p = [i, j, l]
+                    tet = [vid(*p)]
+                    for ax in od:
+                        p[ax] += 1
+                        tet.append(vid(*p))
+                    X = verts[tet]
+                    if np.linalg.det(np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]], axis=1)) < 0:
+                        tet[2], tet[3] = tet[3], tet[2]
+                    elems.append(tet)
+    elems = np.array(elems, np.int64)
+    used = np.unique(elems)
+    remap = -np.ones(verts.shape[0], np.int64)
+    remap[used] = np.arange(len(used))
+    verts = verts[used]
+    elems = remap[elems]
+    ef, fe, fb = _build_faces([list(f) for f in TET_FACES], elems)
+    return Mesh(3, 'tet', verts, elems, ef, fe, fb)

@@ -14,12 +14,17 @@
                                                              (n=40, k=2, R=4)
   hex_convdiff    : one serving request: n^3 hexahedra, Q^k, kappa, unit beta,
                     f = 1, tau = 1 + kappa
+  tet_poisson     : unit cube, Kuhn tetrahedra (6 n^3), P^k, tau = 1,
+                    u = prod sin(pi x_i)
+  tet_obstacle    : Laplace on (-1,1)^3 minus a central cube, Kuhn tetrahedra,
+                    P^k; u = 0 on the obstacle, outward flux n_x on the box
   hex_beam        : cantilever beam (0,5) x (0,1) x (0,1) with 5n x n x n
                     hexahedra (Sec. 6.2: n = 2, 4, 6, 8 gives N_E = 40, 320,
                     1080, 2560), Q^k, lambda = mu = 1, tau = 1; clamped
                     (u = 0) at x = 0, uniform traction t = (0, 0, -1) at
                     x = 5, the other faces traction-free; no body force
-Except for hex_beam, all faces on the domain boundary are Dirichlet faces.
+Except for hex_beam and tet_obstacle, all faces on the domain boundary are
+Dirichlet faces.
 """
 from dataclasses import dataclass
 import numpy as np
@@ -86,10 +91,13 @@ class Workload:
     def n_dof(self):
         return self.n_free * self.M * self.PF
 
-    def blocks(self, e0=0, e1=None):
-        """Element blocks for elements [e0, e1) (row-major, float64)."""
-        e1 = self.n_elem if e1 is None else e1
-        elems = np.arange(e0, e1)
+    def blocks(self, e0=0, e1=None, elems=None):
+        """Element blocks for elements [e0, e1), or for the index array
+        `elems` (row-major, float64)."""
+        if elems is None:
+            e1 = self.n_elem if e1 is None else e1
+            elems = np.arange(e0, e1)
+        elems = np.asarray(elems)
         mats = blk.element_matrices(self.mesh, self.ref, self.perm, elems)
         out = blk.hdg_blocks(mats, self.phys)
         E = len(elems)
@@ -102,7 +110,7 @@ class Workload:
             cols = []
             for s in self.rhs_seeds:
                 rng = np.random.default_rng(s)
-                fn = rng.standard_normal((self.n_elem, self.M, self.PE))[e0:e1]
+                fn = rng.standard_normal((self.n_elem, self.M, self.PE))[elems]
                 cols.append(blk.load_vector_from_nodal(mats, fn))
             ru = np.stack(cols, axis=2)
         out['ru'] = np.ascontiguousarray(ru)
@@ -196,13 +204,42 @@ def hex_convdiff(n, k, kappa, beta, R=1):
 
 def boundary_faces_at(mesh, axis, value, tol=1e-12):
     """(NF,) uint8: boundary faces whose vertices all have x_axis = value."""
-    from .basis import hex_face_vertices
+    from .basis import hex_face_vertices, TET_FACES
     out = np.zeros(mesh.n_face, np.uint8)
     for f in np.nonzero(mesh.face_boundary)[0]:
         e, l = mesh.face_elem[f, 0], mesh.face_elem[f, 1]
-        xs = mesh.verts[mesh.elems[e, hex_face_vertices(l)], axis]
+        lv = hex_face_vertices(l) if mesh.kind == 'hex' else list(TET_FACES[l])
+        xs = mesh.verts[mesh.elems[e, lv], axis]
         out[f] = np.all(np.abs(xs - value) < tol)
     return out
+
+
+def tet_poisson(n=8, k=2, R=1):
+    """Unit cube, Kuhn tetrahedra (6 n^3), P^k, tau = 1, u = prod sin(pi x_i),
+    every boundary face Dirichlet."""
+    m = meshmod.tet_mesh(n)
+    ref = blk.reference_element(m, k)
+    u, f, q = _sin_product(3)
+    return Workload('tet_poisson', m, ref, blk.face_permutations(m, ref), blk.poisson(3), R,
+                    'function', f, u, q, k=k)
+
+
+def tet_obstacle(n=16, k=2, hole=0.25):
+    """Sec. 6.1's three-dimensional Poisson problem, synthetic stand-in: the
+    Laplace equation on the box (-1,1)^3 minus a central cube of half-width
+    `hole` (in place of the cone of the paper's Gmsh mesh), Kuhn tetrahedra,
+    P^k, tau = 1; u = 0 on the obstacle and grad u . n + (1,0,0) . n = 0 on
+    the box, i.e. outward flux g = -grad u . n = n_x."""
+    m = meshmod.tet_mesh(n, -1.0, 1.0, hole)
+    ref = blk.reference_element(m, k)
+    outer = np.zeros(m.n_face, np.uint8)
+    for ax in range(3):
+        for v in (-1.0, 1.0):
+            outer |= boundary_faces_at(m, ax, v)
+    dirichlet = (m.face_boundary.astype(bool) & ~outer.astype(bool)).astype(np.uint8)
+    g = lambda x, nrm: nrm[..., :1].copy()
+    return Workload('tet_obstacle', m, ref, blk.face_permutations(m, ref), blk.poisson(3), 1, 'none', k=k,
+                    dirichlet=dirichlet, neumann_flux=g)
 
 
 def hex_beam(n=4, k=2, lam=1.0, mu=1.0, traction=(0.0, 0.0, -1.0), length=5.0, tau=1.0):
@@ -305,3 +342,35 @@ def shared_blocks(w):
     names = ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J', 'ru', 'ruh')
     strides = [0] * 9 + [out['ru'][0].size, out['ruh'][0].size]
     return {k: out[k] for k in names}, strides
+
+
+def element_classes(w):
+    """Classes of elements with identical blocks: the same vertex positions
+    relative to the first vertex and the same face-node permutations (a
+    structured mesh has few: six Kuhn tetrahedra times the permutation
+    patterns).  Returns (representatives, class_of_element)."""
+    X = w.mesh.verts[w.mesh.elems]
+    scale = np.abs(X).max() + 1.0
+    rel = np.round((X - X[:, :1]) / scale * 1e9).astype(np.int64).reshape(w.n_elem, -1)
+    key = np.concatenate([rel, w.perm.reshape(w.n_elem, -1).astype(np.int64)], axis=1)
+    _, rep, cls = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    return rep, cls.ravel()
+
+
+def class_blocks(w):
+    """Blocks of a workload with constant coefficients and no body force or
+    nodal loads ('none'): one block set per element class, plus the per-element
+    face loads of its traction faces.  Returns (rep_blocks, class_of_element,
+    ruh (NE, nlb, R)); the blocks of elements [a, b) are
+    {k: rep_blocks[k][cls[a:b]]}."""
+    assert w.rhs_kind == 'none'
+    rep, cls = element_classes(w)
+    b = w.blocks(elems=rep)
+    b.pop('_mats')
+    ruh = np.zeros((w.n_elem, w.n_lfe * w.M * w.PF, w.R))
+    if w.neumann_flux is not None and w.face_neumann.any():
+        sel = np.nonzero(w.face_neumann[w.mesh.elem_face].any(axis=1))[0]
+        ruh[sel] = blk.neumann_face_load(w.mesh, w.ref, w.perm, sel, w.face_neumann, w.neumann_flux,
+                                         w.M)[:, :, None]
+    names = ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J')
+    return {k: b[k] for k in names}, cls, ruh

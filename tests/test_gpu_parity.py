@@ -24,7 +24,10 @@ SMALL = {
     'hex_q4': lambda: W.hex_poisson(n=2, k=4),          # K = 375 > 192: tensor-core products in K slices
     'beam_k2': lambda: W.hex_beam(n=2, k=2),            # traction faces: boundary rows with one element
     'elast_q3_R2': lambda: W.hex_elasticity(n=2, k=3, R=2),   # Ebar 192 x 192, ASM patches 288 x 288:
-}                                                        # block inverses beyond one CTA's shared memory
+                                                         # block inverses beyond one CTA's shared memory
+    'tet_k2': lambda: W.tet_poisson(n=2, k=2),          # tetrahedra: N_lfe = 4, 7 slots, permuted face nodes
+    'tet_obst_k3': lambda: W.tet_obstacle(n=4, k=3, hole=0.5),   # obstacle: Dirichlet inside, flux outside
+}
 
 
 def _problem(w, o=None, chunks=1):
@@ -104,7 +107,8 @@ def test_matvec_fp64_fp32_bf16(name):
     p.close()
 
 
-@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'elast_pert_k2_R8', 'beam_k2', 'elast_q3_R2'])
+@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'elast_pert_k2_R8', 'beam_k2', 'elast_q3_R2',
+                                  'tet_k2', 'tet_obst_k3'])
 @pytest.mark.parametrize('pc', ['bj', 'asm'])
 def test_bj_asm_apply(name, pc):
     """Block-Jacobi (Sec. 4.5) and ASM (Sec. 4.6) applies in FP64 against the
@@ -311,7 +315,7 @@ def test_condense_strided_shared_blocks(shared):
     assert rel(K1, K2) < 1e-13 and rel(r1, r2) < 1e-13
 
 
-@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'cdr_k2_R4', 'beam_k2'])
+@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'cdr_k2_R4', 'beam_k2', 'tet_obst_k3'])
 def test_every_tuning_candidate_matches_oracle(name):
     """Every launch configuration the autotuner may pick computes the same
     block-row products: K x at each storage precision (bounds as in the
@@ -407,4 +411,39 @@ def test_beam_preconditioners_match_oracle(pc, poly):
     assert oi['converged']
     tol = max(2, 0.05 * oi['iters']) if oi['iters'] < 500 else 0.25 * oi['iters']
     assert abs(info.iters - oi['iters']) <= tol, (info.iters, oi['iters'])
+    p.close()
+
+
+@pytest.mark.parametrize('pc,deg', [('bj', 10), ('bj', 20), ('asm', 10), ('asm', 20)])
+def test_tet_obstacle_polynomial_preconditioners_match_oracle(pc, deg):
+    """Sec. 6.1's tetrahedral Poisson set-up (synthetic obstacle stand-in,
+    3024 P^1 tetrahedra): BJ-PP(10/20) and ASM-PP(10/20), GMRES(50)-CGS to
+    1e-6: true residual <= 1e-6, iteration count within 5% (at least 2) of the
+    oracle's with the same polynomial start vector."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.tet_obstacle(n=8, k=1, hole=0.25)
+    s = OracleSystem(w)
+    o = driver.opts(restart=50, rtol=1e-6, pc=pc, poly='gmres', degree=deg, max_iters=3000)
+    p = _problem(w)
+    p.assemble(o)
+    v0 = w.random_vector(11)
+    p.setup_precond(o, v0)
+    st, info = p.solve(o)
+    assert st == 0 and info.converged == 1
+    x = p.free_trace()[:, 0]
+    b = s.r[:, 0]
+    assert np.linalg.norm(b - s.K @ x) / np.linalg.norm(b) <= 1e-6
+    if pc == 'bj':
+        Binv = precond.bj_setup(s.K, s.bsz)
+        M = lambda v: precond.bj_apply(Binv, v)
+    else:
+        subs = precond.asm_setup(s.K, s.elem_dofs)
+        M = lambda v: precond.asm_apply(subs, v)
+    A = lambda v: M(s.K @ v)
+    th = precond.pp_setup(A, v0, deg)
+    _, oi = krylov.gmres(lambda v: s.K @ v, lambda v: precond.pp_apply(A, th, M(v)), b, m=50, rtol=1e-6,
+                         maxit=3000)
+    assert oi['converged']
+    assert abs(info.iters - oi['iters']) <= max(2, 0.05 * oi['iters']), (info.iters, oi['iters'])
     p.close()

@@ -226,3 +226,50 @@ def test_beam_tip_deflection_timoshenko():
     delta = 125.0 / (3 * 2.5 / 12.0) + 5.0 / (5.0 / 6.0)
     assert compliance < 0.0                                  # deflects along the traction
     assert abs(-compliance - delta) < 0.02 * delta
+
+
+# ------------------------------------------------------------ tetrahedra
+@pytest.mark.parametrize('k,ns,lo', [(1, (4, 8), 1.85), (2, (2, 4), 2.7)])
+def test_tet_mms_rates(k, ns, lo):
+    """P^k on Kuhn tetrahedra: L2 errors of u and q decrease at about k+1."""
+    errs = [_solve_errors(W.tet_poisson(n=n, k=k))[3] for n in ns]
+    (eu0, eq0), (eu1, eq1) = errs
+    assert np.log2(eu0 / eu1) > lo and np.log2(eq0 / eq1) > lo
+
+
+def test_tet_patch_and_flux_exact():
+    """A quadratic u on P^2 tetrahedra is reproduced exactly, with Dirichlet
+    data on x = 0 and its outward flux g = -grad u . n on the five other
+    sides (the faces' nodes are matched across elements by position, so the
+    permuted face bases are exercised)."""
+    from hdg_inputs import mesh as meshmod
+
+    def u(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return (0.5 + 0.3 * X - 0.2 * Y + 0.4 * Z + X * X - 0.5 * X * Y + 0.7 * Y * Z - 0.3 * Z * Z)[..., None]
+
+    def qf(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return np.stack([0.3 + 2 * X - 0.5 * Y, -0.2 - 0.5 * X + 0.7 * Z, 0.4 + 0.7 * Y - 0.6 * Z], -1)[..., None, :]
+    f = lambda x: np.full(x.shape[:-1] + (1,), -(2.0 - 0.6))          # -lap u
+    m = meshmod.tet_mesh(3)
+    ref = blk.reference_element(m, 2)
+    g = lambda x, n: -np.einsum('...d,...d->...', qf(x)[..., 0, :], n)[..., None]
+    w = W.Workload('tet_patch', m, ref, blk.face_permutations(m, ref), blk.poisson(3), 1, 'function', f,
+                   u, qf, k=2, dirichlet=W.boundary_faces_at(m, 0, 0.0), neumann_flux=g)
+    assert (w.perm != np.arange(w.PF)).any()
+    _, _, _, (eu, eq) = _solve_errors(w)
+    assert eu < 1e-11 and eq < 1e-10
+
+
+def test_class_blocks_equal_per_element_blocks():
+    """The blocks gathered from one representative per element class (same
+    shape up to translation, same face-node permutations) equal the blocks
+    generated element by element; the traction loads stay per element."""
+    w = W.tet_obstacle(n=6, k=2, hole=0.34)
+    rb, cls, ruh = W.class_blocks(w)
+    assert len(np.unique(cls)) < w.n_elem // 50
+    full = w.blocks()
+    for k in ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J'):
+        assert np.abs(rb[k][cls] - full[k]).max() <= 1e-14 * np.abs(full[k]).max(), k
+    assert np.array_equal(ruh, full['ruh']) and not full['ru'].any()
