@@ -54,7 +54,8 @@ def parse():
     ap.add_argument('--serving-budget-gb', type=float, default=160.0)
     ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
     ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
-    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40', 'beam', 'tets'], default='poisson16',
+    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40', 'beam', 'tets', 'burgers'],
+                    default='poisson16',
                     help='poisson16: the step above; elasticity32 / cdr40: solver and kernel measurements '
                          'on the 32^3 perturbed Q2 elasticity (8 RHS) and 40^3 Q2 5-component CDR (4 RHS) '
                          'problems; beam: the cantilever beam runs of Sec. 6.2 (BJ, BJ-PP(10), ASM, '
@@ -63,6 +64,10 @@ def parse():
                          'synthetic obstacle mesh of 6 n^3 Kuhn tetrahedra (--mesh-n, default 26: 104,160); '
                          'one JSON line')
     ap.add_argument('--tet-ks', default='1,2,3,4', help='polynomial degrees of --workload tets')
+    ap.add_argument('--burgers-cases', default='1:16,1:32,1:64,1:128,2:16,2:32,2:64,2:128,3:16,3:32,3:64,3:128,'
+                                               '4:16,4:32,4:64,4:128',
+                    help='k:1/h pairs of --workload burgers (Sec. 6.1 Table 1: steady viscous Burgers, damped '
+                         'Newton with BJ, BJ-PP(10), ASM, ASM-PP(10) GMRES(50) to 1e-6)')
     ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
                     help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
     ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
@@ -763,6 +768,46 @@ def run_tets(args, local):
             'data': 'synthetic', 'cases': rows}
 
 
+def run_burgers(args, local):
+    """Sec. 6.1 steady viscous Burgers problem (nu = 1/200, u = 1 - 2x on three
+    sides, outflow at y = 1) on (1/h)^2 Q^k quadrilaterals: damped Newton to a
+    residual of 1e-8 from u = 1 - 2x, each step's linear solve GMRES(50)-CGS
+    to 1e-6 with BJ, BJ-PP(10), ASM or ASM-PP(10) on the GPU; the total
+    GMRES iterations over the Newton steps, and the time spent in the
+    library's calls and in the host's residual and Jacobian evaluations."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import burgers as BG
+    from paper_2512_13619_gb300 import driver
+    from paper_2512_13619_gb300.newton import newton_solve
+    torch.cuda.set_device(local)
+    rows = []
+    for case in args.burgers_cases.split(','):
+        k, n = (int(v) for v in case.split(':'))
+        P = BG.Burgers(n=n, k=k)
+        v0 = np.random.default_rng(11).standard_normal(P.n_free * P.PF)
+        row = {'k': k, '1/h': n, 'n_dof': P.n_free * P.PF, 'solves': {}}
+        for label, pc, deg in (('BJ', 'bj', 0), ('BJ-PP(10)', 'bj', 10), ('ASM', 'asm', 0), ('ASM-PP(10)', 'asm', 10)):
+            o = driver.opts(restart=50, rtol=1e-6, orth='cgs', pc=pc, poly='gmres' if deg else None, degree=deg,
+                            poly_prec='fp64', max_iters=max(args.max_iters, 20000))
+            try:
+                _, info = newton_solve(P, o, v0 if deg else None, tol=1e-8, device=local)
+                h = info['history']
+                rec = {'newton_steps': len(h) - 1, 'gmres': info['gmres'], 'final_residual': h[-1][0],
+                       'linear_s': round(info['linear_s'], 3), 'host_s': round(info['host_s'], 3),
+                       'status': 'ok' if h[-1][0] <= 1e-8 else 'newton not converged'}
+            except RuntimeError as e:
+                rec = {'status': str(e)}
+            print('burgers k=%d 1/h=%d %s: %s' % (k, n, label, rec), file=sys.stderr, flush=True)
+            row['solves'][label] = rec
+        rows.append(row)
+    return {'workload': 'HDG steady viscous Burgers u_y + (u^2/2)_x - (1/200) lap u = 0 on (0,1)^2, Q^k '
+                        'quadrilaterals, tau = 2; damped Newton to 1e-8, GMRES(50) CGS to 1e-6 per step',
+            'data': 'synthetic', 'cases': rows}
+
+
 def oracle_step(w, blk):
     """One step of the workload with the FP64 oracle (condense, assemble,
     block-Jacobi, GMRES(50) to 1e-8, recover).  Returns (ms, iterations)."""
@@ -872,6 +917,8 @@ def main():
         out = run_beam(args, local)
     elif args.workload == 'tets':
         out = run_tets(args, local)
+    elif args.workload == 'burgers':
+        out = run_burgers(args, local)
     elif args.workload != 'poisson16':
         out = run_config(args, local)
     else:

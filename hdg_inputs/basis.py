@@ -263,3 +263,50 @@ def tet_face_normal(l):
     if np.dot(n, TET_VERTS[l] - A) > 0:
         n = -n
     return n
+
+
+# --------------------------------------------------------- quadrilaterals
+# Reference square [-1,1]^2; vertex v at (bit 0 -> x, bit 1 -> y); local
+# face (edge) l = 2 axis + side fixes coordinate `axis` at -1 / +1, its
+# parameter t runs along the other coordinate.
+QUAD_VERTS = np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]], float)
+
+
+def quad_face_vertices(l):
+    ax, side = l // 2, l % 2
+    val = 1.0 if side else -1.0
+    return [v for v in range(4) if QUAD_VERTS[v, ax] == val]
+
+
+def quad_face_points(l, t):
+    ax, side = l // 2, l % 2
+    t = np.asarray(t, float).ravel()
+    P = np.zeros((t.shape[0], 2))
+    P[:, ax] = 1.0 if side else -1.0
+    P[:, 1 - ax] = t
+    return P
+
+
+def quad_vol_basis(k, pts):
+    """Q^k on the reference square at pts (n, 2): phi (n, P_E) and reference
+    gradients (n, P_E, 2); node (i, j) at index i + (k+1) j."""
+    g = gll_nodes(k)
+    px, dpx = lagrange_1d(g, pts[:, 0])
+    py, dpy = lagrange_1d(g, pts[:, 1])
+    n = pts.shape[0]
+    phi = np.einsum('qi,qj->qji', px, py).reshape(n, -1)
+    gx = np.einsum('qi,qj->qji', dpx, py).reshape(n, -1)
+    gy = np.einsum('qi,qj->qji', px, dpy).reshape(n, -1)
+    return phi, np.stack([gx, gy], axis=-1)
+
+
+def bilinear(X4, ref):
+    """Physical points and Jacobians of the bilinear map of a batch of
+    quadrilaterals: X4 (E, 4, 2), ref (n, 2) -> x (E, n, 2), Jac (E, n, 2, 2)."""
+    s = QUAD_VERTS
+    N = np.prod(1.0 + ref[:, None, :] * s[None, :, :], axis=2) / 4.0
+    dN = np.zeros((ref.shape[0], 4, 2))
+    for b in range(2):
+        o = 1 - b
+        dN[:, :, b] = s[None, :, b] * (1.0 + ref[:, None, o] * s[None, :, o]) / 4.0
+    return np.einsum('nv,evd->end', N, X4), np.einsum('nvb,eva->enab', dN, X4)

@@ -153,7 +153,29 @@ def ref_tet(k, nquad):
                       fpts, fphi, None, fn, psi, node_st, fnode)
 
 
+def ref_quad(k, nquad):
+    x, w = B.gauss_legendre(nquad)
+    pts = np.array([[x[i], x[j]] for j in range(nquad) for i in range(nquad)])
+    wts = np.array([w[i] * w[j] for j in range(nquad) for i in range(nquad)])
+    phi, dphi = B.quad_vol_basis(k, pts)
+    node_t = B.gll_nodes(k)
+    fpts, fphi, fn, fnode = [], [], [], []
+    for l in range(4):
+        P = B.quad_face_points(l, x)
+        fpts.append(P)
+        fphi.append(B.quad_vol_basis(k, P)[0])
+        e = np.zeros(2)
+        e[l // 2] = 1.0 if l % 2 else -1.0
+        fn.append(e)
+        fnode.append(B.quad_face_points(l, node_t))
+    psi, _ = B.lagrange_1d(node_t, x)
+    return RefElement('quad', k, 2, 4, (k + 1) ** 2, k + 1, pts, wts, phi, dphi, x[:, None], w,
+                      fpts, fphi, None, fn, psi, node_t[:, None], fnode)
+
+
 def reference_element(mesh, k, nquad=None):
+    if mesh.kind == 'quad':
+        return ref_quad(k, nquad or (k + 2))
     if mesh.kind == 'hex':
         return ref_hex(k, nquad or (k + 2))
     if mesh.kind == 'tet':
@@ -168,6 +190,8 @@ def geometry(mesh, elems, ref_pts):
     if mesh.kind == 'hex':
         X8 = mesh.verts[mesh.elems[elems]]
         x, Jac = B.trilinear(X8, ref_pts)
+    elif mesh.kind == 'quad':
+        x, Jac = B.bilinear(mesh.verts[mesh.elems[elems]], ref_pts)
     elif mesh.kind == 'tet':
         X4 = mesh.verts[mesh.elems[elems]]                     # (E, 4, 3)
         v0 = X4[:, 0, :]

@@ -10,7 +10,7 @@ face-based assembly and for the ASM update (Welter & Nguyen, Sec. 4.2, 4.6).
 from dataclasses import dataclass
 import numpy as np
 
-from .basis import hex_face_vertices, TRI_EDGES, TET_FACES
+from .basis import hex_face_vertices, quad_face_vertices, TRI_EDGES, TET_FACES
 
 
 @dataclass
@@ -153,3 +153,15 @@ def tet_mesh(n, lo=0.0, hi=1.0, hole=0.0):
     elems = remap[elems]
     ef, fe, fb = _build_faces([list(f) for f in TET_FACES], elems)
     return Mesh(3, 'tet', verts, elems, ef, fe, fb)
+
+
+def quad_mesh(n):
+    """Unit square with n x n quadrilaterals; vertex v of an element at
+    (x_i + (v & 1) h, y_j + (v >> 1) h), elements x fastest."""
+    xs = np.linspace(0.0, 1.0, n + 1)
+    verts = np.array([[xs[i], xs[j]] for j in range(n + 1) for i in range(n + 1)])
+    vid = lambda i, j: j * (n + 1) + i
+    elems = np.array([[vid(i, j), vid(i + 1, j), vid(i, j + 1), vid(i + 1, j + 1)]
+                      for j in range(n) for i in range(n)], np.int64)
+    ef, fe, fb = _build_faces([quad_face_vertices(l) for l in range(4)], elems)
+    return Mesh(2, 'quad', verts, elems, ef, fe, fb)

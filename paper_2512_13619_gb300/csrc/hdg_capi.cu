@@ -136,6 +136,7 @@ struct hdg_problem_s {
          *bnorm = nullptr, *rel = nullptr;
   int *running = nullptr, *jend = nullptr, *on_estimate = nullptr, *done = nullptr, *iters = nullptr;
   unsigned* counter = nullptr;
+  int* dmaxit = nullptr;           // iteration cap read by the Givens step (cycle graphs replay it)
   unsigned* d_err = nullptr;
   float* x32 = nullptr;
   double *t1 = nullptr, *res = nullptr, *pq = nullptr, *pw = nullptr, *ptmp = nullptr, *pAq = nullptr,
@@ -151,6 +152,7 @@ struct hdg_problem_s {
   // captured GMRES cycles (CUDA graphs with one IF node per iteration)
   struct CycleGraph {
     unsigned long long key = 0;
+    unsigned poly_gen = 0;         // polynomial coefficients captured by value
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaGraphConditionalHandle> h;
@@ -158,6 +160,7 @@ struct hdg_problem_s {
   };
   std::vector<CycleGraph> graphs;
   bool use_graphs = true;
+  unsigned poly_gen = 0;           // bumped by every polynomial set-up
   cudaStream_t cap_stream = nullptr;
 
   // timing of block-matvec launches
@@ -819,6 +822,7 @@ void ensure_workspace(hdg_problem p, int m) {
     p->done = (int*)A(sizeof(int) * kMaxR);
     p->iters = (int*)A(sizeof(int) * kMaxR);
     p->counter = (unsigned*)A(sizeof(unsigned) * 4);
+    p->dmaxit = (int*)A(sizeof(int));
     CK(cudaMemset(p->counter, 0, sizeof(unsigned) * 4));
     CK(cudaMemset(p->d_x, 0, sizeof(double) * len));
   } else {
@@ -878,6 +882,7 @@ GmresView make_view(hdg_problem p, int R, int m, double rtol, int maxit) {
   k.done = p->done;
   k.iters = p->iters;
   k.maxit = maxit;
+  k.dmaxit = p->dmaxit;
   k.hflag = p->d_flag;
   k.counter = p->counter;
   k.err = p->d_err;
@@ -949,14 +954,23 @@ unsigned long long graph_key(const hdg_solver_opts& o, int kprec, int mprec, int
 cudaGraphExec_t cycle_graph(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec, int kpoly,
                             const GmresView& kin, long long* kernels_per_iter) {
   const unsigned long long key = graph_key(o, kprec, mprec, kpoly, p->br_variant + 2 * (p->tune_gen & 2047));
-  for (auto& cg : p->graphs)
-    if (cg.key == key) {
-      *kernels_per_iter = cg.kernels_per_iter;
-      return cg.exec;
+  const unsigned pgen = (o.poly != HDG_POLY_NONE) ? p->poly_gen : 0u;
+  for (auto it = p->graphs.begin(); it != p->graphs.end(); ++it) {
+    if (it->key != key) continue;
+    if (it->poly_gen == pgen) {
+      *kernels_per_iter = it->kernels_per_iter;
+      return it->exec;
     }
+    // same shape, stale by-value arguments: re-capture
+    if (it->exec) cudaGraphExecDestroy(it->exec);
+    if (it->g) cudaGraphDestroy(it->g);
+    p->graphs.erase(it);
+    break;
+  }
   if (!p->cap_stream) CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   hdg_problem_s::CycleGraph cg;
   cg.key = key;
+  cg.poly_gen = pgen;
   CK(cudaGraphCreate(&cg.g, 0));
   // one handle per IF node: node 0 starts at 1, the others at 0 on every
   // launch; iteration j's Givens step sets node j+1's handle, so a skipped
@@ -1039,6 +1053,7 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
   CK(cudaMemsetAsync(x, 0, sizeof(double) * len, s));
   CK(cudaMemsetAsync(p->iters, 0, sizeof(int) * R, s));
   CK(cudaMemsetAsync(p->done, 0, sizeof(int) * R, s));
+  if (p->dmaxit) set_ints(p, p->dmaxit, maxit, 1, s);
   set_ints(p, p->running, 1, R, s);
   set_dbls(p, p->cfac, 1.0, R, s);
   // ||b|| and ||P^{-1} b||
@@ -1772,6 +1787,7 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
     }
     p->pc_ready = o->pc;
     p->poly_n = 0;
+    if (o->poly != HDG_POLY_NONE) p->poly_gen++;    // cycle graphs hold the coefficients by value
     p->poly_kind = o->poly;
     if (o->poly != HDG_POLY_NONE) {
       // one Arnoldi(P) cycle with MGS on A = M^{-1} K (FP64) from v0   (Sec. 4.7)
@@ -1781,6 +1797,7 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* o, const doub
       Ops ops{p, s, 1};
       GmresView k = make_view(p, 1, Pa, 0.0, 1 << 30);
       k.chunk = gmres_chunk(p->ndof);
+      if (p->dmaxit) set_ints(p, p->dmaxit, 1 << 30, 1, s);
       // Arnoldi variant of the finalize step: the H column is stored unrotated
       CK(cudaMemcpyAsync(p->V, v0, sizeof(double) * p->ndof, cudaMemcpyDeviceToDevice, s));
       CK(cudaMemsetAsync(p->iters, 0, sizeof(int), s));

@@ -34,6 +34,7 @@ struct GmresView {
   int* done;          // R
   int* iters;         // R
   int maxit;
+  const int* dmaxit;  // device copy of maxit (read by kernels replayed from cycle graphs); may be NULL
   int* hflag;         // host-mapped: hflag[j] = 1 while any RHS is running after step j
   int use_cond;       // inside a captured cycle: set `cond` after every Givens step
   cudaGraphConditionalHandle cond;

@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(kThreads) update_kernel(GmresView k, double* w
         const bool bad = !isfinite(hn) || !isfinite(g[j + 1]);
         const bool est = fabs(g[j + 1]) <= k.tolabs[r];
         if (bad) atomicOr(k.err, ERRBIT_NAN);
-        if (bad || est || hn == 0.0 || j + 1 >= m || h[j] == 0.0 || k.iters[r] >= k.maxit) {
+        const int mx = k.dmaxit ? *k.dmaxit : k.maxit;
+        if (bad || est || hn == 0.0 || j + 1 >= m || h[j] == 0.0 || k.iters[r] >= mx) {
           k.jend[r] = j + 1;
           k.running[r] = 0;
           k.on_estimate[r] = est ? 1 : 0;

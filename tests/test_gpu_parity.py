@@ -447,3 +447,34 @@ def test_tet_obstacle_polynomial_preconditioners_match_oracle(pc, deg):
     assert oi['converged']
     assert abs(info.iters - oi['iters']) <= max(2, 0.05 * oi['iters']), (info.iters, oi['iters'])
     p.close()
+
+
+def test_cycle_graphs_follow_a_new_polynomial_and_iteration_cap():
+    """The GMRES cycles replay CUDA graphs that hold the polynomial's
+    coefficients by value: after a second polynomial set-up (another start
+    vector) the solve equals a fresh problem's solve with that vector, and a
+    changed iteration cap takes effect."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.hex_elasticity(n=2, k=1, R=2)
+    o = driver.opts(restart=20, rtol=1e-10, pc='bj', poly='gmres', degree=6, max_iters=2000)
+    va, vb = w.random_vector(31), w.random_vector(77)
+    p = _problem(w)
+    p.assemble(o)
+    p.setup_precond(o, va)
+    st, _ = p.solve(o)
+    assert st == 0
+    p.setup_precond(o, vb)
+    st, info = p.solve(o)
+    xb = p.free_trace()
+    q = _problem(w)
+    q.assemble(o)
+    q.setup_precond(o, vb)
+    st2, info2 = q.solve(o)
+    assert st == 0 and st2 == 0 and info.iters == info2.iters
+    assert np.array_equal(xb, q.free_trace())
+    o3 = driver.opts(restart=20, rtol=1e-10, pc='bj', poly='gmres', degree=6, max_iters=3)
+    st3, info3 = p.solve(o3)
+    assert info3.iters <= 3 and info3.converged == 0
+    p.close()
+    q.close()
