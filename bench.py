@@ -70,9 +70,11 @@ def parse():
                          'Newton with BJ, BJ-PP(10), ASM, ASM-PP(10) GMRES(50) to 1e-6)')
     ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
                     help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
-    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64'], default=None,
+    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64', 'generate'],
+                    default=None,
                     help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
-                         'one FP32 hdg_apply_K call (matvec) or one solve (solve-*), for profilers; no JSON')
+                         'one FP32 hdg_apply_K call (matvec), one solve (solve-*) or two hdg_hex_blocks calls '
+                         '(generate: the element blocks generated on the device), for profilers; no JSON')
     return ap.parse_args()
 
 
@@ -876,8 +878,21 @@ def run_profile(args):
     from hdg_inputs import workloads as W
     from paper_2512_13619_gb300 import driver, _lib as L
     w = W.hex_poisson(n=args.n, k=args.k)
-    blk = w.blocks()
     p = driver.Problem.from_workload(w, 0)
+    if args.profile == 'generate':
+        verts, perm, nquad = driver.hex_geometry_inputs(w)
+        dv, dp = torch.from_numpy(verts).cuda(), torch.from_numpy(perm).cuda()
+        phys, _keep = L.physics(w.phys.Cq, w.phys.Cu, w.phys.Rr, w.phys.tau)
+        one = w.blocks(0, 1)
+        out = [torch.empty((w.n_elem,) + one[k].shape[1:], dtype=torch.float64, device='cuda')
+               for k in driver.BLOCK_NAMES[:9]]
+        for _ in range(2):
+            driver.check(L.hdg_hex_blocks(p.h, w.n_elem, nquad, dv, dp, phys, out, 1), 'hex_blocks')
+        torch.cuda.synchronize()
+        p.close()
+        print('profile run done')
+        return
+    blk = w.blocks()
     if args.no_graphs:
         L.hdg_set_graphs(p.h, 0)
     dblk = {k: torch.from_numpy(np.ascontiguousarray(blk[k])).cuda() for k in driver.BLOCK_NAMES}
