@@ -205,7 +205,11 @@ typedef struct {
  *              that carries the face's global node j
  *   ru, ruh    as hdg_condense (load vectors; count x M*P_E x R and
  *              count x N_lfe*M*P_F x R)
- * verts, face_perm, ru, ruh are host or device per on_device.  Errors:
+ * verts, face_perm, ru, ruh are host or device per on_device.  The
+ * generation's scratch (per element of a condensation chunk: about
+ * P_E (4 nq + P_E) + 6 nq_f (5 P_F + P_E) + 24 P_F (P_E + P_F) doubles, nq and
+ * nq_f the volume and face quadrature points) and the reference tables are
+ * allocated on first use and are not part of hdg_workspace_bytes.  Errors:
  * HDG_ERR_ARG (shapes, nquad outside 1..12, a face_perm entry outside
  * 0..P_F-1), HDG_ERR_SINGULAR (a degenerate element), as hdg_condense. */
 hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad, const double* verts,
