@@ -1380,9 +1380,14 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
       CK(cudaEventRecord(p->ev_start, s));                  // earlier work on the staging buffers
       CK(cudaStreamWaitEvent(p->copy_stream, p->ev_start, 0));
     }
-    int64_t ci = 0;
-    for (int64_t c0 = 0; c0 < count; c0 += p->chunk, ++ci) {
-      const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
+    // with overlapped copies the first chunks ramp up (1/8, 1/4, 1/2 of the
+    // staging capacity, then full): only the first, small copy is exposed,
+    // and each later copy (faster per element than the condensation) hides
+    // behind the condensation of the chunk before it
+    int64_t ci = 0, ec = 0;
+    for (int64_t c0 = 0; c0 < count; c0 += ec, ++ci) {
+      const int64_t cap = (overlap && ci < 3) ? std::max<int64_t>(1, p->chunk >> (3 - ci)) : p->chunk;
+      ec = std::min<int64_t>(cap, count - c0);
       const int bsel = (int)(ci & 1);
       const double* dev[11];
       double* st = (overlap && bsel) ? p->d_stage2 : p->d_stage;
