@@ -216,6 +216,13 @@ hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad,
                             const int32_t* face_perm, const hdg_physics* phys, const double* ru,
                             const double* ruh, int on_device, void* stream);
 
+/* How hdg_condense_hex / hdg_hex_blocks form M^e and B_d: 1 (default) by sum
+ * factorisation of the tensor-product rule (three 1D contractions per
+ * weight field, FP64; used for k <= 4 and 2 <= nquad <= 8), 0 by dense products
+ * of the weighted basis tables on the condensation's GEMM path.  Both give
+ * the same integrals up to rounding.  Errors: HDG_ERR_ARG. */
+hdg_status hdg_set_hex_generation(hdg_problem p, int sum_factorised);
+
 /* The generated blocks themselves (tests, callers that keep them): out[9]
  * are device buffers for Me, Bd, Cd, D, E, F, G, H, J of `count` elements in
  * hdg_condense's layout.  Inputs as hdg_condense_hex. */

@@ -80,6 +80,7 @@ _SIGS = {
     'hdg_set_tuning': (_I, [_V, _I, _I, ctypes.POINTER(_I)]),
     'hdg_condense_hex': (_I, [_V, _I64, _I64, _I, _P, _P, ctypes.POINTER(hdg_physics), _P, _P, _I, _V]),
     'hdg_hex_blocks': (_I, [_V, _I64, _I, _P, _P, ctypes.POINTER(hdg_physics), ctypes.POINTER(_P), _I, _V]),
+    'hdg_set_hex_generation': (_I, [_V, _I]),
 }
 
 _lib = None
@@ -176,6 +177,10 @@ def hdg_hex_blocks(p, count, nquad, verts, face_perm, phys, out, on_device, stre
     arr = (_P * 9)(*[ptr(a) for a in out])
     return load().hdg_hex_blocks(p, count, nquad, ptr(verts), ptr(face_perm), ctypes.byref(phys), arr,
                                  int(on_device), stream_ptr(stream))
+
+
+def hdg_set_hex_generation(p, sum_factorised):
+    return load().hdg_set_hex_generation(p, int(sum_factorised))
 
 
 def hdg_set_dirichlet(p, uhat_dirichlet, on_device, stream=None):

@@ -191,6 +191,7 @@ struct hdg_problem_s {
   unsigned char* d_genin = nullptr;
   int64_t genin_cap = 0;
   double* d_phys = nullptr;
+  int hex_sf = 1;                  // M^e, B_d of generated blocks by sum factorisation (0: dense products)
   // autotuned launch configurations [operation: K, BJ, ASM][precision]
   BrCfg tune[3][3];
   float tune_us[3][3] = {};        // measured time of the chosen configuration
@@ -1452,7 +1453,7 @@ T* grow(hdg_problem p, T*& buf, int64_t& cap, int64_t need) {
 }
 
 struct HexDev {
-  const double *phi, *dphi, *wq, *dN, *fphi, *fdN, *psi, *wf, *phiT, *fphiT;
+  const double *phi, *dphi, *wq, *dN, *fphi, *fdN, *psi, *wf, *phiT, *fphiT, *b1, *d1;
 };
 
 // Validates the shapes, builds and uploads the reference tables for
@@ -1467,8 +1468,8 @@ hdg_status hex_prepare(hdg_problem p, int nquad, const hdg_physics* ph, HexDev* 
   if (p->hex_k != k || p->hex_nq != nquad) {
     p->hex_tab = build_hex_tables(k, nquad);
     const HexTables& T = p->hex_tab;
-    const std::vector<double>* parts[10] = {&T.phi, &T.dphi, &T.wq, &T.dN, &T.fphi, &T.fdN, &T.psi, &T.wf,
-                                            &T.phiT, &T.fphiT};
+    const std::vector<double>* parts[12] = {&T.phi, &T.dphi, &T.wq, &T.dN, &T.fphi, &T.fdN, &T.psi, &T.wf,
+                                            &T.phiT, &T.fphiT, &T.b1, &T.d1};
     int64_t tot = 0;
     for (auto* v : parts) tot += (int64_t)v->size();
     grow(p, p->d_hextab, p->hextab_cap, tot);
@@ -1483,11 +1484,11 @@ hdg_status hex_prepare(hdg_problem p, int nquad, const hdg_physics* ph, HexDev* 
   }
   const HexTables& T = p->hex_tab;
   const double* base = p->d_hextab;
-  const double** outs[10] = {&dev->phi, &dev->dphi, &dev->wq, &dev->dN, &dev->fphi, &dev->fdN, &dev->psi,
-                             &dev->wf, &dev->phiT, &dev->fphiT};
-  const std::vector<double>* parts[10] = {&T.phi, &T.dphi, &T.wq, &T.dN, &T.fphi, &T.fdN, &T.psi, &T.wf,
-                                          &T.phiT, &T.fphiT};
-  for (int i = 0; i < 10; ++i) {
+  const double** outs[12] = {&dev->phi, &dev->dphi, &dev->wq, &dev->dN, &dev->fphi, &dev->fdN, &dev->psi,
+                             &dev->wf, &dev->phiT, &dev->fphiT, &dev->b1, &dev->d1};
+  const std::vector<double>* parts[12] = {&T.phi, &T.dphi, &T.wq, &T.dN, &T.fphi, &T.fdN, &T.psi, &T.wf,
+                                          &T.phiT, &T.fphiT, &T.b1, &T.d1};
+  for (int i = 0; i < 12; ++i) {
     *outs[i] = base;
     base += parts[i]->size();
   }
@@ -1539,12 +1540,18 @@ void hex_generate_chunk(hdg_problem p, const HexDev& dev, int64_t ec, const doub
   d.Cd = out[2]; d.Dm = out[3]; d.Em = out[4]; d.Fm = out[5]; d.Gm = out[6]; d.Hm = out[7]; d.Jm = out[8];
   d.err = p->d_err;
   const int n = (int)ec;
-  hex_geometry(d, s);
-  // M^e = Phi^T (W Phi);  B_d = G_d^T (W Phi);  Mf = sum over faces Phi_f^T (W Phi_f)
-  gemm_c(p, gd(PE, PE, nq, dev.phiT, nq, 0, 0, d.AW, PE, (int64_t)nq * PE, 0, out[0], PE, (int64_t)PE * PE, 0, 1.0,
-              0.0, n, 1), s);
-  gemm_c(p, gd(PE, PE, nq, d.GT, nq, (int64_t)3 * PE * nq, (int64_t)PE * nq, d.AW, PE, (int64_t)nq * PE, 0, out[1],
-              PE, (int64_t)3 * PE * PE, (int64_t)PE * PE, 1.0, 0.0, n, 3), s);
+  // M^e and B_d: sum factorisation of the tensor-product rule where its
+  // shared memory allows, else M^e = Phi^T (W Phi), B_d = G_d^T (W Phi)
+  if (p->hex_sf && hex_mass_grad_sf(d, T.n1, T.nq1, dev.b1, dev.d1, out[0], out[1], s)) {
+    hex_face_geometry(d, s);
+  } else {
+    hex_geometry(d, s);
+    gemm_c(p, gd(PE, PE, nq, dev.phiT, nq, 0, 0, d.AW, PE, (int64_t)nq * PE, 0, out[0], PE, (int64_t)PE * PE, 0,
+                1.0, 0.0, n, 1), s);
+    gemm_c(p, gd(PE, PE, nq, d.GT, nq, (int64_t)3 * PE * nq, (int64_t)PE * nq, d.AW, PE, (int64_t)nq * PE, 0,
+                out[1], PE, (int64_t)3 * PE * PE, (int64_t)PE * PE, 1.0, 0.0, n, 3), s);
+  }
+  // Mf = sum over faces Phi_f^T (W Phi_f)
   gemm_c(p, gd(PE, PE, 6 * nfq, dev.fphiT, 6 * nfq, 0, 0, d.PW, PE, (int64_t)6 * nfq * PE, 0, d.Mf, PE,
               (int64_t)PE * PE, 0, 1.0, 0.0, n, 1), s);
   // per face: [EF | EFN_d] = Phi_f^T [W psi | W n_d psi],  [FF | FFN_d] = psi^T [W psi | W n_d psi]
@@ -2237,6 +2244,12 @@ hdg_status hdg_set_condense_chunk(hdg_problem p, int64_t elems) {
     p->d_stage2 = nullptr;
   }
   p->chunk = elems;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_hex_generation(hdg_problem p, int sum_factorised) {
+  if (!p || sum_factorised < 0 || sum_factorised > 1) return HDG_ERR_ARG;
+  p->hex_sf = sum_factorised;
   return HDG_OK;
 }
 

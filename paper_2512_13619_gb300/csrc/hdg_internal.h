@@ -61,6 +61,7 @@ struct HexTables {
   std::vector<double> fdN;     // (6 nfq) x 8 x 3
   std::vector<double> psi;     // nfq x PF face basis
   std::vector<double> wf;      // nfq face weights
+  std::vector<double> b1, d1;  // nq1 x (k+1): 1D Lagrange values and derivatives at the 1D Gauss points
 };
 HexTables build_hex_tables(int k, int nquad);
 // per-element scratch (doubles) of the generation steps
@@ -84,8 +85,14 @@ struct HexGenDesc {
   double *Cd, *Dm, *Em, *Fm, *Gm, *Hm, *Jm;
   unsigned* err;
 };
-// AW, GT, BWN, PW, PsiT from the vertices (two kernels)
+// AW, GT (volume) and BWN, PW, PsiT (faces) from the vertices
 void hex_geometry(const HexGenDesc& d, cudaStream_t s);
+void hex_face_geometry(const HexGenDesc& d, cudaStream_t s);
+// M^e and B_d by sum factorisation of the tensor-product rule (FP64, one CTA
+// per element): per weight field three 1D contractions.  b1, d1: device 1D
+// tables (nq1 x n1).  Returns false (nothing launched) beyond n1 <= 5, nq1 <= 8.
+bool hex_mass_grad_sf(const HexGenDesc& d, int n1, int nq1, const double* b1, const double* d1, double* Me,
+                      double* Bd, cudaStream_t s);
 // Cd, D, E, F, G, H, J from Me, Sd, Mf, EF4, FF4 and the physics (seven kernels)
 void hex_expand(const HexGenDesc& d, cudaStream_t s);
 

@@ -204,6 +204,9 @@ HexTables build_hex_tables(int k, int nquad) {
         trilinear_dN(xi, &T.fdN[((size_t)l * nfq + q) * 24]);
       }
     }
+  T.b1.assign((size_t)n * T.n1, 0.0);
+  T.d1.assign((size_t)n * T.n1, 0.0);
+  for (int i = 0; i < n; ++i) lagrange(g, x[i], &T.b1[(size_t)i * T.n1], &T.d1[(size_t)i * T.n1]);
   return T;
 }
 
@@ -276,6 +279,109 @@ __global__ void hex_vol_geom_kernel(HexGenDesc d) {
     for (int a = 0; a < 3; ++a)
       GT[((int64_t)a * PE + i) * nq + q] = dp[0] * gq[1 + a] + dp[1] * gq[4 + a] + dp[2] * gq[7 + a];
   }
+}
+
+// Sum factorisation of M^e and B_d over the tensor-product rule, one CTA per
+// element.  With phi_i = a_{i1}(x) a_{i2}(y) a_{i3}(z) (i = i1 + n1 (i2 + n1 i3))
+// and the points q = q1 + m (q2 + m q3), a weight field W(q) gives (the
+// intermediates stored with the pair (i1, j1) fastest, so that neighbouring
+// threads touch neighbouring shared-memory words)
+//   T1[i1,j1,q2,q3]     = sum_q1 X1[q1,i1] A[q1,j1] W[q1,q2,q3]
+//   T2[i1,j1,i2,j2,q3]  = sum_q2 X2[q2,i2] A[q2,j2] T1[i1,j1,q2,q3]
+//   O[i,j]              = sum_q3 X3[q3,i3] A[q3,j3] T2[i1,j1,i2,j2,q3]
+// (X = A the values, or the derivatives D on one axis).  M^e takes W = w |det J|
+// with X = A; B_c[i,j] = int (grad phi_i)_c phi_j sums, over the axis b of the
+// derivative, the fields W_bc = w |det J| (J^{-1})_bc with D on axis b.
+constexpr int kSfN1 = 5, kSfNQ = 8;
+template <int n1, int m>
+__global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, const double* b1g, const double* d1g,
+                                                                double* Meo, double* Bdo) {
+  extern __shared__ double sm[];
+  constexpr int nq = m * m * m, PE = n1 * n1 * n1;
+  constexpr int n2 = n1 * n1;
+  double* X8 = sm;                          // 24
+  double* b1 = X8 + 24;                     // m x n1
+  double* d1 = b1 + m * n1;                 // m x n1
+  double* geo = d1 + m * n1;                // nq x 10: w |det J| and w |det J| (J^{-1})_bc ([b][c])
+  double* T1 = geo + nq * 10;               // 3 fields x m^2 x n2
+  double* T2 = T1 + 3 * n2 * m * m;         // 3 fields x m x n2^2
+  const int64_t e = blockIdx.x;
+  for (int i = threadIdx.x; i < 24; i += blockDim.x) X8[i] = d.verts[e * 24 + i];
+  for (int i = threadIdx.x; i < m * n1; i += blockDim.x) {
+    b1[i] = b1g[i];
+    d1[i] = d1g[i];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double J[3][3], A[3][3];
+    jac_at(X8, d.dN + (int64_t)q * 24, J);
+    const double det = adj3(J, A);
+    if (!(det != 0.0) || !isfinite(det)) atomicOr(d.err, ERRBIT_SINGULAR);
+    const double wdet = d.wq[q] * fabs(det);
+    const double winv = wdet / det;
+    double* gq = geo + q * 10;
+    gq[0] = wdet;
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) gq[1 + b * 3 + c] = A[b][c] * winv;
+  }
+  __syncthreads();
+  // pass 0: M^e (one field); passes 1..3: B_c (three fields, derivative axis b = 0, 1, 2)
+  for (int pass = 0; pass < 4; ++pass) {
+    const int nf = pass == 0 ? 1 : 3;
+    const int c = pass - 1;
+    // stage 1: T1[f][q3][q2][i1 j1] (i1 j1 fastest: consecutive lanes, consecutive words)
+    for (int t = threadIdx.x; t < nf * n2 * m * m; t += blockDim.x) {
+      const int ij1 = t % n2;
+      const int r = t / n2;
+      const int q2 = r % m, q3 = (r / m) % m, f = r / (m * m);
+      const int i1 = ij1 / n1, j1 = ij1 - i1 * n1;
+      const double* X = (pass > 0 && f == 0) ? d1 : b1;
+      const int wf = pass == 0 ? 0 : 1 + f * 3 + c;
+      double acc = 0.0;
+#pragma unroll
+      for (int q1 = 0; q1 < m; ++q1)
+        acc += X[q1 * n1 + i1] * b1[q1 * n1 + j1] * geo[((q3 * m + q2) * m + q1) * 10 + wf];
+      T1[t] = acc;
+    }
+    __syncthreads();
+    // stage 2: T2[f][q3][i2 j2][i1 j1]
+    for (int t = threadIdx.x; t < nf * n2 * n2 * m; t += blockDim.x) {
+      const int ij1 = t % n2;
+      const int r = t / n2;
+      const int ij2 = r % n2, q3 = (r / n2) % m, f = r / (n2 * m);
+      const int i2 = ij2 / n1, j2 = ij2 - i2 * n1;
+      const double* X = (pass > 0 && f == 1) ? d1 : b1;
+      const double* t1 = T1 + (f * m + q3) * m * n2 + ij1;
+      double acc = 0.0;
+#pragma unroll
+      for (int q2 = 0; q2 < m; ++q2) acc += X[q2 * n1 + i2] * b1[q2 * n1 + j2] * t1[q2 * n2];
+      T2[t] = acc;
+    }
+    __syncthreads();
+    // stage 3: O[i, j], summed over the fields
+    double* out = pass == 0 ? Meo + e * (int64_t)PE * PE : Bdo + (e * 3 + c) * (int64_t)PE * PE;
+    for (int t = threadIdx.x; t < PE * PE; t += blockDim.x) {
+      const int i = t / PE, j = t - i * PE;
+      const int i3 = i / n2, i2 = (i / n1) % n1, i1 = i % n1;
+      const int j3 = j / n2, j2 = (j / n1) % n1, j1 = j % n1;
+      const int ij1 = i1 * n1 + j1, ij2 = i2 * n1 + j2;
+      double acc = 0.0;
+      for (int f = 0; f < nf; ++f) {
+        const double* X = (pass > 0 && f == 2) ? d1 : b1;
+        const double* t2 = T2 + (f * m * n2 + ij2) * n2 + ij1;
+#pragma unroll
+        for (int q3 = 0; q3 < m; ++q3) acc += X[q3 * n1 + i3] * b1[q3 * n1 + j3] * t2[q3 * n2 * n2];
+      }
+      out[t] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+size_t sf_smem(int n1, int m) {
+  const int n2 = n1 * n1;
+  return sizeof(double) * (24 + 2 * (size_t)m * n1 + (size_t)m * m * m * 10 + 3 * (size_t)n2 * m * m +
+                           3 * (size_t)n2 * n2 * m);
 }
 
 // One CTA per element: per face point the cofactor normal nv = adj(J)^T e_l,
@@ -444,13 +550,55 @@ void launch_expand(const HexGenDesc& d, cudaStream_t s) {
 void hex_geometry(const HexGenDesc& d, cudaStream_t s) {
   if (d.count <= 0) return;
   const size_t sv = sizeof(double) * (24 + (size_t)d.nq * 10);
-  const size_t sf = sizeof(double) * (24 + (size_t)6 * d.nfq * 4);
   cudaFuncSetAttribute(hex_vol_geom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(hex_face_geom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   count_launch();
   hex_vol_geom_kernel<<<(unsigned)d.count, 256, sv, s>>>(d);
+  hex_face_geometry(d, s);
+}
+
+void hex_face_geometry(const HexGenDesc& d, cudaStream_t s) {
+  if (d.count <= 0) return;
+  const size_t sf = sizeof(double) * (24 + (size_t)6 * d.nfq * 4);
+  cudaFuncSetAttribute(hex_face_geom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   count_launch();
   hex_face_geom_kernel<<<(unsigned)d.count, 256, sf, s>>>(d);
+}
+
+template <int n1, int m>
+void launch_sf(const HexGenDesc& d, const double* b1, const double* d1, double* Me, double* Bd, size_t smem,
+               cudaStream_t s) {
+  cudaFuncSetAttribute(hex_mass_grad_sf_kernel<n1, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  count_launch();
+  hex_mass_grad_sf_kernel<n1, m><<<(unsigned)d.count, 256, smem, s>>>(d, b1, d1, Me, Bd);
+}
+
+template <int n1>
+bool launch_sf_m(const HexGenDesc& d, int m, const double* b1, const double* d1, double* Me, double* Bd, size_t smem,
+                 cudaStream_t s) {
+  switch (m) {
+    case 2: launch_sf<n1, 2>(d, b1, d1, Me, Bd, smem, s); return true;
+    case 3: launch_sf<n1, 3>(d, b1, d1, Me, Bd, smem, s); return true;
+    case 4: launch_sf<n1, 4>(d, b1, d1, Me, Bd, smem, s); return true;
+    case 5: launch_sf<n1, 5>(d, b1, d1, Me, Bd, smem, s); return true;
+    case 6: launch_sf<n1, 6>(d, b1, d1, Me, Bd, smem, s); return true;
+    case 7: launch_sf<n1, 7>(d, b1, d1, Me, Bd, smem, s); return true;
+    case 8: launch_sf<n1, 8>(d, b1, d1, Me, Bd, smem, s); return true;
+    default: return false;
+  }
+}
+
+bool hex_mass_grad_sf(const HexGenDesc& d, int n1, int nq1, const double* b1, const double* d1, double* Me,
+                      double* Bd, cudaStream_t s) {
+  if (n1 < 2 || n1 > kSfN1 || nq1 < 2 || nq1 > kSfNQ) return false;
+  if (d.count <= 0) return true;
+  const size_t smem = sf_smem(n1, nq1);
+  if (smem > 200 * 1024) return false;
+  switch (n1) {
+    case 2: return launch_sf_m<2>(d, nq1, b1, d1, Me, Bd, smem, s);
+    case 3: return launch_sf_m<3>(d, nq1, b1, d1, Me, Bd, smem, s);
+    case 4: return launch_sf_m<4>(d, nq1, b1, d1, Me, Bd, smem, s);
+    default: return launch_sf_m<5>(d, nq1, b1, d1, Me, Bd, smem, s);
+  }
 }
 
 void hex_expand(const HexGenDesc& d, cudaStream_t s) {

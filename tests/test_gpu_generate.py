@@ -23,10 +23,11 @@ CASES = {
 }
 
 
-def _gen_blocks(w, on_device):
+def _gen_blocks(w, on_device, sf=1):
     import torch
     from paper_2512_13619_gb300 import driver, _lib as L
     p = driver.Problem.from_workload(w)
+    assert L.hdg_set_hex_generation(p.h, sf) == 0
     verts, perm, nquad = driver.hex_geometry_inputs(w)
     ph, keep = L.physics(w.phys.Cq, w.phys.Cu, w.phys.Rr, w.phys.tau)
     ref = w.blocks()
@@ -38,15 +39,17 @@ def _gen_blocks(w, on_device):
     return st, {k: o.cpu().numpy() for k, o in zip(NAMES9, out)}, ref
 
 
+@pytest.mark.parametrize('sf', [1, 0])
 @pytest.mark.parametrize('name', sorted(CASES))
-def test_generated_blocks_match_host_generator(name):
+def test_generated_blocks_match_host_generator(name, sf):
     """Every block of every element equals the host generator's within 1e-13
     of the block's largest entry (the reference tables are built
     independently in C++: Gauss and GLL nodes by Newton's method, Lagrange
-    polynomials in product form)."""
+    polynomials in product form), with M^e and B_d by sum factorisation
+    (sf = 1) and by dense products (sf = 0)."""
     need_gpu()
     w = CASES[name]()
-    st, gen, ref = _gen_blocks(w, on_device=(name == 'poisson_q3'))
+    st, gen, ref = _gen_blocks(w, on_device=(name == 'poisson_q3'), sf=sf)
     assert st == 0
     for k in NAMES9:
         assert rel(gen[k], ref[k]) < 1e-13, (k, rel(gen[k], ref[k]))
