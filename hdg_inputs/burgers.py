@@ -82,7 +82,6 @@ class Burgers:
         mats = blk.element_matrices(m, self.ref, self.perm, np.arange(m.n_elem))
         qb = blk.hdg_blocks(mats, blk.poisson(2))
         self.Me, self.Bd, self.Cd = qb['Me'], qb['Bd'], qb['Cd']
-        self.mats = mats
 
     # sizes
     @property
