@@ -273,3 +273,45 @@ def test_class_blocks_equal_per_element_blocks():
     for k in ('Me', 'Bd', 'Cd', 'D', 'E', 'F', 'G', 'H', 'J'):
         assert np.abs(rb[k][cls] - full[k]).max() <= 1e-14 * np.abs(full[k]).max(), k
     assert np.array_equal(ruh, full['ruh']) and not full['ru'].any()
+
+
+@pytest.mark.parametrize('k,lo', [(1, 1.7), (2, 2.75)])
+def test_quad_mms_rates(k, lo):
+    """Q^k quadrilaterals (the Burgers workload's elements): Poisson with
+    u = sin(pi x) sin(pi y), errors of u and q fall at about order k + 1."""
+    from hdg_inputs import mesh as meshmod
+    errs = []
+    for n in (4, 8):
+        m = meshmod.quad_mesh(n)
+        ref = blk.reference_element(m, k)
+        u, f, q = W._sin_product(2)
+        w = W.Workload('quad_poisson', m, ref, blk.face_permutations(m, ref), blk.poisson(2), 1, 'function', f, u,
+                       q, k=k)
+        errs.append(_solve_errors(w)[3])
+    (eu0, eq0), (eu1, eq1) = errs
+    assert np.log2(eu0 / eu1) > lo and np.log2(eq0 / eq1) > lo
+
+
+def test_beam_preconditioner_ordering():
+    """Sec. 6.2's ordering on the 10 x 2 x 2 Q^1 beam, GMRES(50)-CGS to 1e-6:
+    ASM-PP(10) < BJ-PP(10) < ASM < BJ in iterations (Tables 5-6), with the
+    polynomials cutting the counts at least fivefold (here 6403 -> 19 for BJ,
+    146 -> 16 for ASM)."""
+    from oracle import precond, krylov
+    w = W.hex_beam(n=2, k=1)
+    s = OracleSystem(w)
+    b = s.r[:, 0]
+    K = s.K.tocsr()
+    Binv = precond.bj_setup(K, s.bsz)
+    subs = precond.asm_setup(K, s.elem_dofs)
+    its = {}
+    for name, M in (('BJ', lambda v: precond.bj_apply(Binv, v)), ('ASM', lambda v: precond.asm_apply(subs, v))):
+        _, it = krylov.gmres(lambda v: K @ v, M, b, m=50, rtol=1e-6, maxit=20000)
+        its[name] = it['iters']
+        A = lambda v, M=M: M(K @ v)
+        th = precond.pp_setup(A, w.random_vector(11), 10)
+        _, it = krylov.gmres(lambda v: K @ v, lambda v: precond.pp_apply(A, th, M(v)), b, m=50, rtol=1e-6,
+                             maxit=20000)
+        its[name + '-PP'] = it['iters']
+    assert its['ASM-PP'] < its['BJ-PP'] < its['ASM'] < its['BJ']
+    assert its['BJ-PP'] * 5 < its['BJ'] and its['ASM-PP'] * 5 < its['ASM']
