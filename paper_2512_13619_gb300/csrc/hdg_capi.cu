@@ -1425,6 +1425,8 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
@@ -1678,6 +1680,8 @@ hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhatD, int on_device, 
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
@@ -2027,6 +2031,8 @@ hdg_status hdg_apply_K(hdg_problem p, int prec, const double* x, double* y, void
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
@@ -2067,6 +2073,8 @@ hdg_status hdg_get_condensed(hdg_problem p, int64_t e0, int64_t count, double* K
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
@@ -2096,6 +2104,8 @@ hdg_status hdg_get_face_rows(hdg_problem p, int64_t f0, int64_t count, double* b
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
@@ -2225,6 +2235,8 @@ hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double*
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
@@ -2301,6 +2313,8 @@ hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t 
     return HDG_OK;
   } catch (const CudaError& e) {
     return to_status(e);
+  } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
   }
 }
 
