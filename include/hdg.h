@@ -195,7 +195,7 @@ typedef struct {
  * on the device (the element integrals of Sec. 4.1 as batched products of
  * basis tables with quadrature weights, M = Phi W, then the blocks of
  * Eq. matrixform), chunk by chunk, without the blocks ever leaving the GPU.
- * Requires dim 3, N_lfe 6, P_E = (k+1)^3, P_F = (k+1)^2.  Reference element:
+ * Requires dim 3, N_lfe 6, P_E = (k+1)^3, P_F = (k+1)^2, M <= 5.  Reference element:
  * Q^k on Gauss-Lobatto-Legendre nodes (x fastest), an nquad^3 Gauss rule
  * (nquad^2 on faces), local face l fixing reference coordinate l/2 at -1
  * (l even) or +1 (l odd) with parameters the other two coordinates in
