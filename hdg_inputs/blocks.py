@@ -224,15 +224,16 @@ def face_permutations(mesh, ref):
     perm[:] = np.arange(PF)
     fe = mesh.face_elem
     scale = np.abs(mesh.verts).max() + 1.0
-    for f in np.nonzero(fe[:, 2] >= 0)[0]:
-        e1, l1, e2, l2 = fe[f]
-        A = coords[e1, l1]
-        Bc = coords[e2, l2]
-        dist = np.linalg.norm(A[:, None, :] - Bc[None, :, :], axis=2)
-        p = np.argmin(dist, axis=1)
-        assert np.all(dist[np.arange(PF), p] < 1e-9 * scale), "face nodes do not match"
-        assert len(set(p.tolist())) == PF
-        perm[e2, l2] = p
+    inner = np.nonzero(fe[:, 2] >= 0)[0]
+    for c0 in range(0, len(inner), 8192):
+        f = inner[c0:c0 + 8192]
+        A = coords[fe[f, 0], fe[f, 1]]                                   # (nf, PF, dim)
+        Bc = coords[fe[f, 2], fe[f, 3]]
+        dist = np.linalg.norm(A[:, :, None, :] - Bc[:, None, :, :], axis=3)
+        p = np.argmin(dist, axis=2)                                      # (nf, PF)
+        assert np.all(np.take_along_axis(dist, p[:, :, None], axis=2) < 1e-9 * scale), "face nodes do not match"
+        assert np.all(np.sort(p, axis=1) == np.arange(PF)), "face node matching is not one to one"
+        perm[fe[f, 2], fe[f, 3]] = p
     return perm
 
 
