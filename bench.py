@@ -14,7 +14,7 @@ workload's configured path); the same step with the mixed solve (FP32 blocks
 + FP64 iterative refinement) and the FP64 step to 1e-10 are timed beside it.
 
 Prints ONE JSON line (rank 0).  Several ranks run independent replicas (the
-path is not sharded in this build); timings are the max over ranks.
+path is not sharded); timings are the max over ranks.
 `--impl reference` times the FP64 CPU oracle (test infrastructure) on the
 same workload.
 """
