@@ -150,21 +150,20 @@ class Burgers:
     def _face_fields(self, l, q, u, ue):
         Q = self.Q
         ph, psi, nrm = Q.fph[l], Q.fpsi[l], Q.fn[l]
-        uf = np.einsum('qi,ei->eq', ph, u)
-        qn = np.einsum('qi,edi,eqd->eq', ph, q, nrm)
-        uhf = np.einsum('eqj,ej->eq', psi, ue[:, l])
+        uf = u @ ph.T                                                             # (E, nfq)
+        qn = (q[:, 0] @ ph.T) * nrm[..., 0] + (q[:, 1] @ ph.T) * nrm[..., 1]
+        uhf = np.matmul(psi, ue[:, l][:, :, None])[..., 0]
         return uf, qn, uhf
 
     def residual(self, q, u, uh):
         """R_u (E, PE) and the element-side trace residuals R_uhat (E, n_lfe, PF)."""
         Q, nu, tau = self.Q, self.nu, self.tau
-        uq = np.einsum('qi,ei->eq', Q.phi, u)
-        qq = np.einsum('qi,edi->eqd', Q.phi, q)
-        Fx = 0.5 * uq * uq - nu * qq[..., 0]
-        Fy = uq - nu * qq[..., 1]
-        Ru = -np.einsum('eq,eqi->ei', Q.wJ * Fx, Q.g[..., 0]) - np.einsum('eq,eqi->ei', Q.wJ * Fy, Q.g[..., 1])
+        uq = u @ Q.phi.T                                                          # (E, nq)
+        Fx = 0.5 * uq * uq - nu * (q[:, 0] @ Q.phi.T)
+        Fy = uq - nu * (q[:, 1] @ Q.phi.T)
+        Ru = -(np.matmul((Q.wJ * Fx)[:, None, :], Q.g[..., 0]) + np.matmul((Q.wJ * Fy)[:, None, :], Q.g[..., 1]))[:, 0]
         if self.f is not None:
-            Ru -= np.einsum('eq,eq,qi->ei', Q.wJ, self.f(Q.xq), Q.phi)
+            Ru -= (Q.wJ * self.f(Q.xq)) @ Q.phi
         ue = self.element_traces(uh)
         Ruh = np.zeros((self.n_elem, self.n_lfe, self.PF))
         out = self.face_outflow[self.mesh.elem_face]                                # (E, n_lfe)
@@ -173,9 +172,9 @@ class Burgers:
             nrm, w = Q.fn[l], Q.fw[l]
             cn = 0.5 * uhf * uhf * nrm[..., 0] + uhf * nrm[..., 1]
             Fn = cn - nu * qn + tau * (uf - uhf)
-            Ru += np.einsum('eq,eq,qi->ei', w, Fn, Q.fph[l])
+            Ru += (w * Fn) @ Q.fph[l]
             Fn_tr = Fn - out[:, l][:, None] * cn
-            Ruh[:, l] = np.einsum('eq,eq,eqj->ej', w, Fn_tr, Q.fpsi[l])
+            Ruh[:, l] = np.matmul((w * Fn_tr)[:, None, :], Q.fpsi[l])[:, 0]
         return Ru, Ruh
 
     def residual_norm(self, q, u, uh):
@@ -236,15 +235,15 @@ class Burgers:
         Q = self.Q
         E, PE, PF, nl = self.n_elem, self.PE, self.PF, self.n_lfe
         C = self._constant_blocks()
-        uq = Q.phi @ u.T                                                          # (nq, E)
-        Em = C['E'] - np.transpose((Q.wJ * uq.T)[:, :, None] * Q.g[..., 0], (0, 2, 1)) @ Q.phi
+        uq = u @ Q.phi.T                                                          # (E, nq)
+        Em = C['E'] - np.transpose((Q.wJ * uq)[:, :, None] * Q.g[..., 0], (0, 2, 1)) @ Q.phi
         Fm = C['F'].copy()
         Jd = C['J'].copy()
         ue = self.element_traces(uh)
         out = self.face_outflow[self.mesh.elem_face]
         for l in range(nl):
             ph, psi, nrm, w = Q.fph[l], Q.fpsi[l], Q.fn[l], Q.fw[l]
-            uhf = np.einsum('eqj,ej->eq', psi, ue[:, l])
+            uhf = np.matmul(psi, ue[:, l][:, :, None])[..., 0]
             cu = (w * uhf * nrm[..., 0])[:, :, None]                              # (E, nfq, 1)
             Fm[:, :, l] += np.transpose(cu * ph[None], (0, 2, 1)) @ psi
             Jd[:, l] += np.transpose(psi, (0, 2, 1)) @ ((1.0 - out[:, l])[:, None, None] * cu * psi)
