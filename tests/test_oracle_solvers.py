@@ -233,3 +233,85 @@ def test_chebyshev_bounds_from_exact_ritz_values():
     A = Q @ np.diag(lam) @ Q.T
     a, b = precond.chebyshev_bounds(lambda v: A @ v, rng.standard_normal(6), 6)
     assert abs(a - 0.45) < 1e-10 and abs(b - 4.4) < 1e-10
+
+
+# ------------------------------------------------------------ ASM apply pins
+def _asm_operator_checks(apply, s, subs):
+    """Invariants of P = sum_e R_e^T (R_e K R_e^T)^{-1} R_e (Sec. 3.3) for a
+    symmetric definite K: P is symmetric with K's sign of definiteness, and
+    trace(P) = sum_e trace((R_e K R_e^T)^{-1}) because R_e R_e^T = I.  Returns
+    (symmetry error, definiteness holds, relative trace error)."""
+    rng = np.random.default_rng(12)
+    n = s.K.shape[0]
+    y1, y2 = rng.standard_normal(n), rng.standard_normal(n)
+    p1, p2 = apply(subs, y1), apply(subs, y2)
+    sym = abs(y1 @ p2 - y2 @ p1) / (np.linalg.norm(y1) * np.linalg.norm(p2))
+    sign = np.sign((s.K @ y1) @ y1)
+    definite = all(sign * (y @ apply(subs, y)) > 0 for y in rng.standard_normal((5, n)))
+    tr = 0.0
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        tr += apply(subs, e)[i]
+    tr_local = sum(np.sum(1.0 / np.linalg.eigvalsh(0.5 * (A + A.T)))
+                   for A in precond.asm_local_matrices(s.K, s.elem_dofs))
+    return sym, definite, abs(tr - tr_local) / abs(tr_local)
+
+
+def test_asm_apply_symmetric_definite_and_trace(hex_el_sys):
+    """The HDG elasticity K is symmetric and definite, so the ASM operator of
+    Sec. 3.3 / 4.6 is symmetric, definite with the same sign, and its trace is
+    the sum of the local inverses' traces.  Dropping or overwriting the
+    contribution of one element on a shared face breaks all three."""
+    s = hex_el_sys
+    Kd = s.K.toarray()
+    assert np.abs(Kd - Kd.T).max() < 1e-12 * np.abs(Kd).max()
+    subs = precond.asm_setup(s.K, s.elem_dofs)
+    sym, definite, tr = _asm_operator_checks(precond.asm_apply, s, subs)
+    assert sym < 1e-12 and definite and tr < 1e-10
+
+
+def test_asm_apply_planted_overwrite_is_caught(hex_el_sys):
+    """Planted mistakes: z[d] = ... instead of z[d] += ... (each shared face
+    keeps only the last element's contribution), and one element's
+    contribution left out.  The invariants above must reject both."""
+    s = hex_el_sys
+    subs = precond.asm_setup(s.K, s.elem_dofs)
+
+    def overwrite(subs_, y):
+        z = np.zeros_like(y)
+        for d, inv in subs_:
+            z[d] = inv @ y[d]
+        return z
+
+    def drop_one(subs_, y):
+        z = np.zeros_like(y)
+        for d, inv in subs_[1:]:
+            z[d] += inv @ y[d]
+        return z
+    for wrong in (overwrite, drop_one):
+        sym, definite, tr = _asm_operator_checks(wrong, s, subs)
+        assert sym > 1e-6 or not definite or tr > 1e-6
+
+
+def test_asm_apply_exact_on_disjoint_subdomains():
+    """Subdomains that partition the unknowns of a block-diagonal K (no face
+    shared by two elements): the ASM operator is K^{-1} exactly."""
+    rng = np.random.default_rng(13)
+    sizes = [5, 3, 7, 4]
+    blocks = []
+    for m in sizes:
+        G = rng.standard_normal((m, m))
+        blocks.append(G @ G.T + m * np.eye(m))
+    K = sp.csr_matrix(sp.block_diag(blocks))
+    n = K.shape[0]
+    perm = rng.permutation(n)                       # scatter each subdomain's unknowns
+    Kp = sp.csr_matrix(K.toarray()[np.ix_(np.argsort(perm), np.argsort(perm))])
+    offs = np.cumsum([0] + sizes)
+    dofs = [perm[offs[i]:offs[i + 1]] for i in range(len(sizes))]
+    # pad with -1 entries (Dirichlet faces are skipped)
+    elem_dofs = [np.concatenate([d, [-1, -1]]) for d in dofs]
+    subs = precond.asm_setup(Kp, elem_dofs)
+    y = rng.standard_normal(n)
+    z = precond.asm_apply(subs, y)
+    assert np.abs(z - np.linalg.solve(Kp.toarray(), y)).max() < 1e-12 * np.abs(z).max()
