@@ -122,6 +122,39 @@ class Workload:
         out['_mats'] = mats
         return out
 
+    def load_vectors(self, e0=0, e1=None):
+        """(ru, ruh) of elements [e0, e1) as blocks() gives them, without the
+        element matrices: r_u from the quadrature rule directly (for nodal
+        forces, sum_q w|J| phi_i(x_q) f_h(x_q) = (M^e f)_i), r_uhat zero (plus
+        the flux loads of Neumann faces).  For callers that generate the
+        blocks on the device from the vertices."""
+        e1 = self.n_elem if e1 is None else e1
+        elems = np.arange(e0, e1)
+        E = len(elems)
+        ref = self.ref
+        if self.rhs_kind == 'none':
+            ru = np.zeros((E, self.M * self.PE, self.R))
+        else:
+            x, det = _points_and_det(self.mesh, elems, ref.vol_pts)
+            wJ = ref.vol_wts[None, :] * np.abs(det)                         # (E, nq)
+            if self.rhs_kind == 'function':
+                fq = self.f_exact(x)                                         # (E, nq, M)
+                ru = np.einsum('eq,eqa,qi->eai', wJ, fq, ref.phi).reshape(E, -1)[:, :, None]
+                ru = np.repeat(ru, self.R, axis=2)
+            else:
+                cols = []
+                for sd in self.rhs_seeds:
+                    fn = np.random.default_rng(sd).standard_normal((self.n_elem, self.M, self.PE))[elems]
+                    fq = fn @ ref.phi.T                                      # (E, M, nq): f_h at the points
+                    cols.append(((fq * wJ[:, None, :]) @ ref.phi).reshape(E, -1))
+                ru = np.stack(cols, axis=2)
+        ruh = np.zeros((E, self.n_lfe * self.M * self.PF, self.R))
+        if self.neumann_flux is not None and self.face_neumann.any():
+            gN = blk.neumann_face_load(self.mesh, ref, self.perm, elems, self.face_neumann,
+                                       self.neumann_flux, self.M)
+            ruh += gN[:, :, None]
+        return np.ascontiguousarray(ru), ruh
+
     def uhat_dirichlet(self):
         """(NF, M*PF, R) Dirichlet trace values (zero rows on interior faces)."""
         if self.u_exact is None:
@@ -134,6 +167,31 @@ class Workload:
         """Seeded N(0,1) vector over the free trace dofs, e.g. the starting
         vector of the Arnoldi cycle that defines a polynomial preconditioner."""
         return np.random.default_rng(seed).standard_normal(self.n_dof)
+
+
+def _points_and_det(mesh, elems, ref_pts):
+    """Physical points and Jacobian determinants at reference points (the
+    quantities of blocks.geometry that a load vector needs), with the
+    trilinear hexahedron map written as matrix products."""
+    if mesh.kind != 'hex':
+        x, _, det, _ = blk.geometry(mesh, elems, ref_pts)
+        return x, det
+    from .basis import HEX_VERTS
+    s = HEX_VERTS
+    n = ref_pts.shape[0]
+    N = np.prod(1.0 + ref_pts[:, None, :] * s[None, :, :], axis=2) / 8.0          # (n, 8)
+    dN = np.zeros((n, 8, 3))
+    for b in range(3):
+        other = [c for c in range(3) if c != b]
+        dN[:, :, b] = s[None, :, b] * np.prod(1.0 + ref_pts[:, None, other] * s[None, :, other], axis=2) / 8.0
+    X8 = mesh.verts[mesh.elems[elems]]                                             # (E, 8, 3)
+    XT = np.ascontiguousarray(X8.transpose(0, 2, 1))                               # (E, 3, 8)
+    x = (XT @ N.T).transpose(0, 2, 1)                                              # (E, n, 3)
+    J = (XT @ dN.transpose(1, 0, 2).reshape(8, n * 3)).reshape(len(elems), 3, n, 3)   # J[e, a, q, b]
+    det = (J[:, 0, :, 0] * (J[:, 1, :, 1] * J[:, 2, :, 2] - J[:, 1, :, 2] * J[:, 2, :, 1])
+           - J[:, 0, :, 1] * (J[:, 1, :, 0] * J[:, 2, :, 2] - J[:, 1, :, 2] * J[:, 2, :, 0])
+           + J[:, 0, :, 2] * (J[:, 1, :, 0] * J[:, 2, :, 1] - J[:, 1, :, 1] * J[:, 2, :, 0]))
+    return x, det
 
 
 def _sin_product(D):

@@ -109,7 +109,14 @@ typedef struct {
  *               and preconditioner) run on the inner_prec blocks while every
  *               restart recomputes the true residual with the FP64 blocks,
  *               so convergence is judged in FP64 and no inner solves are
- *               nested */
+ *               nested; -2 selects the preconditioner-only mixed mode: FP64
+ *               GMRES on the FP64 operator (matvecs, Krylov basis, Givens,
+ *               residuals in FP64) whose preconditioner M^{-1} runs on
+ *               inner_prec blocks (BJ inverses, ASM inverses) and whose
+ *               polynomial smoother multiplies by K stored in poly_prec
+ *               (FP64, FP32 or BF16), accumulated in FP32 for low-precision
+ *               blocks.  The preconditioner stays a fixed linear operator,
+ *               so left-preconditioned GMRES applies unchanged */
 typedef struct {
   int restart;
   int max_iters;
@@ -334,8 +341,10 @@ hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* la
  * that device current); make that first call before any stream capture.
  * All calls share the one array: calls whose work overlaps on the GPU (other
  * streams, other problems on the same device) race and must be ordered by the
- * caller.  Nothing in the array needs to start at zero.  x, y: device,
- * n_dof x R doubles. */
+ * caller.  Nothing in the array needs to start at zero.  The looked-up
+ * address is kept for the life of the process, so a device reset
+ * (cudaDeviceReset) after the first call on that device is not supported.
+ * x, y: device, n_dof x R doubles. */
 hdg_status hdg_apply_K_noalloc(hdg_problem p, int prec, const double* x, double* y, void* stream);
 
 /* GMRES cycles as CUDA graphs (default on): each cycle of hdg_solve is
@@ -385,7 +394,9 @@ hdg_status hdg_set_kernel_variant(hdg_problem p, int variant);
  *           tiles); the same results, slower at the condensation shapes.  Synchronizes `stream` to read the error word it shares
  * with other calls of this function in the process (do not call it
  * concurrently).  The paper
- * condenses on the CPU; this entry point has no counterpart there. */
+ * condenses on the GPU with batched vendor BLAS (cuBLAS/hipBLAS GEMMs and
+ * inverses, Sec. 4.1); this entry point, the library's own tensor-core
+ * product, has no counterpart there. */
 hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t lda, int64_t sA, const double* B,
                         int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
                         int64_t count, void* stream);

@@ -23,7 +23,15 @@ using namespace hdg;
 #include <mutex>
 namespace hdg {
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// While this thread captures a stream into a graph, its launches are counted
+// here instead of in the process-wide count (captured kernels are counted
+// when the graph runs); other threads' launches are unaffected.
+static thread_local bool t_capturing = false;
+static thread_local long long t_captured = 0;
+void count_launch() {
+  if (t_capturing) ++t_captured;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 }  // namespace hdg
 
 namespace {
@@ -984,7 +992,8 @@ cudaGraphExec_t cycle_graph(hdg_problem p, const hdg_solver_opts& o, int kprec, 
   IterLauncher it{p, &o, kprec, mprec, kpoly, kin.R};
   const bool timing = p->timing;
   p->timing = false;  // no event records inside a graph
-  const long long n0 = hdg::g_launches.load();   // captured kernels are counted when they run
+  hdg::t_capturing = true;      // captured kernels are counted when they run
+  hdg::t_captured = 0;
   cudaGraphNode_t prev = nullptr;
   for (int j = 0; j < o.restart; ++j) {
     // all bytes of the tagged union past the used member must be zero
@@ -1009,7 +1018,7 @@ cudaGraphExec_t cycle_graph(hdg_problem p, const hdg_solver_opts& o, int kprec, 
       cudaStreamEndCapture(p->cap_stream, &dummy);
       cudaGetLastError();
       p->timing = timing;
-      hdg::g_launches.store(n0);
+      hdg::t_capturing = false;
       cudaGraphDestroy(cg.g);
       throw;
     }
@@ -1018,8 +1027,8 @@ cudaGraphExec_t cycle_graph(hdg_problem p, const hdg_solver_opts& o, int kprec, 
     prev = node;
   }
   p->timing = timing;
-  cg.kernels_per_iter = (hdg::g_launches.load() - n0) / std::max(o.restart, 1);
-  hdg::g_launches.store(n0);
+  hdg::t_capturing = false;
+  cg.kernels_per_iter = hdg::t_captured / std::max(o.restart, 1);
   CK(cudaGraphInstantiate(&cg.exec, cg.g, 0));
   p->graphs.push_back(cg);
   *kernels_per_iter = cg.kernels_per_iter;
@@ -1886,12 +1895,18 @@ hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* o, void* stream, hdg_
     p->ev_used = 0;
     hdg_solve_info inf{};
     hdg_status st = HDG_OK;
-    if (o->inner_prec == HDG_FP64 || o->max_outer == -1) {
+    if (o->inner_prec == HDG_FP64 || o->max_outer == -1 || o->max_outer == -2) {
       // plain FP64 GMRES; or (max_outer = -1) one restarted GMRES whose cycles
-      // run on the low-precision blocks and restart from the FP64 residual
-      const int kp = o->inner_prec;
-      const int pp = (kp != HDG_FP64 && o->poly_prec == HDG_BF16) ? HDG_BF16 : kp;
-      GmresResult g = gmres(p, *o, kp, kp, pp, p->d_r, p->d_x, o->rtol, o->max_iters, 1, s);
+      // run on the low-precision blocks and restart from the FP64 residual;
+      // or (max_outer = -2) FP64 GMRES with the FP64 operator whose
+      // preconditioner alone runs on low-precision blocks
+      int kp = o->inner_prec, mp = o->inner_prec;
+      int pp = (kp != HDG_FP64 && o->poly_prec == HDG_BF16) ? HDG_BF16 : kp;
+      if (o->max_outer == -2) {
+        kp = HDG_FP64;
+        pp = o->poly_prec;
+      }
+      GmresResult g = gmres(p, *o, kp, mp, pp, p->d_r, p->d_x, o->rtol, o->max_iters, 1, s);
       inf.iters = g.iters;
       inf.restarts = g.restarts;
       inf.converged = g.converged ? 1 : 0;
@@ -2284,23 +2299,28 @@ hdg_status hdg_gemm_f64(int mode, int M, int N, int K, const double* A, int64_t 
     CK(gemm_err_word(&err));
     CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
     GemmDesc d = gd(M, N, K, A, lda, sA, 0, B, ldb, sB, 0, C, ldc, sC, 0, alpha, beta, (int)count, 1);
+    // stream-ordered scratch, released on every path (also when a check throws)
+    struct AsyncBuf {
+      void* ptr = nullptr;
+      cudaStream_t s;
+      explicit AsyncBuf(cudaStream_t st) : s(st) {}
+      ~AsyncBuf() {
+        if (ptr) cudaFreeAsync(ptr, s);
+      }
+    };
     if (mode == 2) {
       int64_t exw = 0;
       const int64_t need = gemm_planes_bytes(d, &exw);
-      void* planes = nullptr;
-      void* exs = nullptr;
-      CK(cudaMallocAsync(&planes, (size_t)need, s));
-      CK(cudaMallocAsync(&exs, sizeof(uint16_t) * (size_t)exw, s));
-      gemm_ozaki_planes(d, (unsigned char*)planes, need, (uint16_t*)exs, exw, err, s);
-      CK(cudaFreeAsync(planes, s));
-      CK(cudaFreeAsync(exs, s));
+      AsyncBuf planes(s), exs(s);
+      CK(cudaMallocAsync(&planes.ptr, (size_t)need, s));
+      CK(cudaMallocAsync(&exs.ptr, sizeof(uint16_t) * (size_t)exw, s));
+      gemm_ozaki_planes(d, (unsigned char*)planes.ptr, need, (uint16_t*)exs.ptr, exw, err, s);
     } else if (mode == 1 || mode == 3) {
-      void* scratch = nullptr;
+      AsyncBuf scratch(s);
       const int64_t words = gemm_ozaki_scratch(d);
-      CK(cudaMallocAsync(&scratch, sizeof(uint16_t) * words, s));
-      if (mode == 3) gemm_ozaki_persist(d, (uint16_t*)scratch, words, err, s);
-      else gemm_ozaki(d, (uint16_t*)scratch, err, s);
-      CK(cudaFreeAsync(scratch, s));
+      CK(cudaMallocAsync(&scratch.ptr, sizeof(uint16_t) * words, s));
+      if (mode == 3) gemm_ozaki_persist(d, (uint16_t*)scratch.ptr, words, err, s);
+      else gemm_ozaki(d, (uint16_t*)scratch.ptr, err, s);
     } else {
       gemm_f64(d, s);
     }

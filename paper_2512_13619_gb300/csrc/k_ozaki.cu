@@ -27,17 +27,17 @@
 // FP64 rounding of a dot product; the result is rounded once to FP64.
 //
 // One CTA computes a 128 x NT output tile (NT <= 64) of one batch item with
-// nine warps.  K is staged 32 columns at a time through two shared-memory
-// stages.  Warps 0-7 load the FP64 operands (the next stage's loads are in
-// flight while the current stage is split), split them into digits and
-// write the BF16 digit matrices in the UMMA no-swizzle K-major layout (8 x
-// 16-byte core matrices), then arrive on the stage's `full` mbarrier.  Warp 8
-// allocates the TMEM accumulators (8 NT columns) and one of its lanes issues
-// the stage's 72 MMAs (M = 128, N = NT, K = 16) and commits them to the
-// stage's `empty` mbarrier, so splitting and MMAs overlap.  After the last
-// stage warps 0-7 read the accumulators and form the FP64 result with
-// integer arithmetic (one rounding), so the epilogue spends at most one FP64
-// addition per output (for C += alpha A B).
+// seventeen warps (544 threads).  K is staged 32 columns at a time through
+// two shared-memory stages.  Warps 0-15 load the FP64 operands (the next
+// stage's loads are in flight while the current stage is split), split them
+// into digits and write the BF16 digit matrices in the UMMA no-swizzle
+// K-major layout (8 x 16-byte core matrices), then arrive on the stage's
+// `full` mbarrier.  Warp 16 allocates the TMEM accumulators (8 NT columns)
+// and one of its lanes issues the stage's 72 MMAs (M = 128, N = NT, K = 16)
+// and commits them to the stage's `empty` mbarrier, so splitting and MMAs
+// overlap.  After the last stage warps 0-15 read the accumulators and form
+// the FP64 result with integer arithmetic (one rounding), so the epilogue
+// spends at most one FP64 addition per output (for C += alpha A B).
 #include <algorithm>
 
 #include "hdg_common.cuh"

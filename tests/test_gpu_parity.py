@@ -238,18 +238,20 @@ def test_chebyshev_setup_and_apply():
 
 
 @pytest.mark.parametrize('pc,poly,deg', [('asm', 'chebyshev', 4), ('bj', 'gmres', 6), ('bj', None, 0)])
-@pytest.mark.parametrize('mode', ['refinement', 'restarted'])
+@pytest.mark.parametrize('mode', ['refinement', 'restarted', 'precond'])
 def test_mixed_precision_reaches_1e8(pc, poly, deg, mode):
     """FP32 blocks with FP64 refinement (inner solves to 1e-4), or with FP64
-    true residuals at the restarts of one GMRES (max_outer = -1), reach a
-    true FP64 relative residual of 1e-8; the error against the oracle's direct
-    solution is <= cond * 1e-8."""
+    true residuals at the restarts of one GMRES (max_outer = -1), or FP64
+    GMRES whose preconditioner alone is stored in FP32 and its polynomial's K
+    in BF16 (max_outer = -2), reach a true FP64 relative residual of 1e-8;
+    the error against the oracle's direct solution is <= cond * 1e-8."""
     need_gpu()
     from paper_2512_13619_gb300 import driver
     w = W.hex_elasticity(n=3, k=1, R=8)
     s = OracleSystem(w)
+    mo = {'refinement': 20, 'restarted': -1, 'precond': -2}[mode]
     o = driver.opts(restart=30, rtol=1e-8, pc=pc, poly=poly, degree=deg, inner='fp32', inner_rtol=1e-4,
-                    max_iters=3000, max_outer=20 if mode == 'refinement' else -1)
+                    max_iters=3000, max_outer=mo, poly_prec='bf16' if mode == 'precond' else 'fp32')
     p = _problem(w)
     p.assemble(o)
     p.setup_precond(o, w.random_vector(31) if poly else None)

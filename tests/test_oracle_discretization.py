@@ -315,3 +315,19 @@ def test_beam_preconditioner_ordering():
         its[name + '-PP'] = it['iters']
     assert its['ASM-PP'] < its['BJ-PP'] < its['ASM'] < its['BJ']
     assert its['BJ-PP'] * 5 < its['BJ'] and its['ASM-PP'] * 5 < its['ASM']
+
+
+@pytest.mark.parametrize('name', ['elasticity_perturbed', 'poisson', 'beam', 'tets'])
+def test_load_vectors_equal_block_load_vectors(name):
+    """The load vectors computed without the element matrices (for the
+    device-generated blocks) equal those of the full block generation."""
+    w = {'elasticity_perturbed': lambda: W.hex_elasticity(n=3, k=2, R=3),
+         'poisson': lambda: W.hex_poisson(n=3, k=2),
+         'beam': lambda: W.hex_beam(n=2, k=1),
+         'tets': lambda: W.tet_poisson(n=2, k=2)}[name]()
+    full = w.blocks()
+    ru, ruh = w.load_vectors()
+    assert np.abs(ru - full['ru']).max() <= 1e-14 * max(np.abs(full['ru']).max(), 1e-300)
+    assert np.array_equal(ruh, full['ruh'])
+    part = w.load_vectors(5, 9)
+    assert np.array_equal(part[0], ru[5:9])
