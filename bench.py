@@ -1,22 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the HDG trace-solver hot path (one GB300 per rank).
 
-Workload (default): HDG Poisson on the unit cube, 16^3 hexahedra, Q3 tensor
-basis (16 trace dofs per face, 96 x 96 condensed element blocks), manufactured
-sin-product solution, 184,320 trace unknowns, one right-hand side,
-block-Jacobi GMRES(50).
+Workload (default): HDG linear elasticity (E = 1, nu = 0.3) on a 32^3 hex mesh
+whose interior vertices are moved by up to 0.2h (seed 3), Q2 tensor basis
+(27 trace dofs per face, 162 x 162 condensed element blocks), 2,571,264 trace
+unknowns, 8 right-hand sides from seeded N(0,1) nodal body forces; GMRES(50)
+with block-Jacobi + degree-4 Chebyshev preconditioning to a true FP64
+relative residual of 1e-8 for every right-hand side.
 
-One step = one pass of the whole hot path over the element blocks already
-resident in HBM: batched static condensation -> face-based assembly ->
-block-Jacobi factorization -> GMRES to a true FP64 relative residual of 1e-8
--> element recovery.  `value` is the step with the plain FP64 solve (the
-workload's configured path); the same step with the mixed solve (FP32 blocks
-+ FP64 iterative refinement) and the FP64 step to 1e-10 are timed beside it.
+One step = one pass of the whole hot path: the element blocks generated on
+the device from the vertices and condensed (hdg_condense_hex), face-based
+assembly, preconditioner set-up (block-Jacobi inverses, the Arnoldi cycle of
+the Chebyshev bounds), GMRES to 1e-8, element recovery.  `value` is the step
+with the mixed-precision solve (FP32 or BF16 blocks, FP64 Krylov basis and
+residuals); the same step with the plain FP64 solve, the additive-Schwarz
+variants, the 16^3 Q3 Poisson step and the serving stream are measured beside
+it.
 
 Prints ONE JSON line (rank 0).  Several ranks run independent replicas (the
 path is not sharded); timings are the max over ranks.
-`--impl reference` times the FP64 CPU oracle (test infrastructure) on the
-same workload.
+`--impl reference` times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload.
 """
 import argparse
 import json
@@ -31,6 +35,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = 'time to 1e-8 rel. residual (mixed vs FP64); block-matvec GB/s; p99 latency'
 WORKLOAD = 'HDG Poisson, unit cube, 16^3 hex, Q3 (16 dofs/face, 96x96 element blocks), sin-product MMS, 1 RHS'
+WORKLOAD3 = ('HDG linear elasticity (E=1, nu=0.3), 32^3 hex with interior vertices perturbed by up to 0.2h '
+             '(seed 3), Q2 (27 dofs/face, 162x162 element blocks), 8 RHS from N(0,1) nodal body forces '
+             '(seeds 300-307), BJ + Chebyshev(4) GMRES(50) to 1e-8')
+ORACLE_SAMPLE_N = 6      # the oracle's bounded sample of the elasticity workload: 6^3 elements
 
 
 def parse():
@@ -54,9 +62,18 @@ def parse():
     ap.add_argument('--serving-budget-gb', type=float, default=160.0)
     ap.add_argument('--mesh-n', type=int, default=0, help='mesh size of --workload (0: 40 / 32)')
     ap.add_argument('--max-iters', type=int, default=3000, help='GMRES iteration cap of --workload solves')
-    ap.add_argument('--workload', choices=['poisson16', 'elasticity32', 'cdr40', 'beam', 'tets', 'burgers'],
-                    default='poisson16',
-                    help='poisson16: the step above; elasticity32 / cdr40: solver and kernel measurements '
+    ap.add_argument('--mixed-mode', choices=['restarted', 'refinement', 'precond'], default='restarted',
+                    help='mixed-precision mode of the value leg: restarted (FP32 cycles, FP64 residual at each '
+                         'restart), refinement (FP64 refinement around FP32 inner solves) or precond (FP64 '
+                         'operator and Krylov, preconditioner in FP32)')
+    ap.add_argument('--poly-prec', choices=['fp32', 'bf16'], default='fp32',
+                    help='storage of K inside the Chebyshev polynomial of the mixed legs')
+    ap.add_argument('--no-asm', action='store_true', help='skip the additive-Schwarz legs of the default step')
+    ap.add_argument('--no-config2', action='store_true', help='skip the 16^3 Q3 Poisson leg of the default step')
+    ap.add_argument('--workload', choices=['step3', 'poisson16', 'elasticity32', 'cdr40', 'beam', 'tets', 'burgers'],
+                    default='step3',
+                    help='step3: the step above (default); poisson16: the same step on the 16^3 Q3 Poisson '
+                         'workload with resident element blocks; elasticity32 / cdr40: solver and kernel measurements '
                          'on the 32^3 perturbed Q2 elasticity (8 RHS) and 40^3 Q2 5-component CDR (4 RHS) '
                          'problems; beam: the cantilever beam runs of Sec. 6.2 (BJ, BJ-PP(10), ASM, '
                          'ASM-PP(10), GMRES(50) to 1e-6) over k at N_E = 320 and over N_E at k = 3; '
@@ -70,11 +87,12 @@ def parse():
                          'Newton with BJ, BJ-PP(10), ASM, ASM-PP(10) GMRES(50) to 1e-6)')
     ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
                     help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
-    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64', 'generate'],
+    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64', 'generate', 'step3'],
                     default=None,
                     help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
                          'one FP32 hdg_apply_K call (matvec), one solve (solve-*) or two hdg_hex_blocks calls '
-                         '(generate: the element blocks generated on the device), for profilers; no JSON')
+                         '(generate: the element blocks generated on the device), or two mixed steps of the '
+                         'default workload (step3, --mesh-n sets its size), for profilers; no JSON')
     return ap.parse_args()
 
 
@@ -441,6 +459,375 @@ def run_ours(args, ws, rank, local):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def nonzero_blocks(w):
+    """Real nonzero b x b blocks of K: sum over elements of (free faces)^2
+    minus the free faces (each diagonal block is shared by two elements)."""
+    fd = w.face_dirichlet
+    nfree_e = (fd[w.mesh.elem_face] == 0).sum(axis=1)
+    return int((nfree_e ** 2).sum() - w.n_free)
+
+
+def run_step3(args, ws, rank, local):
+    """The default step on the 32^3 perturbed Q2 elasticity workload (8 RHS):
+    device-generated blocks, condensation, assembly, BJ + Chebyshev(4) set-up,
+    GMRES(50) to 1e-8 (mixed and FP64), recovery."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=dev)
+
+    t_in = time.perf_counter()
+    n = args.mesh_n or 32
+    w = W.hex_elasticity(n=n, k=2, R=8)
+    verts, perm, nquad = driver.hex_geometry_inputs(w)
+    ru, ruh = w.load_vectors()
+    uD = np.zeros((w.n_face, w.M * w.PF, w.R))
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in
+            (('verts', verts), ('perm', perm), ('ru', ru), ('ruh', ruh), ('uD', uD))}
+    dvc = {k: v.to(dev) for k, v in host.items()}
+    phys, _keep = L.physics(w.phys.Cq, w.phys.Cu, w.phys.Rr, w.phys.tau)
+    v0 = torch.from_numpy(w.random_vector(31)).to(dev)      # start vector of the Chebyshev bounds' Arnoldi cycle
+    t_in = time.perf_counter() - t_in
+    R = w.R
+    p = driver.Problem.from_workload(w, local)
+    if args.no_graphs:
+        L.hdg_set_graphs(p.h, 0)
+    u_dev = torch.empty((w.n_elem, w.M * w.PE, R), dtype=torch.float64, device=dev)
+    q_dev = torch.empty((w.n_elem, w.M * w.D * w.PE, R), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    in_bytes = sum(v.numel() * v.element_size() for v in host.values())
+    mo = {'restarted': -1, 'refinement': 20, 'precond': -2}
+
+    def o_of(pc, poly, deg, inner, mode='restarted', pprec='fp32'):
+        return driver.opts(restart=50, rtol=1e-8, pc=pc, poly=poly, degree=deg, inner=inner,
+                           poly_prec=pprec if inner != 'fp64' else 'fp64', inner_rtol=1e-4, max_iters=3000,
+                           max_outer=mo[mode] if inner != 'fp64' else 20)
+    legs = {
+        'mixed': ('BJ + Chebyshev(4), %s mixed, FP32 blocks, %s polynomial' % (args.mixed_mode, args.poly_prec.upper()),
+                  o_of('bj', 'chebyshev', 4, 'fp32', args.mixed_mode, args.poly_prec)),
+        'fp64': ('BJ + Chebyshev(4), plain FP64', o_of('bj', 'chebyshev', 4, 'fp64')),
+    }
+    if not args.no_asm:
+        legs['asm_mixed'] = ('ASM (one-element patches), restarted mixed, FP32 blocks',
+                             o_of('asm', None, 0, 'fp32', 'restarted'))
+        legs['asm_fp64'] = ('ASM (one-element patches), plain FP64', o_of('asm', None, 0, 'fp64'))
+    infos = {}
+
+    def step(o, tag, src, on_device, phases=None, outs=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if phases is not None else None
+        if ev: ev[0].record()
+        driver.check(L.hdg_condense_hex(p.h, 0, w.n_elem, nquad, src['verts'], src['perm'], phys, src['ru'],
+                                        src['ruh'], on_device, st), 'condense_hex')
+        driver.check(L.hdg_set_dirichlet(p.h, src['uD'], on_device, st), 'dirichlet')
+        driver.check(L.hdg_assemble(p.h, o, st), 'assemble')
+        driver.check(L.hdg_setup_precond(p.h, o, v0, st), 'setup')
+        if ev: ev[1].record()
+        info = L.hdg_solve_info()
+        s_ = L.hdg_solve(p.h, o, st, info)
+        if s_ != 0:
+            raise RuntimeError('%s solve: %s rel=%g' % (tag, L.hdg_status_str(s_), info.rel_resid))
+        if ev: ev[2].record()
+        if outs is None:
+            driver.check(L.hdg_recover(p.h, u_dev, q_dev, 1, st), 'recover')
+        else:
+            driver.check(L.hdg_get_trace(p.h, outs[0], 0, st), 'trace')
+            driver.check(L.hdg_recover(p.h, outs[1], outs[2], 0, st), 'recover')
+        if ev:
+            ev[3].record()
+            phases.append(ev)
+        infos[tag] = (info.iters, info.outer, info.rel_resid)
+
+    def timed(o, tag, K, W_):
+        for _ in range(W_):
+            step(o, tag, dvc, 1)
+        torch.cuda.synchronize(dev)
+        if dist: dist.barrier()
+        torch.cuda.synchronize(dev)
+        phases = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = L.hdg_launch_count()
+        e0.record()
+        for _ in range(K):
+            step(o, tag, dvc, 1, phases)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        n1 = L.hdg_launch_count()
+        ms = e0.elapsed_time(e1) / K
+        ph = {'setup': 0.0, 'solve': 0.0, 'recover': 0.0}
+        for ev in phases:
+            ph['setup'] += ev[0].elapsed_time(ev[1]) / K
+            ph['solve'] += ev[1].elapsed_time(ev[2]) / K
+            ph['recover'] += ev[2].elapsed_time(ev[3]) / K
+        ms = max_over_ranks(ms, dist, dev)
+        print('step3 %s: %.1f ms per step (%s), iterations %s' % (tag, ms, {k: round(v, 1) for k, v in ph.items()},
+                                                                    infos[tag]), file=sys.stderr, flush=True)
+        return ms, ph, (n1 - n0) / K
+
+    # set-up: one untimed step of each preconditioner, then the autotuner
+    # picks the block-row launch configurations (K at every stored precision,
+    # BJ and ASM; cached per block shape)
+    tuning = {}
+    for tag in [t for t in ('asm_mixed', 'mixed') if t in legs]:
+        o = legs[tag][1]
+        step(o, tag, dvc, 1)
+        if tag == 'mixed':
+            driver.check(L.hdg_assemble(p.h, o_of('bj', None, 0, 'fp32', 'restarted', 'bf16'), st), 'assemble')
+            driver.check(L.hdg_setup_precond(p.h, o, v0, st), 'setup')
+        driver.check(L.hdg_autotune(p.h, 10, 0, st), 'autotune')
+    for op, opn in ((0, 'K'), (1, 'bj'), (2, 'asm')):
+        for prec, pn in ((0, 'fp64'), (1, 'fp32'), (2, 'bf16')):
+            _, cfg, us, us0 = L.hdg_get_tuning(p.h, op, prec)
+            if us > 0:
+                tuning['%s_%s' % (opn, pn)] = {'cfg': list(cfg), 'us_tuned': round(us, 1), 'us_default': round(us0, 1)}
+
+    clk = Clocks(local)
+    clk.start()
+    res = {}
+    ms_val, ph_val, launches = timed(legs['mixed'][1], 'mixed', args.steps, args.warmup)
+    res['mixed'] = (ms_val, ph_val, args.steps)
+    k_side = max(1, min(args.steps, 2))
+    for tag in [t for t in legs if t != 'mixed']:
+        ks = k_side if tag == 'fp64' else 1
+        ms, ph, _ = timed(legs[tag][1], tag, ks, 1)
+        res[tag] = (ms, ph, ks)
+    clocks = clk.stop()
+
+    # block-row kernels alone (R = 8): FP64, FP32 and BF16 blocks of K, the
+    # library's CUDA events around each launch, an L2 flush (256 MiB write)
+    # between launches, after 2 warm-up launches
+    o16 = o_of('bj', None, 0, 'fp32', 'restarted', 'bf16')
+    driver.check(L.hdg_assemble(p.h, o16, st), 'assemble')       # builds the BF16 copy of K too
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    xv = torch.randn(p.n_dof * R, dtype=torch.float64, device=dev)
+    yv = torch.empty_like(xv)
+    pk = peaks()
+    nnzb = nonzero_blocks(w)
+    b = w.M * w.PF
+    mv = {}
+    for prec, name, sz, ld in ((0, 'fp64', 8, b), (1, 'fp32', 4, (b + 3) // 4 * 4), (2, 'bf16', 2, (b + 7) // 8 * 8)):
+        for _ in range(2):
+            driver.check(L.hdg_apply_K(p.h, prec, xv, yv, st), 'apply_K')
+        torch.cuda.synchronize(dev)
+        nrep = 10
+        L.hdg_set_timing(p.h, 1)
+        for _ in range(nrep):
+            flush.fill_(1.0)
+            driver.check(L.hdg_apply_K(p.h, prec, xv, yv, st), 'apply_K')
+        torch.cuda.synchronize(dev)
+        _, tms, nl = L.hdg_get_timing(p.h, prec)
+        L.hdg_set_timing(p.h, 0)
+        avg = tms / max(nl, 1)
+        # algorithmic bytes: the real blocks (stored columns padded to 16 bytes
+        # in FP32/BF16) + x read once + y written (FP64 x for FP64 blocks, its
+        # FP32 copy otherwise)
+        by = nnzb * b * ld * sz + p.n_dof * R * (16 if prec == 0 else 12)
+        mv[name] = {'avg_ms': round(avg, 4), 'launches': int(nl), 'bytes_per_launch': int(by),
+                    'gbs': round(by / avg / 1e6, 1), 'frac_hbm': round(by / avg / 1e6 / pk['hbm_gbs'], 3),
+                    'tflops': round(2 * nnzb * b * b * R / avg / 1e9, 3),
+                    'timing': 'CUDA events around each block-row launch, L2 flushed between launches'}
+
+    # the dominant kernel inside the step: one more mixed step with the
+    # library's per-launch events (launch by launch, no graphs), the FP32
+    # block-row launches of K averaged
+    driver.check(L.hdg_set_timing(p.h, 1), 'timing')
+    step(legs['mixed'][1], 'mixed_timed', dvc, 1)
+    torch.cuda.synchronize(dev)
+    kp = 2 if args.poly_prec == 'bf16' else 1
+    _, t32, n32 = L.hdg_get_timing(p.h, 1)
+    _, t16, n16 = L.hdg_get_timing(p.h, 2)
+    L.hdg_set_timing(p.h, 0)
+    by32 = nnzb * b * ((b + 3) // 4 * 4) * 4 + p.n_dof * R * 12
+    by16 = nnzb * b * ((b + 7) // 8 * 8) * 2 + p.n_dof * R * 12
+    tot_by = by32 * n32 + by16 * n16
+    tot_ms = t32 + t16
+    achieved = tot_by / tot_ms / 1e6 if tot_ms > 0 else 0.0
+    roof = {'kernel': 'blockrow_vec_kernel (face-block matvec y = K x, R = 8, FP32%s blocks, FP32 accumulation)'
+                      % (' and BF16' if n16 else ''),
+            'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': pk['hbm_gbs'], 'unit': 'GB/s',
+            'frac': round(achieved / pk['hbm_gbs'], 4), 'traffic': None,
+            'bytes_per_launch': {'fp32': int(by32), 'bf16': int(by16)},
+            'launches_in_step': int(n32 + n16), 'ms_in_step': round(tot_ms, 3),
+            'timing': 'CUDA events around every block-row launch of K in one mixed step run launch by launch',
+            'peak_source': 'MEASURED_PEAKS.json hbm_gbs' if not pk.get('_fallback') else 'fallback 6.8 TB/s'}
+
+    # end to end through the C ABI from pinned host buffers: vertices, face
+    # permutations, load vectors and Dirichlet values in; trace, u and q out
+    e2e = None
+    if not args.no_e2e:
+        uh_host = torch.empty((w.n_face, w.M * w.PF, R), dtype=torch.float64).pin_memory()
+        u_host = torch.empty((w.n_elem, w.M * w.PE, R), dtype=torch.float64).pin_memory()
+        q_host = torch.empty((w.n_elem, w.M * w.D * w.PE, R), dtype=torch.float64).pin_memory()
+        k_e2e = max(1, min(args.steps, 5))
+        for _ in range(1):
+            step(legs['mixed'][1], 'e2e', host, 0, outs=(uh_host, u_host, q_host))
+        torch.cuda.synchronize(dev)
+        if dist: dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            step(legs['mixed'][1], 'e2e', host, 0, outs=(uh_host, u_host, q_host))
+        torch.cuda.synchronize(dev)
+        e_ms = (time.perf_counter() - t0) * 1e3 / k_e2e
+        e_ms = max_over_ranks(e_ms, dist, dev)
+        out_bytes = (uh_host.numel() + u_host.numel() + q_host.numel()) * 8
+        e2e = {'value': round(e_ms, 3), 'unit': 'ms', 'h2d_bytes_per_step': int(in_bytes),
+               'd2h_bytes_per_step': int(out_bytes), 'steps': k_e2e,
+               'path': 'pinned host inputs (vertices, face permutations, load vectors, Dirichlet values) -> '
+                       'hdg_condense_hex ... hdg_solve -> hdg_get_trace + hdg_recover into pinned host buffers'}
+    p.close()
+    del dvc
+    torch.cuda.empty_cache()
+
+    ms_mixed, ph_mixed, _ = res['mixed']
+    ms_fp64, ph_fp64, k_fp64 = res['fp64']
+    legs_out = {}
+    for tag, (desc, _) in legs.items():
+        ms, ph, ks = res[tag]
+        it = infos.get(tag, (0, 0, 0.0))
+        legs_out[tag] = {'solver': desc, 'ms_per_step': round(ms, 2), 'steps': ks,
+                         'phases_ms': {k: round(v, 2) for k, v in ph.items()},
+                         'gmres': it[0], 'refinement': it[1], 'rel_resid': it[2]}
+    out = {
+        'metric': METRIC, 'value': round(ms_mixed, 3), 'unit': 'ms', 'n_gpus': ws, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': round(ms_mixed, 3), 'higher_is_better': False, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f32 blocks / f64 Krylov', 'data': 'synthetic',
+        'config': {'workload': WORKLOAD3 if n == 32 else WORKLOAD3.replace('32^3', '%d^3' % n),
+                   'n_elem': w.n_elem, 'n_dof': p.n_dof, 'rhs': R, 'precond': 'block-Jacobi + Chebyshev(4)',
+                   'restart': 50, 'rtol': 1e-8, 'solve': legs['mixed'][0],
+                   'l2': 'inputs larger than L2 (FP32 K alone %.2f GB)' % (nnzb * b * ((b + 3) // 4 * 4) * 4 / 1e9),
+                   'parallelism': 'replicas' if ws > 1 else 'single GPU'},
+        'fp64_ms_per_step': round(ms_fp64, 3),
+        'speedup_mixed_vs_fp64': round(ms_fp64 / ms_mixed, 3),
+        'time_to_1e-8_solve_ms': {'mixed': round(ph_mixed['solve'], 2), 'fp64': round(ph_fp64['solve'], 2)},
+        'speedup_mixed_vs_fp64_solve': round(ph_fp64['solve'] / ph_mixed['solve'], 3),
+        'legs': legs_out,
+        'block_matvec': mv,
+        'autotuned': tuning,
+        'roofline': roof,
+        'gpu_launches': int(round(launches)),
+        'clocks': clocks,
+        'input_generation_s': round(t_in, 2),
+    }
+    if e2e:
+        out['e2e'] = e2e
+    if not args.no_config2:
+        out['config2'] = config2_leg(args, local)
+    if args.serving_requests > 0:
+        out['serving'] = serving_leg(args, local)
+    if rank == 0 and not args.no_cpu:
+        out['cpu_baseline'] = cpu_baseline3(args)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def config2_leg(args, local):
+    """The 16^3 Q3 Poisson step (sin-product MMS, 1 RHS, BJ-GMRES(50) to
+    1e-8, element blocks resident in HBM) with the plain FP64 solve and the
+    preconditioner-only mixed solve (FP64 operator and Krylov, FP32 BJ
+    inverses), min(steps, 5) timed steps each after 2 warm-up steps."""
+    import numpy as np
+    import torch
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    dev = torch.device('cuda', local)
+    w = W.hex_poisson(n=16, k=3)
+    blk = w.blocks()
+    names = driver.BLOCK_NAMES
+    dblk = {k: torch.from_numpy(np.ascontiguousarray(blk[k])).to(dev) for k in names}
+    uD = torch.from_numpy(w.uhat_dirichlet()).to(dev)
+    p = driver.Problem.from_workload(w, local)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    u_dev = torch.empty((w.n_elem, w.M * w.PE, 1), dtype=torch.float64, device=dev)
+    q_dev = torch.empty((w.n_elem, w.M * w.D * w.PE, 1), dtype=torch.float64, device=dev)
+    opts = {'fp64': driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp64', max_iters=5000),
+            'mixed_precond': driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp32', max_iters=5000, max_outer=-2),
+            'mixed_restarted': driver.opts(restart=50, rtol=1e-8, pc='bj', inner='fp32', max_iters=5000,
+                                           max_outer=-1)}
+    out = {'workload': WORKLOAD, 'n_elem': w.n_elem, 'n_dof': p.n_dof}
+    K = max(1, min(args.steps, 5))
+    for tag, o in opts.items():
+        def step():
+            driver.check(L.hdg_condense(p.h, 0, w.n_elem, *[dblk[k] for k in names], 1, st), 'condense')
+            driver.check(L.hdg_set_dirichlet(p.h, uD, 1, st), 'dirichlet')
+            driver.check(L.hdg_assemble(p.h, o, st), 'assemble')
+            driver.check(L.hdg_setup_precond(p.h, o, None, st), 'setup')
+            info = L.hdg_solve_info()
+            s_ = L.hdg_solve(p.h, o, st, info)
+            if s_ != 0:
+                raise RuntimeError('config2 %s: %s' % (tag, L.hdg_status_str(s_)))
+            driver.check(L.hdg_recover(p.h, u_dev, q_dev, 1, st), 'recover')
+            return info
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            info = step()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        out[tag] = {'ms_per_step': round(e0.elapsed_time(e1) / K, 3), 'gmres': info.iters,
+                    'rel_resid': info.rel_resid, 'steps': K}
+    out['speedup_mixed_precond_vs_fp64'] = round(out['fp64']['ms_per_step'] / out['mixed_precond']['ms_per_step'], 3)
+    p.close()
+    del dblk
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_step3(w):
+    """One step of the elasticity workload with the FP64 oracle: element
+    blocks, condensation, assembly, block-Jacobi, Chebyshev(4) bounds from an
+    Arnoldi(10) cycle on M^{-1} K, GMRES(50) to 1e-8 for every right-hand
+    side, recovery.  Returns (ms, max iterations)."""
+    import numpy as np
+    from oracle.condense import condense_local
+    from oracle.assemble import assemble, element_traces, recover
+    from oracle import krylov, precond
+    t0 = time.perf_counter()
+    blk = w.blocks()
+    uD = w.uhat_dirichlet()
+    Kb, rb, rec = condense_local(blk, w.M, w.n_lfe)
+    K, r = assemble(Kb, rb, w.mesh.elem_face, w.face_dirichlet, uD, w.M, w.PF)
+    Binv = precond.bj_setup(K, w.M * w.PF)
+    M = lambda v: precond.bj_apply(Binv, v)
+    A = lambda v: M(K @ v)
+    lo, hi = precond.chebyshev_bounds(A, w.random_vector(31), 10)
+    Pinv = lambda v: precond.chebyshev_apply(A, lo, hi, 4, M(v))
+    X = np.zeros_like(r)
+    its = 0
+    for c in range(w.R):
+        X[:, c], info = krylov.gmres(lambda v: K @ v, Pinv, r[:, c], m=50, rtol=1e-8)
+        its = max(its, info['iters'])
+    ue = element_traces(X, w.mesh.elem_face, w.face_dirichlet, uD, w.M, w.PF)
+    recover(rec, ue, w.M, w.n_lfe)
+    return (time.perf_counter() - t0) * 1e3, its
+
+
+def cpu_baseline3(args):
+    from hdg_inputs import workloads as W
+    w = W.hex_elasticity(n=ORACLE_SAMPLE_N, k=2, R=8)
+    ms, it = oracle_step3(w)
+    full = 32 ** 3
+    return {'value': round(ms, 1), 'unit': 'ms', 'cores': cpu_cores(), 'kind': 'oracle',
+            'sample': 'one full step of the same workload family on a %d^3 instance (%d of the %d elements, '
+                      'seeded the same way): blocks, condensation, assembly, BJ + Chebyshev(4) set-up, GMRES(50) '
+                      'to 1e-8 for all 8 RHS (%d iterations at most), recovery, FP64 on the host cores'
+                      % (ORACLE_SAMPLE_N, w.n_elem, full, it),
+            'per_element_ms': round(ms / w.n_elem, 3),
+            'linear_extrapolation_to_32^3_ms': round(ms / w.n_elem * full, 1)}
 
 
 def serving_leg(args, local):
@@ -847,6 +1234,8 @@ def cpu_baseline(args, w, blk):
 def run_reference(args, ws, rank):
     if rank != 0:
         return None
+    if args.workload == 'step3':
+        return run_reference3(args, ws)
     from hdg_inputs import workloads as W
     w = W.hex_poisson(n=args.n, k=args.k)
     blk = w.blocks()
@@ -868,6 +1257,32 @@ def run_reference(args, ws, rank):
             'e2e': {'value': round(ms, 1), 'unit': 'ms', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
 
 
+def run_reference3(args, ws):
+    """The oracle arm of the default step: each step is the FP64 oracle's
+    full step on the bounded 6^3 sample of the elasticity workload."""
+    from hdg_inputs import workloads as W
+    w = W.hex_elasticity(n=ORACLE_SAMPLE_N, k=2, R=8)
+    for _ in range(args.warmup):
+        oracle_step3(w)
+    ts, it = [], 0
+    for _ in range(args.steps):
+        ms, it = oracle_step3(w)
+        ts.append(ms)
+    ms = sum(ts) / len(ts)
+    cores = cpu_cores()
+    sample = ('each step: the FP64 oracle (blocks, condensation, assembly, BJ + Chebyshev(4), GMRES(50) to 1e-8 for '
+              '8 RHS, recovery) on a %d^3 instance of the workload (%d elements, %d iterations at most)'
+              % (ORACLE_SAMPLE_N, w.n_elem, it))
+    return {'impl': 'reference', 'metric': METRIC, 'value': round(ms, 1), 'unit': 'ms', 'n_gpus': ws,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': round(ms, 1), 'higher_is_better': False,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': WORKLOAD3, 'n_elem': 32 ** 3, 'rhs': 8, 'precond': 'block-Jacobi + Chebyshev(4)',
+                       'restart': 50, 'rtol': 1e-8, 'solve': 'FP64 oracle (CPU), bounded sample',
+                       'sample_n_elem': w.n_elem, 'parallelism': 'rank 0 only'},
+            'cpu_baseline': {'value': round(ms, 1), 'unit': 'ms', 'cores': cores, 'kind': 'oracle', 'sample': sample},
+            'e2e': {'value': round(ms, 1), 'unit': 'ms', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+
+
 def run_profile(args):
     """Minimal set-up for a profiler: the workload on cuda:0, then the
     kernels under study once."""
@@ -877,6 +1292,33 @@ def run_profile(args):
     __graft_entry__.build()
     from hdg_inputs import workloads as W
     from paper_2512_13619_gb300 import driver, _lib as L
+    if args.profile == 'step3':
+        w = W.hex_elasticity(n=args.mesh_n or 32, k=2, R=8)
+        verts, perm, nquad = driver.hex_geometry_inputs(w)
+        ru, ruh = w.load_vectors()
+        d = {k: torch.from_numpy(v).cuda() for k, v in (('verts', verts), ('perm', perm), ('ru', ru), ('ruh', ruh))}
+        phys, _keep = L.physics(w.phys.Cq, w.phys.Cu, w.phys.Rr, w.phys.tau)
+        v0 = w.random_vector(31)
+        mo = {'restarted': -1, 'refinement': 20, 'precond': -2}[args.mixed_mode]
+        o = driver.opts(restart=50, rtol=1e-8, pc='bj', poly='chebyshev', degree=4, inner='fp32',
+                        poly_prec=args.poly_prec, inner_rtol=1e-4, max_iters=3000, max_outer=mo)
+        p = driver.Problem.from_workload(w, 0)
+        for it in range(2):
+            driver.check(L.hdg_condense_hex(p.h, 0, w.n_elem, nquad, d['verts'], d['perm'], phys, d['ru'], d['ruh'],
+                                            1), 'condense_hex')
+            p.set_dirichlet(np.zeros((w.n_face, w.M * w.PF, w.R)))
+            p.assemble(o)
+            p.setup_precond(o, v0)
+            if it == 0:
+                driver.check(L.hdg_autotune(p.h, 10, 0, None), 'autotune')
+            st, info = p.solve(o)
+            driver.check(st, 'solve')
+            p.recover()
+        torch.cuda.synchronize()
+        print('iterations', info.iters)
+        p.close()
+        print('profile run done')
+        return
     w = W.hex_poisson(n=args.n, k=args.k)
     p = driver.Problem.from_workload(w, 0)
     if args.profile == 'generate':
@@ -934,6 +1376,8 @@ def main():
         out = run_tets(args, local)
     elif args.workload == 'burgers':
         out = run_burgers(args, local)
+    elif args.workload == 'step3':
+        out = run_step3(args, ws, rank, local)
     elif args.workload != 'poisson16':
         out = run_config(args, local)
     else:
