@@ -431,8 +431,13 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
  * 16-byte loads of 4 (FP32) or 8 (BF16) rows per thread with the slots of a
  * row split over sp adjacent lanes (sp in {1,2,4,8}), 4 = FP64 rows with the
  * slots split over sp adjacent lanes (sp in {2,4,8}) and a shuffle
- * reduction; cps = CTAs per SM of the grid-stride launch (0 = heuristic).  Every configuration computes the same sums; they differ
- * in summation order only. */
+ * reduction, 5 = FP32/BF16 blocks of whole face rows streamed by one bulk
+ * copy each (evict-first in L2) into a shared-memory ring of one persistent
+ * CTA per SM, 16-byte vectors of 4 (FP32) or 8 (BF16) rows per thread, the
+ * columns split over the CTA's warps (units whose blocks exceed 48 KB fall
+ * back to the default); cps = CTAs per SM of the grid-stride launch (0 =
+ * heuristic).  Every configuration computes the same sums; they differ in
+ * summation order only. */
 
 /* Time every candidate configuration of every operation the problem can run
  * now (K at each stored precision; BJ or ASM when set up) with `reps`

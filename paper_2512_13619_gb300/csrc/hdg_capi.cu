@@ -147,6 +147,10 @@ struct hdg_problem_s {
   int* dmaxit = nullptr;           // iteration cap read by the Givens step (cycle graphs replay it)
   unsigned* d_err = nullptr;
   float* x32 = nullptr;
+  // FP32 work vectors of the low-precision preconditioner (allocated on first use):
+  // polynomial state (lp0, lp1, lp2), K products (ks32), the FP32 copy of the
+  // GMRES iteration's K v_j (t1_32), ASM element results (ze32)
+  float *lp0 = nullptr, *lp1 = nullptr, *lp2 = nullptr, *ks32 = nullptr, *t1_32 = nullptr, *ze32 = nullptr;
   double *t1 = nullptr, *res = nullptr, *pq = nullptr, *pw = nullptr, *ptmp = nullptr, *pAq = nullptr,
          *pt = nullptr, *ze = nullptr, *xo = nullptr, *bo = nullptr;
   // pinned host mirrors
@@ -638,6 +642,18 @@ BrCfg cfg_of(hdg_problem p, int op, int prec) {
   return p->tune[op][prec];
 }
 
+// FP32 work vectors of the low-precision preconditioner path
+void ensure_low(hdg_problem p) {
+  if (p->lp0) return;
+  const int64_t len = p->ndof * p->R;
+  p->lp0 = (float*)p->dalloc(sizeof(float) * len);
+  p->lp1 = (float*)p->dalloc(sizeof(float) * len);
+  p->lp2 = (float*)p->dalloc(sizeof(float) * len);
+  p->ks32 = (float*)p->dalloc(sizeof(float) * len);
+  p->t1_32 = (float*)p->dalloc(sizeof(float) * len);
+  p->ze32 = (float*)p->dalloc(sizeof(float) * std::max<int64_t>(p->NE * p->nlb * p->R, 1));
+}
+
 struct Ops {
   hdg_problem p;
   cudaStream_t s;
@@ -646,8 +662,82 @@ struct Ops {
   void mv_timed_begin(cudaEvent_t*) { timed_begin(p, s); }
   void mv_timed_end(int prec) { timed_end(p, s, prec); }
 
-  // y = K x (prec storage), epilogue
-  void K(int prec, const double* x, double* y, int epi, const double* rhs, const double* scale, const int* active) {
+  BlockRowDesc kdesc(int prec) const {
+    BlockRowDesc d{};
+    d.prec = prec;
+    d.blk = prec == HDG_FP64 ? (const void*)p->K64 : prec == HDG_FP32 ? (const void*)p->K32 : (const void*)p->K16;
+    d.blk_stride = prec == HDG_FP64 ? p->s64 : prec == HDG_FP32 ? p->s32 : p->s16;
+    d.rowptr = p->d_rowptr;
+    d.nbr = p->d_nbr;
+    d.cnt = p->d_cnt;
+    d.n_units = p->nfree;
+    d.b_rows = p->b;
+    d.ld = prec == HDG_FP64 ? p->b : prec == HDG_FP32 ? p->ld32 : p->ld16;
+    d.bc = p->b;
+    d.max_slots = p->ms;
+    d.R = R;
+    d.err = p->d_err;
+    return d;
+  }
+  // y32 = K x32 with FP32 / BF16 blocks, FP32 in and out
+  void K_low(int prec, const float* x32, float* y32, const int* active) {
+    BlockRowDesc d = kdesc(prec);
+    d.in32 = x32;
+    d.out32 = y32;
+    d.epi = EPI_STORE;
+    d.active = active;
+    cudaEvent_t a;
+    mv_timed_begin(&a);
+    blockrow(d, cfg_of(p, TUNE_K, prec), s);
+    mv_timed_end(prec);
+  }
+  // M^{-1} v32 (low-precision blocks) followed by the polynomial step e
+  void Minv_epi(int pc, int prec, const float* v32, const PolyEpi& e, const int* active) {
+    if (pc == HDG_PC_NONE) {
+      poly_epi_apply(e, v32, p->ndof * R, active, R, s);
+      return;
+    }
+    BlockRowDesc d{};
+    d.prec = prec;
+    d.R = R;
+    d.in32 = v32;
+    d.active = active;
+    d.err = p->d_err;
+    d.bc = p->b;
+    if (pc == HDG_PC_BJ) {
+      d.blk = prec == HDG_FP32 ? (const void*)p->bj32 : (const void*)p->bj16;
+      d.blk_stride = prec == HDG_FP32 ? p->bs32 : p->bs16;
+      d.rowptr = p->d_bj_rowptr;
+      d.nbr = p->d_bj_nbr;
+      d.cnt = p->d_bj_cnt;
+      d.n_units = p->nfree;
+      d.b_rows = p->b;
+      d.ld = prec == HDG_FP32 ? p->ld32 : p->ld16;
+      d.max_slots = 1;
+      d.epi = EPI_POLY;
+      d.pe = e;
+      blockrow(d, cfg_of(p, TUNE_BJ, prec), s);
+    } else {
+      d.blk = prec == HDG_FP32 ? (const void*)p->as32 : (const void*)p->as16;
+      d.blk_stride = prec == HDG_FP32 ? p->as_s32 : p->as_s16;
+      d.rowptr = p->d_asm_rowptr;
+      d.nbr = p->d_asm_face_free;
+      d.cnt = p->d_asm_cnt;
+      d.n_units = p->NE;
+      d.b_rows = p->nlb;
+      d.ld = prec == HDG_FP32 ? p->as_ld32 : p->as_ld16;
+      d.max_slots = p->nl;
+      d.epi = EPI_STORE;
+      d.out32 = p->ze32;
+      blockrow(d, cfg_of(p, TUNE_ASM, prec), s);
+      asm_face_sum_f32(p->ze32, p->nlb, p->b, R, p->nfree, p->d_fsum, &e, nullptr, nullptr, s);
+    }
+  }
+
+  // y = K x (prec storage), epilogue; y32 (optional) receives an FP32 copy of
+  // y; x32 (optional) is an FP32 copy of x already at hand
+  void K(int prec, const double* x, double* y, int epi, const double* rhs, const double* scale, const int* active,
+         float* y32 = nullptr, const float* x32 = nullptr) {
     BlockRowDesc d{};
     d.prec = prec;
     d.blk = prec == HDG_FP64 ? (const void*)p->K64 : prec == HDG_FP32 ? (const void*)p->K32 : (const void*)p->K16;
@@ -664,10 +754,15 @@ struct Ops {
     d.in = x;
     d.in32 = nullptr;
     if (prec != HDG_FP64) {
-      to_f32(x, p->x32, p->ndof * R, s);
-      d.in32 = p->x32;
+      if (x32) {
+        d.in32 = x32;
+      } else {
+        to_f32(x, p->x32, p->ndof * R, s);
+        d.in32 = p->x32;
+      }
     }
     d.out = y;
+    d.out32 = y32;
     d.epi = epi;
     d.rhs = rhs;
     d.scale = scale;
@@ -678,8 +773,8 @@ struct Ops {
     blockrow(d, cfg_of(p, TUNE_K, prec), s);
     mv_timed_end(prec);
   }
-  // y = M^{-1} x for the base preconditioner
-  void Minv(int pc, int prec, const double* x, double* y, const int* active) {
+  // y = M^{-1} x for the base preconditioner (x32: optional FP32 copy of x)
+  void Minv(int pc, int prec, const double* x, double* y, const int* active, const float* x32 = nullptr) {
     if (pc == HDG_PC_NONE) {
       launch_axpby(y, x, 1.0, 0.0, p->ndof * R, active, R, s);
       return;
@@ -690,8 +785,12 @@ struct Ops {
     d.in = x;
     d.in32 = nullptr;
     if (prec != HDG_FP64) {
-      to_f32(x, p->x32, p->ndof * R, s);
-      d.in32 = p->x32;
+      if (x32) {
+        d.in32 = x32;
+      } else {
+        to_f32(x, p->x32, p->ndof * R, s);
+        d.in32 = p->x32;
+      }
     }
     d.epi = EPI_STORE;
     d.active = active;
@@ -719,9 +818,17 @@ struct Ops {
       d.b_rows = p->nlb;
       d.ld = prec == HDG_FP64 ? p->nlb : prec == HDG_FP32 ? p->as_ld32 : p->as_ld16;
       d.max_slots = p->nl;
-      d.out = p->ze;
-      blockrow(d, cfg_of(p, TUNE_ASM, prec), s);
-      asm_face_sum(p->ze, p->nlb, p->b, R, p->nfree, p->d_fsum, y, s);
+      if (prec == HDG_FP64) {
+        d.out = p->ze;
+        blockrow(d, cfg_of(p, TUNE_ASM, prec), s);
+        asm_face_sum(p->ze, p->nlb, p->b, R, p->nfree, p->d_fsum, y, s);
+      } else {
+        // FP32 element results, summed per face in FP32
+        ensure_low(p);
+        d.out32 = p->ze32;
+        blockrow(d, cfg_of(p, TUNE_ASM, prec), s);
+        asm_face_sum_f32(p->ze32, p->nlb, p->b, R, p->nfree, p->d_fsum, nullptr, y, nullptr, s);
+      }
     }
   }
   // y = A x with A = M^{-1} K
@@ -733,11 +840,103 @@ struct Ops {
       Minv(pc, mprec, p->ptmp, y, active);
     }
   }
+  // Low-precision polynomial preconditioner: every step is one K product
+  // (FP32 in and out) and one M^{-1} apply whose epilogue performs the
+  // recurrence on FP32 state vectors; the last step writes y in FP64.
+  void Pinv_low(const hdg_solver_opts& o, int mprec, int kpoly, const double* x, const float* x32, double* y,
+                const int* active) {
+    ensure_low(p);
+    const float* xin = x32;
+    if (!xin) {
+      to_f32(x, p->x32, p->ndof * R, s);
+      xin = p->x32;
+    }
+    PolyEpi e{};
+    e.out64 = y;
+    e.p0 = p->lp0;
+    e.p1 = p->lp1;
+    e.p2 = p->lp2;
+    if (o.poly == HDG_POLY_CHEBYSHEV) {
+      // Chebyshev iteration (Saad, Alg. 12.1), degree+1 terms from z = 0
+      const double theta = 0.5 * (p->cheb_b + p->cheb_a), delta = 0.5 * (p->cheb_b - p->cheb_a);
+      const double sigma = theta / delta;
+      double rho = 1.0 / sigma;
+      const int deg = p->poly_n;
+      e.op = CHEB_INIT;
+      e.c1 = (float)(1.0 / theta);
+      e.last = deg == 0 ? 1 : 0;
+      Minv_epi(o.pc, mprec, xin, e, active);
+      for (int kq = 0; kq < deg; ++kq) {
+        K_low(kpoly, p->lp2, p->ks32, active);
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        e.op = CHEB_STEP;
+        e.c1 = (float)(rho_new * rho);
+        e.c2 = (float)(2.0 * rho_new / delta);
+        e.last = kq == deg - 1 ? 1 : 0;
+        Minv_epi(o.pc, mprec, p->ks32, e, active);
+        rho = rho_new;
+      }
+      return;
+    }
+    // GMRES polynomial (Sec. 4.7): q = M^{-1} x; real values and conjugate pairs
+    const int P = p->poly_n;
+    auto real_at = [&](int i) { return i < P && p->th_im[i] == 0.0; };
+    e.op = PP_INIT;
+    e.fin = (P == 1 && real_at(0)) ? 1 : 0;
+    e.cfin = (float)(1.0 / p->th_re[0]);
+    Minv_epi(o.pc, mprec, xin, e, active);
+    int i = 0;
+    bool first = true;
+    while (i < P) {
+      const double a = p->th_re[i], bi = p->th_im[i];
+      PolyEpi f = e;
+      f.wzero = first ? 1 : 0;
+      f.fin = 0;
+      f.last = 0;
+      if (bi == 0.0) {
+        if (i == P - 1) break;          // folded into the step that last updated q
+        K_low(kpoly, p->lp0, p->ks32, active);
+        f.op = PP_REAL;
+        f.c1 = (float)(1.0 / a);
+        f.fin = (i + 1 == P - 1 && real_at(i + 1)) ? 1 : 0;
+        f.cfin = f.fin ? (float)(1.0 / p->th_re[i + 1]) : 0.f;
+        Minv_epi(o.pc, mprec, p->ks32, f, active);
+        i += 1;
+      } else {
+        const double mod2 = a * a + bi * bi;
+        const bool last = (i + 1 >= P - 1);
+        K_low(kpoly, p->lp0, p->ks32, active);
+        f.op = PP_PAIR_T;
+        f.c1 = (float)(2.0 * a);
+        f.c2 = (float)(1.0 / mod2);
+        f.last = last ? 1 : 0;
+        Minv_epi(o.pc, mprec, p->ks32, f, active);
+        if (!last) {
+          K_low(kpoly, p->lp2, p->ks32, active);
+          PolyEpi g = e;
+          g.op = PP_PAIR_Q;
+          g.c2 = (float)(1.0 / mod2);
+          g.fin = (i + 2 == P - 1 && real_at(i + 2)) ? 1 : 0;
+          g.cfin = g.fin ? (float)(1.0 / p->th_re[i + 2]) : 0.f;
+          Minv_epi(o.pc, mprec, p->ks32, g, active);
+        }
+        i += 2;
+      }
+      first = false;
+    }
+  }
+
   // y = P^{-1} x : polynomial p(M^{-1}K) applied to M^{-1} x, or M^{-1} x.
-  void Pinv(const hdg_solver_opts& o, int mprec, int kpoly, const double* x, double* y, const int* active) {
+  // x32 (optional): an FP32 copy of x already at hand.
+  void Pinv(const hdg_solver_opts& o, int mprec, int kpoly, const double* x, double* y, const int* active,
+            const float* x32 = nullptr) {
     const int64_t len = p->ndof * R;
     if (o.poly == HDG_POLY_NONE || p->poly_n == 0) {
-      Minv(o.pc, mprec, x, y, active);
+      Minv(o.pc, mprec, x, y, active, x32);
+      return;
+    }
+    if (mprec != HDG_FP64 && kpoly != HDG_FP64) {
+      Pinv_low(o, mprec, kpoly, x, x32, y, active);
       return;
     }
     double* q = p->pq;
@@ -941,8 +1140,9 @@ struct IterLauncher {
     const int64_t len = p->ndof * R;
     double* vj = p->V + (int64_t)j * len;
     double* vn = p->V + (int64_t)(j + 1) * len;
-    ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running);
-    ops.Pinv(*o, mprec, kpoly, p->t1, vn, p->running);
+    float* t32 = mprec != HDG_FP64 ? p->t1_32 : nullptr;   // the preconditioner's FP32 input, from the epilogue
+    ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running, t32);
+    ops.Pinv(*o, mprec, kpoly, p->t1, vn, p->running, t32);
     orthogonalize(k, o->orth, j, s);
   }
 };
@@ -1058,6 +1258,7 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
   GmresResult out;
   const int R = p->R, m = o.restart;
   const int64_t len = p->ndof * R;
+  if (mprec != HDG_FP64 || kprec != HDG_FP64 || kpoly != HDG_FP64) ensure_low(p);   // before any capture
   Ops ops{p, s, R};
   GmresView k = make_view(p, R, m, rtol, maxit);
   CK(cudaMemsetAsync(x, 0, sizeof(double) * len, s));
@@ -1135,8 +1336,9 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
       }
       double* vj = p->V + (int64_t)j * len;
       double* vn = p->V + (int64_t)(j + 1) * len;
-      ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running);
-      ops.Pinv(o, mprec, kpoly, p->t1, vn, p->running);
+      float* t32 = mprec != HDG_FP64 ? p->t1_32 : nullptr;
+      ops.K(kprec, vj, p->t1, EPI_SCALE, nullptr, p->vscale + (int64_t)j * R, p->running, t32);
+      ops.Pinv(o, mprec, kpoly, p->t1, vn, p->running, t32);
       orthogonalize(k, o.orth, j, s);
       CK(cudaEventRecord(p->ev_iter[j], s));
     }
@@ -1334,6 +1536,8 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
   const int m = opts ? opts->restart : 50;
   by += (int64_t)(m + 12) * nfree * b * R * 8;
   by += NE * nlb * R * 8;
+  if (opts && opts->inner_prec != HDG_FP64)                       // FP32 vectors of the low-precision preconditioner
+    by += (5 * nfree * b + NE * nlb) * R * 4;
   return (size_t)by;
 }
 
@@ -2501,7 +2705,7 @@ int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap) {
 
 hdg_status hdg_set_tuning(hdg_problem p, int op, int prec, const int* cfg3) {
   if (!p || op < 0 || op > 2 || prec < 0 || prec > 2 || !cfg3) return HDG_ERR_ARG;
-  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_SPLIT || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
+  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_BULK || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
     return HDG_ERR_ARG;
   p->tune[op][prec].kind = cfg3[0];
   p->tune[op][prec].sp = cfg3[1];

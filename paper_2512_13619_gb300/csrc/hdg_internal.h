@@ -105,7 +105,35 @@ void copy_block_f64(double* dst, int64_t ldd, int64_t sd, const double* src, int
 //                   blk[u][s](row, c) * in[(nbr[u][s]*bc + c)*R + r] )
 // blk[u][s] is a column-major b_rows x bc block at blk + (rowptr[u] + s)*
 // blk_stride elements (compact storage: cnt[u] = rowptr[u+1] - rowptr[u]).
-enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_SCALE = 2 };
+enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_SCALE = 2, EPI_POLY = 3 };
+
+// One step of a polynomial preconditioner fused into the epilogue of the
+// block-Jacobi apply (or of the ASM face sum), on FP32 state vectors: v is the
+// freshly computed (M^{-1} K s)[o] (or (M^{-1} x)[o] for the INIT steps).
+//   CHEB_INIT  r = v; d = c1 v; z = d                       (c1 = 1 / theta)
+//   CHEB_STEP  r -= v; d = c1 d + c2 r; z += d               (Chebyshev iteration)
+//   PP_INIT    q = v
+//   PP_REAL    w += c1 q; q -= c1 v                          (c1 = 1 / theta_i)
+//   PP_PAIR_T  t = c1 q - v; w += c2 t                       (c1 = 2a, c2 = 1 / (a^2 + b^2))
+//   PP_PAIR_Q  q -= c2 v                                     (c2 = 1 / (a^2 + b^2))
+// p0, p1, p2 hold (r, z, d) for Chebyshev and (q, w, t) for the GMRES
+// polynomial.  wzero: w reads as 0 (first term).  fin: the step is followed
+// by the final real value theta_P, so out64 = w + cfin q_new (PP_INIT:
+// cfin v).  last: the step completes the polynomial, out64 = z (Chebyshev) or
+// w (PP_PAIR_T); the state is then not written back.
+enum PolyOp { POLY_OP_NONE = 0, CHEB_INIT = 1, CHEB_STEP = 2, PP_INIT = 3, PP_REAL = 4, PP_PAIR_T = 5,
+              PP_PAIR_Q = 6 };
+struct PolyEpi {
+  int op;
+  int wzero, fin, last;
+  float c1, c2, cfin;
+  float *p0, *p1, *p2;
+  double* out64;
+};
+// out64 / FP32 state update of one polynomial step on `len` values of v
+// (FP32), for the preconditioner without a base (M = I).
+void poly_epi_apply(const PolyEpi& e, const float* v, int64_t len, const int* active, int R, cudaStream_t s);
+
 struct BlockRowDesc {
   int prec;               // HDG_FP64 / HDG_FP32 / HDG_BF16 storage of blk
   const void* blk;
@@ -118,7 +146,9 @@ struct BlockRowDesc {
   int ld;                 // stored rows per block column (>= b_rows; rows past b_rows are padding)
   const double* in;
   const float* in32;      // FP32 copy of `in` (required for FP32/BF16 blocks)
-  double* out;
+  double* out;            // FP64 output (may be NULL when out32 is set)
+  float* out32;           // optional FP32 copy of the output
+  PolyEpi pe;             // EPI_POLY: the polynomial step applied to the output
   int epi;
   const double* rhs;      // EPI_RESID: out = rhs - acc
   const double* scale;    // EPI_SCALE: out = scale[r] * acc (per RHS)
@@ -132,7 +162,7 @@ struct BlockRowDesc {
 // row), BR_VEC (VR rows per thread, 16-byte loads, sp slot parts), BR_SPLIT
 // (sp threads per row, each summing every sp-th slot, shuffle reduction).
 // cps: CTAs per SM of the grid-stride launch (0 = heuristic).
-enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4 };
+enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5 };
 struct BrCfg {
   int kind = BR_DEFAULT, sp = 0, cps = 0;
 };
@@ -186,6 +216,10 @@ void asm_pack(const double* Pinv, int nlb, int b, int nl, int64_t n_elem, const 
 // z_f = z^{e1}[slot s1] + z^{e2}[slot s2] (face-parallel, no atomics)
 void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum, double* z,
                   cudaStream_t s);
+// the same sum from FP32 element results, followed by a polynomial step (or,
+// with pe->op == POLY_OP_NONE, stored to z64 and/or z32)
+void asm_face_sum_f32(const float* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum,
+                      const PolyEpi* pe, double* z64, float* z32, cudaStream_t s);
 
 // --------------------------------------------------------------- recovery
 struct RecoverDesc {

@@ -4,6 +4,7 @@
 // element recovery (Eq. w19, Eq. w16).
 #include "hdg_common.cuh"
 #include "hdg_internal.h"
+#include "k_poly.cuh"
 
 namespace hdg {
 
@@ -139,6 +140,25 @@ __global__ void asm_face_sum_kernel(const double* ze, int nlb, int b, int R, int
   }
 }
 
+__global__ void asm_face_sum_f32_kernel(const float* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum,
+                                        PolyEpi pe, double* z64, float* z32) {
+  const int64_t total = n_free * b * R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = idx / (b * R);
+    const int rem = (int)(idx - f * b * R);
+    const int e1 = fsum[f * 4], s1 = fsum[f * 4 + 1], e2 = fsum[f * 4 + 2], s2 = fsum[f * 4 + 3];
+    float v = ze[((int64_t)e1 * nlb + s1 * b) * R + rem];
+    if (e2 >= 0) v += ze[((int64_t)e2 * nlb + s2 * b) * R + rem];
+    if (pe.op != POLY_OP_NONE) {
+      poly_epi(pe, idx, v);
+    } else {
+      if (z64) z64[idx] = (double)v;
+      if (z32) z32[idx] = v;
+    }
+  }
+}
+
 __global__ void expand_trace_kernel(const double* x, const double* uhatD, const int32_t* free_of_face, int64_t n_face,
                                     int b, int R, double* full) {
   const int64_t total = n_face * b * R;
@@ -246,6 +266,16 @@ void asm_face_sum(const double* ze, int nlb, int b, int R, int64_t n_free, const
   int64_t total = n_free * b * R;
   if (total <= 0) return;
   count_launch(); asm_face_sum_kernel<<<grid_for(total, 256), 256, 0, s>>>(ze, nlb, b, R, n_free, fsum, z);
+}
+
+void asm_face_sum_f32(const float* ze, int nlb, int b, int R, int64_t n_free, const int32_t* fsum,
+                      const PolyEpi* pe, double* z64, float* z32, cudaStream_t s) {
+  int64_t total = n_free * b * R;
+  if (total <= 0) return;
+  PolyEpi e{};
+  if (pe) e = *pe;
+  count_launch();
+  asm_face_sum_f32_kernel<<<grid_for(total, 256), 256, 0, s>>>(ze, nlb, b, R, n_free, fsum, e, z64, z32);
 }
 
 void bcast_copy(double* dst, const double* src, int64_t n, int64_t count, cudaStream_t s) {

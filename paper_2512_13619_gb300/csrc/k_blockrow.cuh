@@ -28,6 +28,7 @@
 #include <type_traits>
 #include "hdg_common.cuh"
 #include "hdg_internal.h"
+#include "k_poly.cuh"
 
 namespace hdg {
 
@@ -38,9 +39,33 @@ template <> struct Acc<double> { using type = double; };
 
 __device__ __forceinline__ void epi_store(const BlockRowDesc& d, int64_t u, int row, int r, double v) {
   const int64_t o = (u * d.b_rows + row) * d.R + r;
+  if (d.epi == EPI_POLY) {
+    poly_epi(d.pe, o, (float)v);
+    return;
+  }
   if (d.epi == EPI_RESID) v = d.rhs[o] - v;
   else if (d.epi == EPI_SCALE) v = d.scale[r] * v;
-  d.out[o] = v;
+  if (d.out) d.out[o] = v;
+  if (d.out32) d.out32[o] = (float)v;
+}
+
+// Four consecutive outputs (u, row, r0 .. r0+3) of a row, r0 a multiple of 4
+// (R a multiple of 4): 16-byte state and output accesses.
+__device__ __forceinline__ void epi_store4(const BlockRowDesc& d, int64_t u, int row, int r0, float4 v) {
+  const int64_t o = (u * d.b_rows + row) * d.R + r0;
+  if (d.epi == EPI_POLY) {
+    poly_epi4(d.pe, o, v);
+    return;
+  }
+  if (d.epi == EPI_RESID || d.epi == EPI_SCALE) {
+    epi_store(d, u, row, r0, (double)v.x);
+    epi_store(d, u, row, r0 + 1, (double)v.y);
+    epi_store(d, u, row, r0 + 2, (double)v.z);
+    epi_store(d, u, row, r0 + 3, (double)v.w);
+    return;
+  }
+  if (d.out) st4d(d.out + o, v);
+  if (d.out32) st4(d.out32 + o, v);
 }
 
 __device__ __forceinline__ bool any_active(const int* active, int R) {
@@ -453,13 +478,218 @@ __global__ void __launch_bounds__(288) blockrow_vec_kernel(BlockRowDesc d, int G
 #pragma unroll
       for (int v = 0; v < VR; ++v)
         if (rg * VR + v < d.b_rows) {
+          if constexpr (R % 4 == 0) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) epi_store(d, u, rg * VR + v, r, (double)acc[v][r]);
+            for (int r = 0; r < R; r += 4)
+              epi_store4(d, u, rg * VR + v, r, make_float4(acc[v][r], acc[v][r + 1], acc[v][r + 2], acc[v][r + 3]));
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) epi_store(d, u, rg * VR + v, r, (double)acc[v][r]);
+          }
         }
     }
   }
 }
 
+
+// Kernel "bulk": persistent CTAs (one per SM) stream G whole units per stage
+// with ONE bulk copy (a unit's blocks are contiguous in HBM; the copy is
+// tagged evict-first in L2 so that the gathered x stays resident there) into
+// a ring of shared-memory stages that a single producer lane keeps full.
+// Eight consumer warps read K from shared memory, VR rows of a column per
+// 16-byte vector, and x directly through L1/L2.  Consumer thread (unit g,
+// row group rg, column part cp) sums the columns c = cp, cp + NCP, ... of the
+// unit's concatenated slot columns; the NSUB parts inside a warp meet by
+// shuffles, the WPU warps of a unit in shared memory.  FP32/BF16 blocks.
+struct BulkPlan {
+  int G, NS, WPU, NSUB, NRG;
+  int stage_bytes;     // bytes of one stage (a multiple of 128)
+  int red_floats;      // reduction area
+  int64_t ntasks;
+};
+constexpr int kBulkConsumers = 256;
+template <typename T, int R, int BC>
+__global__ void __launch_bounds__(kBulkConsumers + 32, 1) blockrow_bulk_kernel(BlockRowDesc d, BulkPlan pl) {
+  constexpr int VR = Vec16<T>::N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + 8;
+  float* red = reinterpret_cast<float*>(smem + 256);
+  unsigned char* stages = smem + 256 + ((size_t)pl.red_floats * 4 + 127) / 128 * 128;
+  __shared__ volatile int s_abort;
+  __shared__ long long s_issued[8];
+  const int tid = threadIdx.x;
+  if (!any_active(d.active, R)) return;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int i = 0; i < pl.NS; ++i) {
+      s_issued[i] = -1;
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kBulkConsumers / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
+  const T* blk = static_cast<const T*>(d.blk);
+  if (tid >= kBulkConsumers) {
+    // ------------------------------------------------------------ producer
+    if (tid == kBulkConsumers) {
+      uint64_t pol;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+      int64_t k = 0;
+      for (int64_t t = blockIdx.x; t < pl.ntasks; t += gridDim.x, ++k) {
+        const int st = (int)(k % pl.NS);
+        const unsigned ph = (unsigned)((k / pl.NS) & 1);
+        if (s_abort || !mbar_wait_bounded(&empty[st], ph ^ 1u)) {
+          if (!s_abort) atomicOr(d.err, ERRBIT_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        const int64_t u0 = t * pl.G;
+        const int64_t u1 = min(u0 + pl.G, d.n_units);
+        const int64_t b0 = d.rowptr[u0];
+        const unsigned bytes = (unsigned)((d.rowptr[u1] - b0) * blk_bytes);
+        unsigned char* dst = stages + (size_t)st * pl.stage_bytes;
+        s_issued[st] = k;
+        mbar_arrive_expect_tx(&full[st], bytes);
+        if (bytes)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+              "%4;" ::"r"(smem_u32(dst)),
+              "l"(blk + b0 * d.blk_stride), "r"(bytes), "r"(smem_u32(&full[st])), "l"(pol)
+              : "memory");
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int w = tid >> 5, lane = tid & 31;
+    const int g = w / pl.WPU, wu = w - g * pl.WPU;
+    const int rg = lane / pl.NSUB, sub = lane - rg * pl.NSUB;
+    const bool valid = rg < pl.NRG && g < pl.G;
+    const int NCP = pl.WPU * pl.NSUB;
+    const int cp = wu * pl.NSUB + sub;
+    bool abort = false;
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < pl.ntasks; t += gridDim.x, ++k) {
+      const int st = (int)(k % pl.NS);
+      const unsigned ph = (unsigned)((k / pl.NS) & 1);
+      if (!abort && !mbar_wait_bounded(&full[st], ph)) {
+        atomicOr(d.err, ERRBIT_TIMEOUT);
+        abort = true;
+        s_abort = 1;
+      }
+      const int64_t u0 = t * pl.G;
+      const int64_t u = u0 + g;
+      float acc[VR][R];
+#pragma unroll
+      for (int v = 0; v < VR; ++v)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[v][r] = 0.f;
+      if (!abort && valid && u < d.n_units) {
+        const int n = d.cnt[u];
+        const int64_t off = d.rowptr[u] - d.rowptr[u0];
+        const T* sb = reinterpret_cast<const T*>(stages + (size_t)st * pl.stage_bytes) + off * d.blk_stride +
+                      rg * VR;
+        const int32_t* nbr = d.nbr + u * d.max_slots;
+        const int ncol = n * BC;
+        for (int c = cp; c < ncol; c += NCP) {
+          const int sl = c / BC;
+          const int col = c - sl * BC;
+          float kv[VR];
+          if constexpr (std::is_same<T, float>::value) {
+            const float4 q = *reinterpret_cast<const float4*>(sb + (int64_t)sl * d.blk_stride + col * d.ld);
+            kv[0] = q.x; kv[1] = q.y; kv[2] = q.z; kv[3] = q.w;
+          } else {
+            const uint4 q = *reinterpret_cast<const uint4*>(sb + (int64_t)sl * d.blk_stride + col * d.ld);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+            for (int i = 0; i < VR / 2; ++i) {
+              const float2 f = __bfloat1622float2(h[i]);
+              kv[2 * i] = f.x;
+              kv[2 * i + 1] = f.y;
+            }
+          }
+          const float* xin = d.in32 + ((int64_t)nbr[sl] * BC + col) * R;
+          float xv[R];
+          if constexpr (R % 4 == 0) {
+#pragma unroll
+            for (int r4 = 0; r4 < R; r4 += 4) {
+              const float4 q = __ldg(reinterpret_cast<const float4*>(xin + r4));
+              xv[r4] = q.x; xv[r4 + 1] = q.y; xv[r4 + 2] = q.z; xv[r4 + 3] = q.w;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) xv[r] = __ldg(xin + r);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int v = 0; v < VR; ++v) acc[v][r] = fmaf(kv[v], xv[r], acc[v][r]);
+        }
+      }
+      // the warp is done with the stage's blocks
+      __syncwarp();
+      if (lane == 0 && !abort) mbar_arrive(&empty[st]);
+      // the NSUB column parts of a warp
+      for (int o = 1; o < pl.NSUB; o <<= 1)
+#pragma unroll
+        for (int v = 0; v < VR; ++v)
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[v][r] += __shfl_xor_sync(0xffffffffu, acc[v][r], o);
+      if (pl.WPU == 1) {
+        if (!abort && valid && sub == 0 && u < d.n_units) {
+#pragma unroll
+          for (int v = 0; v < VR; ++v)
+            if (rg * VR + v < d.b_rows) {
+              if constexpr (R % 4 == 0) {
+#pragma unroll
+                for (int r = 0; r < R; r += 4)
+                  epi_store4(d, u, rg * VR + v, r,
+                             make_float4(acc[v][r], acc[v][r + 1], acc[v][r + 2], acc[v][r + 3]));
+              } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) epi_store(d, u, rg * VR + v, r, (double)acc[v][r]);
+              }
+            }
+        }
+      } else {
+        // red[g][wu][row][r], rows rg * VR + v
+        const int rows = pl.NRG * VR;
+        if (valid && sub == 0) {
+#pragma unroll
+          for (int v = 0; v < VR; ++v)
+#pragma unroll
+            for (int r = 0; r < R; ++r) red[(((int64_t)g * pl.WPU + wu) * rows + rg * VR + v) * R + r] = acc[v][r];
+        }
+        consumer_bar(kBulkConsumers);
+        if (!abort) {
+          for (int idx = tid; idx < pl.G * d.b_rows * R; idx += kBulkConsumers) {
+            const int gg = idx / (d.b_rows * R);
+            const int rem = idx - gg * d.b_rows * R;
+            const int row = rem / R, r = rem - row * R;
+            const int64_t uu = u0 + gg;
+            if (uu >= d.n_units) continue;
+            float sum = 0.f;
+            for (int q = 0; q < pl.WPU; ++q) sum += red[(((int64_t)gg * pl.WPU + q) * rows + row) * R + r];
+            epi_store(d, uu, row, r, (double)sum);
+          }
+        }
+        consumer_bar(kBulkConsumers);
+      }
+      if (abort) break;
+    }
+  }
+  // after an abort, copies may still be in flight: wait (bounded) for them
+  // before the CTA's shared memory goes away
+  __syncthreads();
+  if (tid == 0 && s_abort) {
+    for (int i = 0; i < pl.NS; ++i) {
+      const long long q = s_issued[i];
+      if (q >= 0 && !mbar_wait_bounded(&full[i], (unsigned)((q / pl.NS) & 1))) atomicOr(d.err, ERRBIT_TIMEOUT);
+    }
+  }
+}
 
 int num_sms() {
   int dev = 0, n = 0;
@@ -513,6 +743,54 @@ Plan make_plan(const BlockRowDesc& d) {
   pl.NPW = std::max(1, std::min(4, 1 + (pl.nstage - 1) / pl.nch));
   pl.ntasks = (d.n_units + pl.G - 1) / pl.G;
   return pl;
+}
+
+// Plan of the bulk kernel; false when a unit's blocks do not fit a stage of
+// kBulkStageMax bytes or the rows do not divide into 16-byte vectors.
+constexpr size_t kBulkStageMax = 48 * 1024;
+template <typename T>
+bool bulk_plan(const BlockRowDesc& d, BulkPlan* pl) {
+  if constexpr (std::is_same<T, double>::value) {
+    return false;
+  } else {
+    constexpr int VR = Vec16<T>::N;
+    if (d.in32 == nullptr || d.ld % VR != 0 || d.ld < d.b_rows) return false;
+    const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
+    const size_t row_bytes = (size_t)d.max_slots * blk_bytes;
+    if (blk_bytes % 16 != 0 || row_bytes > kBulkStageMax) return false;
+    BulkPlan q{};
+    q.NRG = d.ld / VR;
+    if (q.NRG > 32) return false;
+    q.NSUB = 1;
+    while (q.NSUB * 2 * q.NRG <= 32) q.NSUB *= 2;
+    // units per stage: as many as fit the stage size, with a whole number of
+    // consumer warps each (G * WPU = 8)
+    int G = 1;
+    while (G * 2 <= 8 && (size_t)G * 2 * row_bytes <= kBulkStageMax) G *= 2;
+    q.G = G;
+    q.WPU = (kBulkConsumers / 32) / G;
+    q.stage_bytes = (int)(((size_t)G * row_bytes + 127) / 128 * 128);
+    q.red_floats = q.WPU > 1 ? G * q.WPU * q.NRG * VR * d.R : 0;
+    const size_t red_bytes = ((size_t)q.red_floats * 4 + 127) / 128 * 128;
+    q.NS = (int)std::min<size_t>(8, (kSmemCap - red_bytes) / q.stage_bytes);
+    if (q.NS < 2) return false;
+    q.ntasks = (d.n_units + G - 1) / G;
+    *pl = q;
+    return true;
+  }
+}
+
+template <typename T, int R, int BC>
+bool launch_bulk(const BlockRowDesc& d, cudaStream_t s) {
+  BulkPlan pl;
+  if (!bulk_plan<T>(d, &pl)) return false;
+  const size_t smem = 256 + ((size_t)pl.red_floats * 4 + 127) / 128 * 128 + (size_t)pl.NS * pl.stage_bytes;
+  auto kern = blockrow_bulk_kernel<T, R, BC>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);  // per context; cheap
+  int64_t grid = std::min<int64_t>(pl.ntasks, (int64_t)num_sms());
+  if (grid < 1) grid = 1;
+  count_launch(); kern<<<(unsigned)grid, kBulkConsumers + 32, smem, s>>>(d, pl);
+  return true;
 }
 
 template <typename T, int R>
@@ -614,6 +892,11 @@ void launch_split(const BlockRowDesc& d, int sp, int cps, cudaStream_t s) {
 
 template <typename T, int R, int BC>
 void launch_direct_bc(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
+  // the bulk kernel for the shapes whose face rows fit a stage (b = 9, 16,
+  // 20, 27) with several right-hand sides
+  if constexpr (!std::is_same<T, double>::value && (BC == 9 || BC == 16 || BC == 20 || BC == 27) && R >= 4) {
+    if (cfg.kind == BR_BULK && launch_bulk<T, R, BC>(d, s)) return;
+  }
   if constexpr (!std::is_same<T, double>::value && BC > 0) {
     if ((cfg.kind == BR_DEFAULT || cfg.kind == BR_VEC) && vec_ok<T>(d)) {
       launch_vec<T, R, BC>(d, cfg.sp, cfg.cps, s);
@@ -649,22 +932,34 @@ void launch_direct(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
   }
 }
 
-template <typename T>
-void dispatch_R(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
 #define HDG_BR_CASE(RR)                                  \
   case RR:                                               \
     if (cfg.kind == BR_TMA) launch_tma<T, RR>(d, s);     \
     else launch_direct<T, RR>(d, cfg, s);                \
     break;
+// R in {1, 2} and R in {4, 8}: separate translation units compile them in parallel
+template <typename T>
+void dispatch_R_narrow(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
   switch (d.R) {
     HDG_BR_CASE(1)
     HDG_BR_CASE(2)
+    default: break;
+  }
+}
+template <typename T>
+void dispatch_R_wide(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
+  switch (d.R) {
     HDG_BR_CASE(4)
     HDG_BR_CASE(8)
     default: break;
   }
-#undef HDG_BR_CASE
 }
+template <typename T>
+void dispatch_R(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
+  if (d.R <= 2) dispatch_R_narrow<T>(d, cfg, s);
+  else dispatch_R_wide<T>(d, cfg, s);
+}
+#undef HDG_BR_CASE
 
 template <typename T>
 int candidates_T(const BlockRowDesc& d, BrCfg* out, int cap) {
@@ -685,6 +980,9 @@ int candidates_T(const BlockRowDesc& d, BrCfg* out, int cap) {
       for (int sp : {1, 2, 4, 8})
         if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
           for (int cps : {8, 16, 32}) add(BR_VEC, sp, cps);
+      BulkPlan bp;
+      if ((d.bc == 9 || d.bc == 16 || d.bc == 20 || d.bc == 27) && d.R >= 4 && bulk_plan<T>(d, &bp))
+        add(BR_BULK, 0, 0);
     }
   }
   add(BR_TMA, 0, 0);

@@ -15,6 +15,7 @@
 // Golub & Van Loan Sec. 7.5) with the Leja ordering of the Ritz values.
 #include "hdg_common.cuh"
 #include "hdg_gmres.h"
+#include "k_poly.cuh"
 
 namespace hdg {
 
@@ -454,6 +455,13 @@ __global__ void pp_pair_q_kernel(double* q, const double* At, double inv_mod2, i
     q[e] = q[e] - inv_mod2 * At[e];
 }
 
+// A polynomial step whose "M^{-1}" is the identity: v is the input vector.
+__global__ void poly_epi_kernel(PolyEpi e, const float* v, int64_t len, const int* running, int R) {
+  if (running && !any_running(running, R)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    poly_epi(e, i, v[i]);
+}
+
 // Chebyshev step: z += d; then (unless last) r -= Ad computed by the caller
 // before; d = c1 d + c2 r.  `phase` 0: z = d (first), 1: z += d,
 // 2: r -= Ad; d = c1 d + c2 r.
@@ -749,6 +757,11 @@ void launch_cheb(double* z, double* d, double* r, const double* Ad, double c1, d
                  const int* running, int R, cudaStream_t s) {
   count_launch(); cheb_kernel<<<ew_grid(len), 256, 0, s>>>(z, d, r, Ad, c1, c2, len, phase, running, R);
 }
+void poly_epi_apply(const PolyEpi& e, const float* v, int64_t len, const int* active, int R, cudaStream_t s) {
+  if (len <= 0) return;
+  count_launch(); poly_epi_kernel<<<ew_grid(len), kThreads, 0, s>>>(e, v, len, active, R);
+}
+
 void launch_ritz_leja(const double* H, int ldh, int P, int harmonic, double* re, double* im, int* nout,
                       unsigned* err, cudaStream_t s) {
   const size_t smem = sizeof(double) * 2 * kMaxPoly * kMaxPoly;

@@ -317,7 +317,8 @@ def test_condense_strided_shared_blocks(shared):
     assert rel(K1, K2) < 1e-13 and rel(r1, r2) < 1e-13
 
 
-@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'cdr_k2_R4', 'beam_k2', 'tet_obst_k3'])
+@pytest.mark.parametrize('name', ['hex_k2', 'elast_R2', 'cdr_M5_R4', 'cdr_k2_R4', 'beam_k2', 'tet_obst_k3',
+                                  'elast_pert_k2_R8'])
 def test_every_tuning_candidate_matches_oracle(name):
     """Every launch configuration the autotuner may pick computes the same
     block-row products: K x at each storage precision (bounds as in the
@@ -360,6 +361,11 @@ def test_every_tuning_candidate_matches_oracle(name):
             assert L.hdg_set_tuning(p.h, op, 0, cfg) == 0
             z = p.apply_precond(o, x, 'fp64')
             assert rel(z, z_ref) < 1e-10, (pc, cfg)
+            ncand += 1
+        for cfg in L.hdg_tuning_candidates(p.h, op, 1):      # FP32 blocks, FP32 accumulation
+            assert L.hdg_set_tuning(p.h, op, 1, cfg) == 0
+            z = p.apply_precond(o, x, 'fp32')
+            assert rel(z, z_ref) < 1e-3, (pc, cfg)
             ncand += 1
         assert ncand > 8
         assert L.hdg_autotune(p.h, 3, 1) == 0
@@ -480,3 +486,46 @@ def test_cycle_graphs_follow_a_new_polynomial_and_iteration_cap():
     assert info3.iters <= 3 and info3.converged == 0
     p.close()
     q.close()
+
+
+@pytest.mark.parametrize('pc,poly,deg', [('bj', 'chebyshev', 4), ('asm', 'chebyshev', 4), ('bj', 'chebyshev', 1),
+                                         ('bj', 'gmres', 5), ('bj', 'gmres', 6), ('asm', 'gmres', 7),
+                                         ('none', 'gmres', 4)])
+def test_low_precision_polynomial_apply(pc, poly, deg):
+    """The polynomial preconditioner with FP32 blocks (M^{-1} and K), its
+    recurrence fused into the epilogue of M^{-1} on FP32 state vectors,
+    against the oracle's FP64 apply of the same polynomial (Sec. 4.7 /
+    Chebyshev iteration): within the FP32 rounding of the degree+1 products
+    (relative 1e-4), for every right-hand side."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver
+    w = W.hex_elasticity(n=3, k=1, R=4)
+    s = OracleSystem(w)
+    o = driver.opts(pc=pc, poly=poly, degree=deg, inner='fp32', poly_prec='fp32')
+    p = _problem(w)
+    p.assemble(o)
+    v0 = w.random_vector(31)
+    p.setup_precond(o, v0)
+    if pc == 'bj':
+        Binv = precond.bj_setup(s.K, s.bsz)
+        M = lambda v: precond.bj_apply(Binv, v)
+    elif pc == 'asm':
+        subs = precond.asm_setup(s.K, s.elem_dofs)
+        M = lambda v: precond.asm_apply(subs, v)
+    else:
+        M = lambda v: v
+    A = lambda v: M(s.K @ v)
+    x = np.random.default_rng(12).standard_normal((p.n_dof, w.R))
+    if poly == 'chebyshev':
+        a, b = p.poly().real[:2]
+        zo = np.column_stack([precond.chebyshev_apply(A, a, b, deg, M(x[:, r])) for r in range(w.R)])
+    else:
+        th = p.poly()
+        zo = np.column_stack([precond.pp_apply(A, th, M(x[:, r])) for r in range(w.R)])
+    z = p.apply_precond(o, x, 'fp32')
+    for r in range(w.R):
+        assert rel(z[:, r], zo[:, r]) < 1e-4, (r, rel(z[:, r], zo[:, r]))
+    # the FP64 apply of the same set-up agrees with the oracle to FP64 rounding
+    z64 = p.apply_precond(o, x, 'fp64')
+    assert rel(z64, zo) < 1e-8
+    p.close()
