@@ -87,12 +87,15 @@ def parse():
                          'Newton with BJ, BJ-PP(10), ASM, ASM-PP(10) GMRES(50) to 1e-6)')
     ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
                     help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
-    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64', 'generate', 'step3'],
+    ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64', 'generate', 'step3',
+                                          'matvec3'],
                     default=None,
                     help='set up the workload and run only one hdg_condense call (condense), one FP64 and '
                          'one FP32 hdg_apply_K call (matvec), one solve (solve-*) or two hdg_hex_blocks calls '
                          '(generate: the element blocks generated on the device), or two mixed steps of the '
-                         'default workload (step3, --mesh-n sets its size), for profilers; no JSON')
+                         'default workload (step3, --mesh-n sets its size), or one FP64, FP32 and BF16 '
+                         'hdg_apply_K call on the default workload after autotuning (matvec3), for profilers; '
+                         'no JSON')
     return ap.parse_args()
 
 
@@ -1292,7 +1295,7 @@ def run_profile(args):
     __graft_entry__.build()
     from hdg_inputs import workloads as W
     from paper_2512_13619_gb300 import driver, _lib as L
-    if args.profile == 'step3':
+    if args.profile in ('step3', 'matvec3'):
         w = W.hex_elasticity(n=args.mesh_n or 32, k=2, R=8)
         verts, perm, nquad = driver.hex_geometry_inputs(w)
         ru, ruh = w.load_vectors()
@@ -1305,6 +1308,25 @@ def run_profile(args):
         p = driver.Problem.from_workload(w, 0)
         if args.no_graphs:
             L.hdg_set_graphs(p.h, 0)
+        if args.profile == 'matvec3':
+            driver.check(L.hdg_condense_hex(p.h, 0, w.n_elem, nquad, d['verts'], d['perm'], phys, d['ru'], d['ruh'],
+                                            1), 'condense_hex')
+            p.set_dirichlet(np.zeros((w.n_face, w.M * w.PF, w.R)))
+            o16 = driver.opts(pc='bj', inner='fp32', poly_prec='bf16')
+            p.assemble(o16)
+            p.setup_precond(o16)
+            driver.check(L.hdg_autotune(p.h, 5, 0, None), 'autotune')
+            x = torch.randn(p.n_dof * w.R, dtype=torch.float64, device='cuda')
+            y = torch.empty_like(x)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push('matvec')
+            for prec in (L.HDG_FP64, L.HDG_FP32, L.HDG_BF16):
+                driver.check(L.hdg_apply_K(p.h, prec, x, y), 'apply_K')
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            p.close()
+            print('profile run done')
+            return
         for it in range(2):
             driver.check(L.hdg_condense_hex(p.h, 0, w.n_elem, nquad, d['verts'], d['perm'], phys, d['ru'], d['ruh'],
                                             1), 'condense_hex')

@@ -280,6 +280,32 @@ hdg_status hdg_setup_precond(hdg_problem p, const hdg_solver_opts* opts, const d
  * Returns HDG_OK when every RHS met rtol, HDG_ERR_NOT_CONVERGED otherwise. */
 hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* opts, void* stream, hdg_solve_info* info);
 
+/* Restarted GMRES(m) for several problems at once (Sec. 3.1, Sec. 4.4), the
+ * batching of many small systems: ONE persistent cooperative launch runs the
+ * cycles and iterations of all `count` problems in lock-step, each phase
+ * (block-row products, block-Jacobi applies, Gram-Schmidt reductions, Givens
+ * steps, restarts with the FP64 true residual) spread over the whole GPU
+ * through ragged work lists over the problems' rows and vector entries, so
+ * systems of different meshes, orders and block sizes share every launch
+ * and no per-iteration launches remain.  Each problem's result does not
+ * depend on the others in the batch (fixed summation orders); it can differ
+ * from hdg_solve's in the last bits.  The paper solves one system at a time;
+ * this entry point has no counterpart there.
+ * Requirements: every problem assembled on the same device with
+ * hdg_setup_precond(opts) done (pc HDG_PC_NONE or HDG_PC_BJ, no
+ * polynomial), orth HDG_ORTH_CGS, and inner_prec HDG_FP64 (plain FP64) or
+ * HDG_FP32 with max_outer = -1 (the restarted mixed mode: FP32 blocks and
+ * block-Jacobi inverses in the cycles, FP64 true residual at every
+ * restart); at most 256 problems of at most 4,194,304 entries (n_dof x R)
+ * each.  The solutions stay on the device (hdg_get_trace per problem);
+ * infos (host, may be NULL) receives one hdg_solve_info per problem.
+ * Allocates a few KB of stream-ordered device memory for the work lists.
+ * Returns HDG_OK when every problem converged, HDG_ERR_NOT_CONVERGED
+ * otherwise, HDG_ERR_ARG / HDG_ERR_STATE for unsupported options or a
+ * problem not ready. */
+hdg_status hdg_solve_batch(hdg_problem* problems, int count, const hdg_solver_opts* opts, void* stream,
+                           hdg_solve_info* infos);
+
 /* Full trace uhat (host or device): n_face x b x R, Dirichlet faces filled
  * with u_D. */
 hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* stream);
@@ -290,8 +316,10 @@ hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* strea
 hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void* stream);
 
 /* y = K x with K stored in `prec` (FP64, FP32 or BF16 blocks; products
- * accumulated in FP64 for FP64 blocks, FP32 otherwise) (Sec. 4.3).  x, y:
- * device, n_dof x R doubles.  For tests and benchmarks. */
+ * accumulated in FP64 for FP64 blocks -- with R = 4 or 8 on the tensor cores
+ * through exact digit expansions, see the autotuner's configuration 6 --,
+ * FP32 otherwise) (Sec. 4.3).  x, y: device, n_dof x R doubles.  For tests
+ * and benchmarks. */
 hdg_status hdg_apply_K(hdg_problem p, int prec, const double* x, double* y, void* stream);
 
 /* y = P^{-1} x for the preconditioner of the last hdg_setup_precond call,
@@ -435,9 +463,16 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
  * copy each (evict-first in L2) into a shared-memory ring of one persistent
  * CTA per SM, 16-byte vectors of 4 (FP32) or 8 (BF16) rows per thread, the
  * columns split over the CTA's warps (units whose blocks exceed 48 KB fall
- * back to the default); cps = CTAs per SM of the grid-stride launch (0 =
- * heuristic).  Every configuration computes the same sums; they differ in
- * summation order only. */
+ * back to the default), 6 = FP64 blocks with R = 4 or 8 right-hand sides
+ * (square blocks of at most 32 rows) on the BF16 tensor cores: K kept as
+ * exact 8-digit expansions of 54-bit fixed point per row (rebuilt by every
+ * hdg_assemble, 8 bytes per entry next to the FP64 blocks), the gathered x
+ * split the same way per face row and RHS, the digit products summed exactly
+ * and the result rounded once to FP64 (error below 4 * 2^-53 * ncol *
+ * max_j |K_ij| * max_j |x_jr| over the row's ncol columns); the default for
+ * those shapes; cps = CTAs per SM of the grid-stride launch (0 =
+ * heuristic).  Every other configuration computes the same sums; they differ
+ * in summation order only. */
 
 /* Time every candidate configuration of every operation the problem can run
  * now (K at each stored precision; BJ or ASM when set up) with `reps`

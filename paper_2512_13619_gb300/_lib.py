@@ -56,6 +56,8 @@ _SIGS = {
     'hdg_assemble': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _V]),
     'hdg_setup_precond': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _P, _V]),
     'hdg_solve': (_I, [_V, ctypes.POINTER(hdg_solver_opts), _V, ctypes.POINTER(hdg_solve_info)]),
+    'hdg_solve_batch': (_I, [ctypes.POINTER(_V), _I, ctypes.POINTER(hdg_solver_opts), _V,
+                             ctypes.POINTER(hdg_solve_info)]),
     'hdg_get_trace': (_I, [_V, _P, _I, _V]),
     'hdg_recover': (_I, [_V, _P, _P, _I, _V]),
     'hdg_apply_K': (_I, [_V, _I, _P, _P, _V]),
@@ -197,6 +199,15 @@ def hdg_setup_precond(p, opts, v0, stream=None):
 
 def hdg_solve(p, opts, stream=None, info=None):
     return load().hdg_solve(p, ctypes.byref(opts), stream_ptr(stream), ctypes.byref(info) if info is not None else None)
+
+
+def hdg_solve_batch(handles, opts, stream=None):
+    """Returns (status, [hdg_solve_info per problem])."""
+    n = len(handles)
+    arr = (_V * n)(*handles)
+    infos = (hdg_solve_info * n)()
+    st = load().hdg_solve_batch(arr, n, ctypes.byref(opts), stream_ptr(stream), infos)
+    return st, list(infos)
 
 
 def hdg_get_trace(p, uhat, on_device, stream=None):

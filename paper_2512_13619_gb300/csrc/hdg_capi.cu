@@ -145,12 +145,18 @@ struct hdg_problem_s {
   int *running = nullptr, *jend = nullptr, *on_estimate = nullptr, *done = nullptr, *iters = nullptr;
   unsigned* counter = nullptr;
   int* dmaxit = nullptr;           // iteration cap read by the Givens step (cycle graphs replay it)
+  int* bdone = nullptr;            // "this system is finished" flag of the batched solve
   unsigned* d_err = nullptr;
   float* x32 = nullptr;
   // FP32 work vectors of the low-precision preconditioner (allocated on first use):
   // polynomial state (lp0, lp1, lp2), K products (ks32), the FP32 copy of the
   // GMRES iteration's K v_j (t1_32), ASM element results (ze32)
   float *lp0 = nullptr, *lp1 = nullptr, *lp2 = nullptr, *ks32 = nullptr, *t1_32 = nullptr, *ze32 = nullptr;
+  // K as exact digits for the FP64 products on the tensor cores (R = 4, 8; built by hdg_assemble)
+  unsigned char* kdig = nullptr;
+  int64_t* d_kdoff = nullptr;
+  int32_t* kex = nullptr;
+  bool kdig_ready = false;
   double *t1 = nullptr, *res = nullptr, *pq = nullptr, *pw = nullptr, *ptmp = nullptr, *pAq = nullptr,
          *pt = nullptr, *ze = nullptr, *xo = nullptr, *bo = nullptr;
   // pinned host mirrors
@@ -642,6 +648,8 @@ BrCfg cfg_of(hdg_problem p, int op, int prec) {
   return p->tune[op][prec];
 }
 
+constexpr int kMaxBatch = 256;     // systems per hdg_solve_batch call
+
 // FP32 work vectors of the low-precision preconditioner path
 void ensure_low(hdg_problem p) {
   if (p->lp0) return;
@@ -770,7 +778,10 @@ struct Ops {
     d.err = p->d_err;
     cudaEvent_t a;
     mv_timed_begin(&a);
-    blockrow(d, cfg_of(p, TUNE_K, prec), s);
+    const BrCfg cfg = cfg_of(p, TUNE_K, prec);
+    const bool tc = prec == HDG_FP64 && p->kdig_ready && (cfg.kind == BR_DEFAULT || cfg.kind == BR_TC) &&
+                    tc_blockrow(d, p->kdig, p->d_kdoff, p->kex, s);
+    if (!tc) blockrow(d, cfg, s);
     mv_timed_end(prec);
   }
   // y = M^{-1} x for the base preconditioner (x32: optional FP32 copy of x)
@@ -1031,6 +1042,7 @@ void ensure_workspace(hdg_problem p, int m) {
     p->iters = (int*)A(sizeof(int) * kMaxR);
     p->counter = (unsigned*)A(sizeof(unsigned) * 4);
     p->dmaxit = (int*)A(sizeof(int));
+    p->bdone = (int*)A(sizeof(int));
     CK(cudaMemset(p->counter, 0, sizeof(unsigned) * 4));
     CK(cudaMemset(p->d_x, 0, sizeof(double) * len));
   } else {
@@ -1536,6 +1548,7 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
   const int m = opts ? opts->restart : 50;
   by += (int64_t)(m + 12) * nfree * b * R * 8;
   by += NE * nlb * R * 8;
+  if ((R == 4 || R == 8) && b <= 32) by += nfree * ms * b * b * 8 + nfree * b * 4;   // K as digits (tensor cores)
   if (opts && opts->inner_prec != HDG_FP64)                       // FP32 vectors of the low-precision preconditioner
     by += (5 * nfree * b + NE * nlb) * R * 4;
   return (size_t)by;
@@ -1944,6 +1957,39 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
     d.ld16 = p->ld16;
     d.r = p->d_r;
     assemble(d, s);
+    // FP64 products with several right-hand sides run on the tensor cores
+    // from the blocks as exact digits (rebuilt with every assembly)
+    p->kdig_ready = false;
+    {
+      BlockRowDesc kd{};
+      kd.prec = HDG_FP64;
+      kd.R = p->R;
+      kd.b_rows = p->b;
+      kd.bc = p->b;
+      kd.max_slots = p->ms;
+      kd.epi = EPI_STORE;
+      if (tc_supported(kd) && p->nfree > 0) {
+        if (!p->kdig) {
+          std::vector<int64_t> doff(p->nfree + 1);
+          const int64_t bytes = tc_digit_layout(p->h_rowptr.data(), p->nfree, p->b, p->b, doff.data());
+          p->kdig = (unsigned char*)p->dalloc((size_t)std::max<int64_t>(bytes, 16));
+          p->kex = (int32_t*)p->dalloc(sizeof(int32_t) * p->nfree * p->b);
+          p->d_kdoff = (int64_t*)p->dalloc(sizeof(int64_t) * (p->nfree + 1));
+          CK(cudaMemcpyAsync(p->d_kdoff, doff.data(), sizeof(int64_t) * (p->nfree + 1), cudaMemcpyHostToDevice, s));
+          CK(cudaStreamSynchronize(s));        // doff is a host temporary
+        }
+        kd.blk = p->K64;
+        kd.blk_stride = p->s64;
+        kd.rowptr = p->d_rowptr;
+        kd.nbr = p->d_nbr;
+        kd.cnt = p->d_cnt;
+        kd.n_units = p->nfree;
+        kd.ld = p->b;
+        kd.err = p->d_err;
+        tc_split(kd, p->kdig, p->d_kdoff, p->kex, s);
+        p->kdig_ready = true;
+      }
+    }
     CK(cudaGetLastError());
     hdg_status st = check_err(p, s);
     if (st != HDG_OK) return st;
@@ -2164,6 +2210,151 @@ hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* o, void* stream, hdg_
   } catch (const CudaError& e) {
     return to_status(e);
   } catch (const std::bad_alloc&) {
+    return HDG_ERR_OOM;
+  }
+}
+
+hdg_status hdg_solve_batch(hdg_problem* probs, int count, const hdg_solver_opts* o, void* stream,
+                           hdg_solve_info* infos) {
+  if (!probs || !o || count < 1 || count > kMaxBatch) return HDG_ERR_ARG;
+  if (o->restart < 1 || o->restart + 1 > kMaxBasis || o->max_iters < 1 || !(o->rtol > 0.0)) return HDG_ERR_ARG;
+  if (o->poly != HDG_POLY_NONE || (o->pc != HDG_PC_NONE && o->pc != HDG_PC_BJ) || o->orth != HDG_ORTH_CGS)
+    return HDG_ERR_ARG;
+  const bool mixed = o->inner_prec != HDG_FP64;
+  if (mixed && (o->inner_prec != HDG_FP32 || o->max_outer != -1)) return HDG_ERR_ARG;
+  const int dev = probs[0] ? probs[0]->device : -1;
+  for (int i = 0; i < count; ++i) {
+    hdg_problem p = probs[i];
+    if (!p || p->device != dev) return HDG_ERR_ARG;
+    if (!p->assembled || p->pc_ready != o->pc) return HDG_ERR_STATE;
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == p) return HDG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  void* dmem = nullptr;
+  try {
+    DeviceGuard dg(dev);
+    const int m = o->restart;
+    std::vector<BatchItem> items(count);
+    std::vector<int64_t> pre(3 * count);
+    int64_t rows = 0, elems = 0, chunks = 0;
+    for (int i = 0; i < count; ++i) {
+      hdg_problem p = probs[i];
+      ensure_workspace(p, m);
+      if (mixed) ensure_low(p);
+      BatchItem& it = items[i];
+      it.len = p->ndof * p->R;
+      it.nchunks = batch_chunks(it.len);
+      if (it.nchunks > 1024) return HDG_ERR_ARG;        // the problem's reduction scratch holds 1024 chunks
+      it.b = p->b;
+      it.R = p->R;
+      it.ms = p->ms;
+      it.pc = o->pc;
+      it.kprec = mixed ? HDG_FP32 : HDG_FP64;
+      it.ld32 = p->ld32;
+      it.K64 = p->K64;
+      it.s64 = p->s64;
+      it.K32 = p->K32;
+      it.s32 = p->s32;
+      it.rowptr = p->d_rowptr;
+      it.nbr = p->d_nbr;
+      it.cnt = p->d_cnt;
+      it.bj64 = p->bj64;
+      it.bs64 = p->bs64;
+      it.bj32 = p->bj32;
+      it.bs32 = p->bs32;
+      it.rhs = p->d_r;
+      it.x = p->d_x;
+      it.res = p->res;
+      it.t1 = p->t1;
+      it.x32 = p->x32;
+      it.t32 = p->t1_32;
+      it.V = p->V;
+      it.vscale = p->vscale;
+      it.H = p->H;
+      it.g = p->g;
+      it.cs = p->cs;
+      it.sn = p->sn;
+      it.hcol = p->hcol;
+      it.htmp = p->htmp;
+      it.ycoef = p->ycoef;
+      it.part = p->partial;
+      it.bnorm = p->bnorm;
+      it.zb = p->zb;
+      it.rel = p->rel;
+      it.cfac = p->cfac;
+      it.tolabs = p->tolabs;
+      it.running = p->running;
+      it.done = p->done;
+      it.iters = p->iters;
+      it.jend = p->jend;
+      it.on_est = p->on_estimate;
+      it.done_all = p->bdone;
+      pre[i] = rows;
+      pre[count + i] = elems;
+      pre[2 * count + i] = chunks;
+      rows += p->nfree * p->b;
+      elems += it.len;
+      chunks += it.nchunks;
+    }
+    // items, prefix sums and the grid-barrier words in one stream-ordered allocation
+    const size_t items_bytes = sizeof(BatchItem) * count, pre_bytes = sizeof(int64_t) * 3 * count;
+    const size_t bar_off = (items_bytes + pre_bytes + 255) / 256 * 256;
+    CK(cudaMallocAsync(&dmem, bar_off + 256, s));
+    CK(cudaMemcpyAsync(dmem, items.data(), items_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((char*)dmem + items_bytes, pre.data(), pre_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync((char*)dmem + bar_off, 0, 256, s));
+    BatchDesc B{};
+    B.items = static_cast<BatchItem*>(dmem);
+    B.n = count;
+    B.m = m;
+    B.maxit = o->max_iters;
+    B.rtol = o->rtol;
+    B.rows_total = rows;
+    B.elems_total = elems;
+    B.chunks_total = chunks;
+    const int64_t* dpre = reinterpret_cast<const int64_t*>((char*)dmem + items_bytes);
+    B.row_pre = dpre;
+    B.elem_pre = dpre + count;
+    B.chunk_pre = dpre + 2 * count;
+    B.bar = (char*)dmem + bar_off;
+    B.err = probs[0]->d_err;
+    if (!batch_gmres(B, s)) {
+      cudaGetLastError();
+      cudaFreeAsync(dmem, s);
+      return HDG_ERR_CUDA;
+    }
+    CK(cudaFreeAsync(dmem, s));
+    dmem = nullptr;
+    hdg_status st_all = HDG_OK;
+    for (int i = 0; i < count; ++i) {
+      hdg_problem p = probs[i];
+      const int R = p->R;
+      CK(cudaMemcpyAsync(p->h_dbl, p->rel, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(p->h_int, p->iters, sizeof(int) * R, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(p->h_int + kMaxR, p->done, sizeof(int) * R, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      hdg_solve_info inf{};
+      bool conv = true;
+      for (int r = 0; r < R; ++r) {
+        inf.iters = std::max(inf.iters, p->h_int[r]);
+        inf.rel_resid = std::max(inf.rel_resid, p->h_dbl[r]);
+        conv = conv && p->h_int[kMaxR + r];
+      }
+      inf.converged = conv ? 1 : 0;
+      if (infos) infos[i] = inf;
+      if (i == 0) {
+        const hdg_status e = check_err(p, s);
+        if (e != HDG_OK) return e;
+      }
+      if (!conv && st_all == HDG_OK) st_all = HDG_ERR_NOT_CONVERGED;
+    }
+    return st_all;
+  } catch (const CudaError& e) {
+    if (dmem) cudaFreeAsync(dmem, s);
+    return to_status(e);
+  } catch (const std::bad_alloc&) {
+    if (dmem) cudaFreeAsync(dmem, s);
     return HDG_ERR_OOM;
   }
 }
@@ -2582,6 +2773,13 @@ bool tune_available(hdg_problem p, int op, int prec) {
          (prec == HDG_FP64 ? p->as64 != nullptr : prec == HDG_FP32 ? p->as32 != nullptr : p->as16 != nullptr);
 }
 
+// elements per stored block (slot) of operation op in precision prec
+int64_t stride_of(hdg_problem p, int op, int prec) {
+  if (op == TUNE_K) return prec == HDG_FP64 ? p->s64 : prec == HDG_FP32 ? p->s32 : p->s16;
+  if (op == TUNE_BJ) return prec == HDG_FP64 ? p->bs64 : prec == HDG_FP32 ? p->bs32 : p->bs16;
+  return prec == HDG_FP64 ? p->as_s64 : prec == HDG_FP32 ? p->as_s32 : p->as_s16;
+}
+
 int ld_of(hdg_problem p, int op, int prec) {
   if (op == TUNE_ASM) return prec == HDG_FP64 ? p->nlb : prec == HDG_FP32 ? ld_f32(p->nlb) : ld_bf16(p->nlb);
   return prec == HDG_FP64 ? p->b : prec == HDG_FP32 ? p->ld32 : p->ld16;
@@ -2652,11 +2850,18 @@ hdg_status hdg_autotune(hdg_problem p, int reps, int force, void* stream) {
         d.R = p->R;
         d.b_rows = key.b_rows;
         d.ld = ld_of(p, op, prec);
+        d.blk_stride = stride_of(p, op, prec);
         d.bc = p->b;
         d.max_slots = key.max_slots;
         d.in32 = p->x32;
         BrCfg cand[32];
-        const int nc = blockrow_candidates(d, cand, 32);
+        int nc = blockrow_candidates(d, cand, 32);
+        if (op == TUNE_K && prec == HDG_FP64 && p->kdig_ready && nc < 32) {
+          cand[nc].kind = BR_TC;
+          cand[nc].sp = 0;
+          cand[nc].cps = 0;
+          ++nc;
+        }
         BrCfg best;
         const float us0 = time_cfg(best);
         float bus = us0;
@@ -2692,11 +2897,18 @@ int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap) {
   d.R = p->R;
   d.b_rows = key.b_rows;
   d.ld = ld_of(p, op, prec);
+  d.blk_stride = stride_of(p, op, prec);
   d.bc = p->b;
   d.max_slots = key.max_slots;
   d.in32 = reinterpret_cast<const float*>(16);   // only tested for non-null
   BrCfg cand[32];
-  const int nc = blockrow_candidates(d, cand, 32);
+  int nc = blockrow_candidates(d, cand, 32);
+  if (op == TUNE_K && prec == HDG_FP64 && p->kdig_ready && nc < 32) {
+    cand[nc].kind = BR_TC;
+    cand[nc].sp = 0;
+    cand[nc].cps = 0;
+    ++nc;
+  }
   for (int i = 0; i < nc && i < cap && cfg3; ++i) {
     cfg3[3 * i] = cand[i].kind; cfg3[3 * i + 1] = cand[i].sp; cfg3[3 * i + 2] = cand[i].cps;
   }
@@ -2705,7 +2917,7 @@ int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap) {
 
 hdg_status hdg_set_tuning(hdg_problem p, int op, int prec, const int* cfg3) {
   if (!p || op < 0 || op > 2 || prec < 0 || prec > 2 || !cfg3) return HDG_ERR_ARG;
-  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_BULK || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
+  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_TC || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
     return HDG_ERR_ARG;
   p->tune[op][prec].kind = cfg3[0];
   p->tune[op][prec].sp = cfg3[1];

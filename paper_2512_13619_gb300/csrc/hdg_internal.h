@@ -162,7 +162,7 @@ struct BlockRowDesc {
 // row), BR_VEC (VR rows per thread, 16-byte loads, sp slot parts), BR_SPLIT
 // (sp threads per row, each summing every sp-th slot, shuffle reduction).
 // cps: CTAs per SM of the grid-stride launch (0 = heuristic).
-enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5 };
+enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5, BR_TC = 6 };
 struct BrCfg {
   int kind = BR_DEFAULT, sp = 0, cps = 0;
 };
@@ -176,6 +176,53 @@ int blockrow_candidates(const BlockRowDesc& d, BrCfg* out, int cap);
 int blockrow_variants();
 // FP64 -> FP32 copy of a vector (rounding to nearest)
 void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+
+// ------------------------------------- FP64 block rows on the tensor cores
+// FP64-accurate products of FP64 blocks with R = 4 or 8 right-hand sides on
+// the BF16 tensor cores (k_tcmv.cu), from the blocks stored as exact digits:
+// per unit u and row i an exponent ex[u * b_rows + i] and, at byte offset
+// doff[u], 8 digit bytes per entry ((k * 8 + s) * b_rows + i) * 16 + jj for
+// column 16 k + jj.  tc_digit_layout fills the host offsets (n_units + 1)
+// from the host block offsets and returns the bytes; tc_split writes the
+// digits of d's FP64 blocks; tc_blockrow runs the product (false, nothing
+// launched, when tc_supported(d) is not: FP64 blocks, R in {4, 8}, square
+// blocks of at most 32 rows, no polynomial epilogue).
+int64_t tc_digit_layout(const int64_t* h_rowptr, int64_t n_units, int b_rows, int bc, int64_t* h_doff);
+bool tc_supported(const BlockRowDesc& d);
+void tc_split(const BlockRowDesc& d, unsigned char* dig, const int64_t* doff, int32_t* ex, cudaStream_t s);
+bool tc_blockrow(const BlockRowDesc& d, const unsigned char* dig, const int64_t* doff, const int32_t* ex,
+                 cudaStream_t s);
+
+// ------------------------------------------------ batched persistent GMRES
+// One system of a batch solved by batch_gmres (k_batch.cu): its blocks,
+// preconditioner, vectors and GMRES workspace (the problem's own buffers).
+struct BatchItem {
+  int64_t len;                  // n_dof * R
+  int64_t nchunks;              // reduction chunks of len entries
+  int b, R, ms, pc, kprec, ld32;
+  const double* K64; int64_t s64;
+  const float* K32; int64_t s32;
+  const int64_t* rowptr; const int32_t* nbr; const int32_t* cnt;
+  const double* bj64; int64_t bs64;
+  const float* bj32; int64_t bs32;
+  const double* rhs; double* x; double* res; double* t1;
+  float* x32; float* t32;
+  double *V, *vscale, *H, *g, *cs, *sn, *hcol, *htmp, *ycoef, *part;
+  double *bnorm, *zb, *rel, *cfac, *tolabs;
+  int *running, *done, *iters, *jend, *on_est, *done_all;
+};
+struct BatchDesc {
+  BatchItem* items;             // device, n
+  int n, m, maxit;
+  double rtol;
+  int64_t rows_total, elems_total, chunks_total;
+  const int64_t *row_pre, *elem_pre, *chunk_pre;   // device prefix sums (n entries)
+  void* bar;                    // device grid-barrier words (zeroed before the launch)
+  unsigned* err;
+};
+int64_t batch_chunks(int64_t len);
+// one cooperative launch; false if it could not be launched
+bool batch_gmres(const BatchDesc& B, cudaStream_t s);
 
 // --------------------------------------------------------------- assembly etc.
 struct AssembleDesc {

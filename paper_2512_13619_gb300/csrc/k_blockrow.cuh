@@ -757,7 +757,7 @@ bool bulk_plan(const BlockRowDesc& d, BulkPlan* pl) {
     if (d.in32 == nullptr || d.ld % VR != 0 || d.ld < d.b_rows) return false;
     const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
     const size_t row_bytes = (size_t)d.max_slots * blk_bytes;
-    if (blk_bytes % 16 != 0 || row_bytes > kBulkStageMax) return false;
+    if (blk_bytes == 0 || blk_bytes % 16 != 0 || row_bytes > kBulkStageMax) return false;
     BulkPlan q{};
     q.NRG = d.ld / VR;
     if (q.NRG > 32) return false;

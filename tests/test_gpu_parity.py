@@ -529,3 +529,42 @@ def test_low_precision_polynomial_apply(pc, poly, deg):
     z64 = p.apply_precond(o, x, 'fp64')
     assert rel(z64, zo) < 1e-8
     p.close()
+
+
+@pytest.mark.parametrize('name', ['elast_pert_k2_R8', 'cdr_M5_R4'])
+@pytest.mark.parametrize('xkind', ['normal', 'scaled'])
+def test_tensor_core_fp64_matvec_rowwise_bound(name, xkind):
+    """The FP64 block-row product with R = 8 / 4 right-hand sides on the
+    tensor cores (K and the gathered x as exact 8-digit expansions, the
+    digit products summed exactly, the result rounded once) against the
+    oracle's FP64 product, row by row: the error stays within
+    4 * 2^-53 * ncol * max_j |K_ij| * max_j |x_jr| over the face row's
+    columns j, the error bound of the scheme (the same form as FP64
+    rounding of a dot product of ncol terms).  'scaled' gives the faces of x
+    magnitudes 10^-4 .. 10^4, so the per-row exponents of x matter."""
+    need_gpu()
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w = SMALL[name]()
+    s = OracleSystem(w)
+    p = _problem(w)
+    p.assemble(driver.opts())
+    b = s.bsz
+    nf = p.n_free
+    blocks, nbr, _ = p.face_rows()
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((p.n_dof, w.R))
+    if xkind == 'scaled':
+        x *= np.repeat(10.0 ** rng.uniform(-4, 4, size=nf), b)[:, None]
+    assert L.hdg_set_tuning(p.h, 0, 0, [6, 0, 0]) == 0          # the tensor-core kernel
+    y = p.apply_K(x, 'fp64')
+    y_ref = sparse_mv(s.K, x)
+    xb = x.reshape(nf, b, w.R)
+    for f in range(nf):
+        cols = [g for g in nbr[f] if g >= 0]
+        ncol = len(cols) * b
+        kmax = np.abs(blocks[f, :len(cols)]).max(axis=(0, 2))                 # (b,) max_j |K_ij|
+        xmax = np.abs(xb[cols]).max(axis=(0, 1))                              # (R,) max_j |x_jr|
+        bound = 4 * 2.0 ** -53 * ncol * np.outer(kmax, xmax)
+        err = np.abs(y[f * b:(f + 1) * b] - y_ref[f * b:(f + 1) * b])
+        assert np.all(err <= bound + 1e-300), (f, float((err / (bound + 1e-300)).max()))
+    p.close()

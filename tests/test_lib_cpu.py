@@ -63,6 +63,13 @@ def test_null_handles_rejected_on_host():
     for name, call in calls.items():
         assert call() == L.HDG_ERR_ARG, name
     assert L.load().hdg_workspace_bytes(None, 1, None) == 0
+    # the batched solve refuses a NULL problem in its list, an empty list and
+    # options it does not run (a polynomial preconditioner), on the host
+    assert L.hdg_solve_batch([None], o)[0] == L.HDG_ERR_ARG
+    assert L.load().hdg_solve_batch(None, 0, ctypes.byref(o), None, None) == L.HDG_ERR_ARG
+    o2 = L.hdg_solver_opts()
+    o2.restart, o2.max_iters, o2.rtol, o2.poly = 30, 100, 1e-8, L.HDG_POLY_GMRES
+    assert L.hdg_solve_batch([None], o2)[0] == L.HDG_ERR_ARG
 
 
 def test_gemm_shape_checks_on_host():
