@@ -52,8 +52,8 @@ def parse():
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-graphs', action='store_true', help='launch GMRES iterations one by one')
-    ap.add_argument('--serving-requests', type=int, default=512,
-                    help='requests of the serving stream timed beside the step (0: none)')
+    ap.add_argument('--serving-requests', type=int, default=256,
+                    help='requests of the serving stream per load point, timed beside the step (0: none)')
     ap.add_argument('--lanes', type=int, default=4, help='concurrent requests of the serving loop')
     ap.add_argument('--serving-mixed', choices=['refinement', 'restarted'], default='restarted',
                     help='mixed-precision mode of the serving solves')
@@ -70,7 +70,8 @@ def parse():
                     help='storage of K inside the Chebyshev polynomial of the mixed legs')
     ap.add_argument('--no-asm', action='store_true', help='skip the additive-Schwarz legs of the default step')
     ap.add_argument('--no-config2', action='store_true', help='skip the 16^3 Q3 Poisson leg of the default step')
-    ap.add_argument('--workload', choices=['step3', 'poisson16', 'elasticity32', 'cdr40', 'beam', 'tets', 'burgers'],
+    ap.add_argument('--workload', choices=['step3', 'poisson16', 'elasticity32', 'cdr40', 'beam', 'beamcheck', 'tets',
+                                           'burgers'],
                     default='step3',
                     help='step3: the step above (default); poisson16: the same step on the 16^3 Q3 Poisson '
                          'workload with resident element blocks; elasticity32 / cdr40: solver and kernel measurements '
@@ -836,13 +837,17 @@ def cpu_baseline3(args):
 def serving_leg(args, local):
     """The serving stream: HDG convection-diffusion requests (kappa
     log-uniform in [1e-3, 1], seeded unit velocity, n^3 hex meshes with n in
-    8..24 and Q1..Q3) arriving as a seeded Poisson process at 0.8x the
-    capacity measured on a burst of the first requests; FP32 blocks with FP64
-    refinement, BJ-GMRES(30) to 1e-8 in CUDA graphs, `lanes` requests in
-    flight on their own streams, admission by a device-memory budget.  The
-    meshes of the 51 shapes are generated before the stream starts (a request
-    names a mesh the server holds); the element blocks of each request are
-    computed from its kappa and velocity inside its latency."""
+    8..24 and Q1..Q3) arriving as a seeded Poisson process; FP32 blocks with
+    FP64 residuals at the restarts (restarted mixed mode), BJ-GMRES(30) to
+    1e-8, admission by a device-memory budget.  Two schedulers: `lanes`
+    (each request prepared and solved on its own lane's stream, GMRES cycles
+    as CUDA graphs) and `batch` (lanes prepare, every prepared request is
+    solved together in ONE persistent launch, hdg_solve_batch).  For each,
+    the capacity is measured on a burst of the first requests, then the
+    stream runs at 0.5x, 0.8x and 1.2x of it.  The meshes of the 51 shapes are
+    generated before the stream starts (a request names a mesh the server
+    holds); the element blocks of each request are computed from its kappa
+    and velocity inside its latency."""
     import numpy as np
     from hdg_inputs import workloads as W
     from paper_2512_13619_gb300 import driver
@@ -858,38 +863,48 @@ def serving_leg(args, local):
     reqs = W.serving_requests(args.serving_requests)
     for r in reqs:
         r['shape'] = (r['n'], r['k'])
-    be = HdgBackend(inputs, o, device=local)
+    shapes = sorted({r['shape'] for r in reqs})
+    probe = HdgBackend(inputs, o, device=local)
     t0 = time.perf_counter()
-    for sh in sorted({r['shape'] for r in reqs}):
-        be.slot_bytes(sh)                              # generates and caches the mesh
+    for sh in shapes:
+        probe.slot_bytes(sh)                           # generates and caches the mesh
     t_mesh = time.perf_counter() - t0
     budget = int(args.serving_budget_gb * (1 << 30))
-    srv = Server(be, lanes=args.lanes, mem_budget=budget)
-    warm_slots = 0
-    if args.serving_warm:
-        # the server holds one slot per mesh shape before requests arrive
-        warm_slots = srv.warm(sorted({r['shape'] for r in reqs}))
-    ncal = min(32, len(reqs))
-    cal = [dict(r, id=('cal', r['id'])) for r in reqs[:ncal]]
-    st_cal = srv.run(cal, np.zeros(ncal))              # burst: capacity (and first slots)
-    rate = 0.8 * st_cal['solves_per_s']
-    arr = W.poisson_arrivals(len(reqs), rate)
-    st = srv.run(reqs, arr)
-    res = [srv.results[r['id']] for r in reqs if r['id'] in srv.results]
-    srv.close()
-    its = np.array([x['iters'] for x in res]) if res else np.zeros(1)
-    rel = max([x['rel'] for x in res] + [0.0])
-    return {
-        'requests': len(reqs), 'completed': st['completed'], 'errors': st['errors'], 'lanes': args.lanes,
-        'arrival_rate_per_s': round(rate, 2), 'capacity_burst_solves_per_s': round(st_cal['solves_per_s'], 2),
-        'p50_ms': round(st['p50_ms'], 3), 'p99_ms': round(st['p99_ms'], 3), 'mean_ms': round(st['mean_ms'], 3),
-        'solves_per_s': round(st['solves_per_s'], 2),
-        'slot_creations': st['slot_creations'],       # cumulative: warm-up, calibration burst and stream
-        'evictions': st['evictions'], 'max_in_flight': st['max_in_flight'],
-        'budget_gb': args.serving_budget_gb, 'gmres_iters_mean': float(its.mean()), 'gmres_iters_max': int(its.max()),
-        'max_rel_resid': rel, 'mesh_generation_s': round(t_mesh, 2), 'warm_slots': warm_slots,
-        'solve': 'FP32 blocks, BJ-GMRES(30) to 1e-8, CUDA graphs, mixed mode: ' + args.serving_mixed,
-        'latency': 'arrival to trace in host memory (includes element-block generation on the host)'}
+    out = {'requests': len(reqs), 'lanes': args.lanes, 'budget_gb': args.serving_budget_gb,
+           'mesh_generation_s': round(t_mesh, 2),
+           'solve': 'FP32 blocks, BJ-GMRES(30) to 1e-8, mixed mode: ' + args.serving_mixed,
+           'latency': 'arrival to trace in host memory (includes element-block generation on the host)'}
+    modes = ('lanes', 'batch') if args.serving_mixed == 'restarted' else ('lanes',)
+    for mode in modes:
+        be = HdgBackend(inputs, o, device=local)
+        be._mesh_cache = probe._mesh_cache
+        srv = Server(be, lanes=args.lanes, mem_budget=budget, batch=(mode == 'batch'))
+        warm = srv.warm(shapes) if args.serving_warm else 0
+        ncal = min(32, len(reqs))
+        cal = [dict(r, id=('cal', r['id'])) for r in reqs[:ncal]]
+        st_cal = srv.run(cal, np.zeros(ncal))           # burst: capacity (and first slots)
+        cap = st_cal['solves_per_s']
+        res = {'capacity_burst_solves_per_s': round(cap, 2), 'warm_slots': warm, 'loads': {}}
+        for fac in (0.5, 0.8, 1.2):
+            tag = '%.1fx' % fac
+            rq = [dict(r, id=(tag, r['id'])) for r in reqs]
+            st = srv.run(rq, W.poisson_arrivals(len(rq), fac * cap))
+            got = [srv.results[r['id']] for r in rq if r['id'] in srv.results]
+            its = np.array([x['iters'] for x in got]) if got else np.zeros(1)
+            res['loads'][tag] = {
+                'arrival_rate_per_s': round(fac * cap, 2), 'completed': st['completed'], 'errors': st['errors'],
+                'p50_ms': round(st['p50_ms'], 3), 'p99_ms': round(st['p99_ms'], 3),
+                'mean_ms': round(st['mean_ms'], 3), 'solves_per_s': round(st['solves_per_s'], 2),
+                'gmres_iters_mean': float(its.mean()), 'max_rel_resid': max([x['rel'] for x in got] + [0.0])}
+            print('serving %s %s: %s' % (mode, tag, res['loads'][tag]), file=sys.stderr, flush=True)
+        res.update({'slot_creations': srv.creations, 'evictions': srv.evictions,
+                    'max_in_flight': srv.max_in_flight})
+        if mode == 'batch':
+            res['batches'] = srv.batches
+            res['mean_batch'] = round(float(np.mean(srv.batch_sizes)), 2) if srv.batch_sizes else None
+        srv.close()
+        out[mode] = res
+    return out
 
 
 def run_config(args, local):
@@ -1090,6 +1105,61 @@ def run_beam(args, local):
     return {'workload': 'HDG linear elasticity cantilever beam (0,5)x(0,1)^2, lambda = mu = 1, Q^k hexahedra, '
                         'clamped x = 0, traction (0,0,-1) at x = 5; GMRES(50) CGS to 1e-6',
             'data': 'synthetic', 'max_iters': maxit, 'cases': rows}
+
+
+def run_beamcheck(args, local):
+    """The Sec. 6.2 beam at N_E = 1080, k = 3 (5n x n x n with n = 6, or
+    --mesh-n): the harmonic Ritz values of the BJ-PP(10) set-up on the GPU
+    against the oracle's (Arnoldi(10) with MGS on BJ^{-1} K from the same
+    start vector, on the host), and the GPU's BJ-PP(10) GMRES(50)-CGS
+    iteration counts to 1e-6 from three seeded start vectors."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from hdg_inputs import workloads as W
+    from paper_2512_13619_gb300 import driver, _lib as L
+    from oracle import precond
+    from oracle.condense import condense_local
+    from oracle.assemble import assemble
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    n = args.mesh_n or 6
+    w = W.hex_beam(n=n, k=3)
+    hb, strides = W.shared_blocks(w)
+    p = driver.Problem.from_workload(w, local)
+    dblk = [torch.from_numpy(hb[x]).to(dev) for x in driver.BLOCK_NAMES]
+    driver.check(L.hdg_condense_strided(p.h, 0, w.n_elem, dblk, strides, 1, st), 'condense')
+    driver.check(L.hdg_set_dirichlet(p.h, w.uhat_dirichlet(), 0, st), 'dirichlet')
+    t0 = time.perf_counter()
+    full = {k: np.repeat(hb[k], w.n_elem, axis=0) if strides[i] == 0 else hb[k]
+            for i, k in enumerate(driver.BLOCK_NAMES)}
+    Kb, rb, _ = condense_local(full, w.M, w.n_lfe)
+    K, r = assemble(Kb, rb, w.mesh.elem_face, w.face_dirichlet, w.uhat_dirichlet(), w.M, w.PF)
+    Binv = precond.bj_setup(K, w.M * w.PF)
+    A = lambda v: precond.bj_apply(Binv, K @ v)
+    t_or = time.perf_counter() - t0
+    rows = []
+    for seed in (11, 12, 13):
+        v0 = w.random_vector(seed)
+        o = driver.opts(restart=50, rtol=1e-6, orth='cgs', pc='bj', poly='gmres', degree=10, max_iters=20000)
+        p.assemble(o)
+        p.setup_precond(o, v0)
+        th_gpu = p.poly()
+        th_or = precond.pp_setup(A, v0, 10)
+        key = lambda t: (round(t.real, 9), round(t.imag, 9))
+        a, b = sorted(th_gpu, key=key), sorted(th_or, key=key)
+        dev_rel = float(max(abs(x - y) for x, y in zip(a, b)) / max(abs(y) for y in b)) if len(a) == len(b) else None
+        stt, info = p.solve(o)
+        rows.append({'seed': seed, 'gmres': info.iters, 'status': L.hdg_status_str(stt), 'rel_resid': info.rel_resid,
+                     'ritz_count_gpu': len(th_gpu), 'ritz_count_oracle': len(th_or),
+                     'ritz_max_rel_diff': dev_rel, 'min_abs_ritz': float(min(abs(th_or))),
+                     'max_abs_ritz': float(max(abs(th_or)))})
+        print('beamcheck seed %d: %s' % (seed, rows[-1]), file=sys.stderr, flush=True)
+    p.close()
+    return {'workload': 'Sec. 6.2 beam, N_E = %d, Q3, BJ-PP(10) GMRES(50)-CGS to 1e-6' % w.n_elem,
+            'n_dof': int(K.shape[0]), 'oracle_setup_s': round(t_or, 1), 'seeds': rows}
 
 
 def run_tets(args, local):
@@ -1401,6 +1471,8 @@ def main():
         out = run_reference(args, ws, rank)
     elif args.workload == 'beam':
         out = run_beam(args, local)
+    elif args.workload == 'beamcheck':
+        out = run_beamcheck(args, local)
     elif args.workload == 'tets':
         out = run_tets(args, local)
     elif args.workload == 'burgers':

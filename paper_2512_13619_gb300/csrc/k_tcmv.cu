@@ -29,16 +29,16 @@
 // (t, r) as t * R + r.  One persistent CTA per SM walks the units:
 //   warps 0-3   epilogue: tensor-memory loads of both accumulator tiles
 //               (lane quadrant = warp), integer recombination, FP64 output;
-//   warps 4-7   digits of K: the stored digit bytes of two 16-column steps
+//   warps 4-11  digits of K: the stored digit bytes of two 16-column steps
 //               from the copy ring, converted to BF16 (a byte c as the bits
 //               of 128 + c, minus 128 or 192) into a ring of A stages;
-//   warps 8-11  x: per-RHS exponents of the unit's gathered columns, split
+//   warps 12-19 x: per-RHS exponents of the unit's gathered columns, split
 //               into the B operand of the whole unit (double-buffered);
-//   warp 12     tensor-memory allocation and, on one lane, the MMAs (two
+//   warp 20     tensor-memory allocation and, on one lane, the MMAs (two
 //               per 16-column step) with commits to the rings' mbarriers;
-//   warp 13     one lane copies each unit's x slots (b x R doubles each,
+//   warp 21     one lane copies each unit's x slots (b x R doubles each,
 //               through the neighbour table) into one of two x buffers;
-//   warp 14     one lane copies the digit chunks (contiguous, evict-first in
+//   warp 22     one lane copies the digit chunks (contiguous, evict-first in
 //               L2) into a ring of six stages, independently of the x copies.
 // The accumulators (8R + 6R columns) are double-buffered in tensor memory,
 // so the epilogue of one unit overlaps the products of the next.  Every wait
@@ -54,7 +54,11 @@ namespace hdg {
 
 namespace {
 
-constexpr int kTcThreads = 480;              // 15 warps
+constexpr int kAW = 256;                     // digit converters (warps 4 ..)
+constexpr int kBBase = 128 + kAW;            // first thread of the x splitters
+constexpr int kBW = 256;                     // x splitters
+constexpr int kMmaWarp = (kBBase + kBW) / 32;           // then the MMA warp and two copy warps
+constexpr int kTcThreads = kBBase + kBW + 96;           // 23 warps
 constexpr int kCK = 2;                       // 16-column steps per A stage
 constexpr int kAStages = 2;
 constexpr int kARows = 256;                  // (s, i) rows of both tiles
@@ -234,18 +238,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
   if (tid == 0) {
     for (int i = 0; i < kRawStages; ++i) {
       mbar_init(&bars->raw_full[i], 1);
-      mbar_init(&bars->raw_empty[i], 128);
+      mbar_init(&bars->raw_empty[i], kAW);
       bars->issued_raw[i] = -1;
     }
     for (int i = 0; i < kAStages; ++i) {
-      mbar_init(&bars->a_full[i], 128);
+      mbar_init(&bars->a_full[i], kAW);
       mbar_init(&bars->a_empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars->xs_full[i], 1);
-      mbar_init(&bars->xs_empty[i], 128);
+      mbar_init(&bars->xs_empty[i], kBW);
       bars->issued_xs[i] = -1;
-      mbar_init(&bars->b_full[i], 128);
+      mbar_init(&bars->b_full[i], kBW);
       mbar_init(&bars->b_empty[i], 1);
       mbar_init(&bars->d_full[i], 1);
       mbar_init(&bars->d_empty[i], 4);
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
   // A rows past b (i >= b) are never written: zero the whole ring once
   for (int o = tid * 16; o < kAStages * kAStageBytes; o += kTcThreads * 16)
     *reinterpret_cast<uint4*>(astage + o) = make_uint4(0, 0, 0, 0);
-  if (warp == 12) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tmem)),
                  "r"(kTmemCols)
                  : "memory");
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
   const uint32_t tmem = bars->tmem;
   auto nks_of = [&](int64_t u) { return (d.cnt[u] * d.bc + 15) / 16; };
 
-  if (warp == 13) {
+  if (warp == kMmaWarp + 1) {
     // ------------------------------------------------------- x slots (one lane)
     // per unit: its x slots (contiguous b x R doubles each, through the
     // neighbour table) into one of two x buffers
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
       }
     }
     __syncwarp();
-  } else if (warp == 14) {
+  } else if (warp == kMmaWarp + 2) {
     // ------------------------------------------------------- digit chunks (one lane)
     // each unit's digits (contiguous), two 16-column steps per copy,
     // evict-first in L2, into a ring of six stages
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
       }
     }
     __syncwarp();
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 4 && warp < 4 + kAW / 32) {
     // ------------------------------------------------------- digits of K: raw ring -> A stages
     const int tq = tid - 128;
     int64_t seq = 0;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
         unsigned char* dst = astage + as * kAStageBytes;
         // piece = (k, s, i): 16 stored bytes = 16 columns of digit s of row i
         const int npieces = nk * 8 * b;
-        for (int pc = tq; pc < npieces; pc += 128) {
+        for (int pc = tq; pc < npieces; pc += kAW) {
           const int i = pc % b;
           const int sd = (pc / b) & 7;
           const int kk = pc / (8 * b);
@@ -369,10 +373,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
         break;
       }
     }
-  } else if (warp >= 8 && warp < 12) {
+  } else if (warp >= kBBase / 32 && warp < (kBBase + kBW) / 32) {
     // ------------------------------------------------------- x: exponents and split
-    const int tq = tid - 256;
-    __shared__ int s_fmax[4][8];
+    const int tq = tid - kBBase;
+    __shared__ int s_fmax[kBW / 32][8];
     int64_t n = 0;
     for (int64_t u = blockIdx.x; u < d.n_units; u += gridDim.x, ++n) {
       const int ncol = d.cnt[u] * d.bc;
@@ -384,33 +388,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
         tc_give_up(bars, d.err);
         bars->bstop = 1;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kBW) : "memory");
       if (*(volatile int*)&bars->bstop) break;
       const double* xs = xsbuf + (size_t)xb * xs_elems;      // (slot, column, r) = x of column j at j * R
-      // per-RHS exponent over the columns: thread (r = tq % R) takes j = tq / R, + 128 / R, ...
+      // per-RHS exponent over the columns (integer maximum of |x| as bit
+      // patterns): thread (r = tq % R) takes j = tq / R, + kBW / R, ...
       {
         const int r = tq % R;
-        double m = 0.0;
-        for (int j = tq / R; j < ncol; j += 128 / R) m = fmax(m, fabs(xs[j * R + r]));
-        for (int o = R; o < 32; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane < R) s_fmax[tq >> 5][lane] = m > 0.0 ? tc_exponent(m) : -100000;
+        unsigned long long m = 0;
+        for (int j = tq / R; j < ncol; j += kBW / R)
+          m = max(m, (unsigned long long)__double_as_longlong(xs[j * R + r]) & 0x7FFFFFFFFFFFFFFFull);
+        for (int o = R; o < 32; o <<= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
+        const int ef = (int)(m >> 52);
+        if (lane < R) s_fmax[tq >> 5][lane] = m ? ef - 1022 : -100000;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kBW) : "memory");
       int fr[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const int a = max(max(s_fmax[0][r], s_fmax[1][r]), max(s_fmax[2][r], s_fmax[3][r]));
+        int a = -100000;
+        for (int q = 0; q < kBW / 32; ++q) a = max(a, s_fmax[q][r]);
         fr[r] = a < -90000 ? 0 : a;
       }
       if (tc_aborted(bars) || !mbar_wait_bounded(&bars->b_empty[bb], ph ^ 1u)) {
         tc_give_up(bars, d.err);
         bars->bstop = 1;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kBW) : "memory");
       if (*(volatile int*)&bars->bstop) break;
       unsigned char* bdst = bbuf + bb * b_bytes;
       // work item (8-column group jg, r): 8 values -> 8 digit planes t, 16 bytes each
-      for (int w = tq; w < (kp / 8) * R; w += 128) {
+      for (int w = tq; w < (kp / 8) * R; w += kBW) {
         const int jg = w / R, r = w - jg * R;
         unsigned dg[8][8];
 #pragma unroll
@@ -435,7 +443,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
       mbar_arrive(&bars->xs_empty[xb]);
       if (tq == 0) mbar_arrive(&bars->f_full[n & 3]);
     }
-  } else if (warp == 12) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------- MMA issue
     if (lane == 0) {
       const uint32_t idA = instr_desc(NA), idB = instr_desc(NB);
@@ -532,23 +540,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->d_empty[bb]);
+      // partials in [quadrant][r][H/L][row]: a warp's 32 lanes write 256
+      // contiguous bytes per store
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        red[((q * 32 + lane) * R + r) * 2] = H[r];
-        red[((q * 32 + lane) * R + r) * 2 + 1] = L[r];
+        red[((q * R + r) * 2) * 32 + lane] = H[r];
+        red[((q * R + r) * 2 + 1) * 32 + lane] = L[r];
       }
       asm volatile("bar.sync 2, 128;" ::: "memory");
       for (int o = tid; o < b * R; o += 128) {
-        const int i = o / R, r = o - i * R;
+        const int r = o / b, i = o - r * b;
         long long h = 0, l = 0;
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
-          h += red[((qq * 32 + i) * R + r) * 2];
-          l += red[((qq * 32 + i) * R + r) * 2 + 1];
+          h += red[((qq * R + r) * 2) * 32 + i];
+          l += red[((qq * R + r) * 2 + 1) * 32 + i];
         }
+        // (h 2^35 + l) 2^sc with one rounding, the power of two built exactly
         const int sc = ex[u * b + i] + bars->fexp[n & 3][r] - 73;
-        const double v = scalbn(fma((double)h, 34359738368.0, (double)l), sc);   // (h 2^35 + l) 2^sc
-        epi_store_tc(d, u, i, r, v);
+        const double p2 = (sc >= -1022 && sc <= 1023) ? __longlong_as_double((long long)(sc + 1023) << 52)
+                                                      : scalbn(1.0, sc);
+        epi_store_tc(d, u, i, r, fma((double)h, 34359738368.0, (double)l) * p2);
       }
       asm volatile("bar.sync 2, 128;" ::: "memory");
     }
@@ -566,7 +578,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
       if (qn >= 0) mbar_wait_bounded(&bars->xs_full[i], (unsigned)((qn >> 1) & 1));
     }
   }
-  if (warp == 12) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }

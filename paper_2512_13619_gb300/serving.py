@@ -10,6 +10,13 @@ reused by the next request of the same shape; idle slots of other shapes are
 evicted when the budget requires it.  Latency is measured from a request's
 arrival to the moment its trace is back in host memory.
 
+With `batch=True` the lanes only prepare their requests (condensation,
+assembly, preconditioner set-up on their streams), and one batching thread
+solves every prepared request together in ONE persistent launch
+(hdg_solve_batch): requests of different meshes and orders share the
+launches of every GMRES phase instead of each running its own iterations.
+Prepared requests that arrive while a batch runs form the next batch.
+
 Every numerical step runs in libhdg.so; this module only schedules.  The
 scheduler is independent of the backend (`Backend`), so its admission and
 eviction logic can be exercised without a GPU.
@@ -38,6 +45,15 @@ class Backend:
         """Returns a result object (e.g. the trace) once it is on the host."""
         raise NotImplementedError
 
+    def prepare(self, slot, request, lane):
+        """Batch mode: everything before the solve, finished when it returns."""
+        raise NotImplementedError
+
+    def solve_batch(self, items):
+        """Batch mode: solve the prepared (slot, request) pairs together;
+        returns one result per pair, on the host."""
+        raise NotImplementedError
+
     def lane_setup(self, lane):
         pass
 
@@ -53,10 +69,16 @@ class Slot:
 
 
 class Server:
-    def __init__(self, backend, lanes=4, mem_budget=64 << 30):
+    def __init__(self, backend, lanes=4, mem_budget=64 << 30, batch=False, max_batch=64):
         self.backend = backend
         self.lanes = lanes
         self.mem_budget = mem_budget
+        self.batch = batch
+        self.max_batch = max_batch
+        self.prepared = collections.deque()
+        self.preparing = 0
+        self.batches = 0
+        self.batch_sizes = []
         self.slots = []
         self.used_bytes = 0
         self.cv = threading.Condition()
@@ -117,9 +139,14 @@ class Server:
                         if sl is not None:
                             self.ready.popleft()
                             break
-                    self.cv.wait(timeout=0.05)
+                    self.cv.wait(timeout=0.01)
                 self.in_flight += 1
                 self.max_in_flight = max(self.max_in_flight, self.in_flight)
+                if self.batch:
+                    self.preparing += 1
+            if self.batch:
+                self._prepare(req, sl, lane)
+                continue
             try:
                 if sl.handle is None:
                     sl.handle = self.backend.create_slot(sl.shape, lane)
@@ -139,11 +166,77 @@ class Server:
                     self.in_flight -= 1
                     self.cv.notify_all()
 
+    def _release(self, sl):
+        """Called with self.cv held."""
+        sl.busy = False
+        sl.last_used = time.perf_counter()
+        sl.uses += 1
+        self.in_flight -= 1
+        self.cv.notify_all()
+
+    def _prepare(self, req, sl, lane):
+        ok = False
+        try:
+            if sl.handle is None:
+                sl.handle = self.backend.create_slot(sl.shape, lane)
+            self.backend.prepare(sl.handle, req, lane)
+            ok = True
+        except Exception as exc:
+            with self.cv:
+                self.errors.append((req['id'], repr(exc)))
+        with self.cv:
+            self.preparing -= 1
+            if ok:
+                self.prepared.append((req, sl))
+            else:
+                self._release(sl)
+            self.cv.notify_all()
+
+    def _batcher(self):
+        """Batch mode: solve whatever is prepared, together, until closed."""
+        while True:
+            with self.cv:
+                while not self.prepared:
+                    if self._closed and not self.ready and self.preparing == 0 and self.lanes_done == self.lanes:
+                        return
+                    self.cv.wait(timeout=0.01)
+                items = []
+                while self.prepared and len(items) < self.max_batch:
+                    items.append(self.prepared.popleft())
+            try:
+                res = self.backend.solve_batch([(sl.handle, req) for req, sl in items])
+                t = time.perf_counter()
+                with self.cv:
+                    for (req, _), r in zip(items, res):
+                        self.results[req['id']] = r
+                        self.t_done[req['id']] = t
+                    self.batches += 1
+                    self.batch_sizes.append(len(items))
+            except Exception as exc:
+                with self.cv:
+                    for req, _ in items:
+                        self.errors.append((req['id'], repr(exc)))
+            finally:
+                with self.cv:
+                    for _, sl in items:
+                        self._release(sl)
+
+    def _lane_main(self, lane):
+        try:
+            self._lane(lane)
+        finally:
+            with self.cv:
+                self.lanes_done += 1
+                self.cv.notify_all()
+
     def run(self, requests, arrivals):
         """Serve `requests` (dicts with 'id' and 'shape'), request i arriving
         arrivals[i] seconds after the start.  Returns the statistics."""
         self._closed = False
-        threads = [threading.Thread(target=self._lane, args=(i,), daemon=True) for i in range(self.lanes)]
+        self.lanes_done = 0
+        threads = [threading.Thread(target=self._lane_main, args=(i,), daemon=True) for i in range(self.lanes)]
+        if self.batch:
+            threads.append(threading.Thread(target=self._batcher, daemon=True))
         for th in threads:
             th.start()
         t0 = time.perf_counter()
@@ -173,6 +266,8 @@ class Server:
             'solves_per_s': done / span if span > 0 else None,
             'slot_creations': self.creations, 'evictions': self.evictions,
             'max_in_flight': self.max_in_flight, 'resident_bytes': self.used_bytes,
+            'batches': self.batches,
+            'mean_batch': float(np.mean(self.batch_sizes)) if self.batch_sizes else None,
         }
 
     def warm(self, shapes, per_shape=1):
@@ -248,6 +343,32 @@ class HdgBackend(Backend):
     def destroy_slot(self, slot):
         if slot.handle is not None:
             slot.handle.close()
+
+    def prepare(self, prob, request, lane):
+        L, check = self.L, self.driver.check
+        st = self.streams[lane].cuda_stream
+        _, blocks, strides, uD = self.inputs(request['shape'], request)
+        check(L.hdg_condense_strided(prob.h, 0, prob.n_elem, [blocks[k] for k in self.driver.BLOCK_NAMES],
+                                     strides, 0, st), 'condense')
+        check(L.hdg_set_dirichlet(prob.h, uD, 0, st), 'dirichlet')
+        check(L.hdg_assemble(prob.h, self.opts, st), 'assemble')
+        check(L.hdg_setup_precond(prob.h, self.opts, None, st), 'setup')
+        self.streams[lane].synchronize()
+
+    def solve_batch(self, items):
+        L, check = self.L, self.driver.check
+        if not hasattr(self, '_bstream'):
+            self.torch.cuda.set_device(self.device)
+            self._bstream = self.torch.cuda.Stream(device=self.device)
+        st = self._bstream.cuda_stream
+        s, infos = L.hdg_solve_batch([prob.h for prob, _ in items], self.opts, st)
+        check(s, 'solve_batch')
+        out = []
+        for (prob, _), info in zip(items, infos):
+            tr = np.empty((prob.n_face, prob.b, prob.R))
+            check(L.hdg_get_trace(prob.h, tr, 0, st), 'trace')
+            out.append({'trace': tr, 'iters': info.iters, 'outer': 0, 'rel': info.rel_resid})
+        return out
 
     def solve(self, prob, request, lane):
         L, check = self.L, self.driver.check
