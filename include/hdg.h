@@ -296,8 +296,8 @@ hdg_status hdg_solve(hdg_problem p, const hdg_solver_opts* opts, void* stream, h
  * polynomial), orth HDG_ORTH_CGS, and inner_prec HDG_FP64 (plain FP64) or
  * HDG_FP32 with max_outer = -1 (the restarted mixed mode: FP32 blocks and
  * block-Jacobi inverses in the cycles, FP64 true residual at every
- * restart); at most 256 problems of at most 4,194,304 entries (n_dof x R)
- * each.  The solutions stay on the device (hdg_get_trace per problem);
+ * restart); at most 256 problems of at most 2,097,152 entries (n_dof x R)
+ * and block size b <= 256 each.  The solutions stay on the device (hdg_get_trace per problem);
  * infos (host, may be NULL) receives one hdg_solve_info per problem.
  * Allocates a few KB of stream-ordered device memory for the work lists.
  * Returns HDG_OK when every problem converged, HDG_ERR_NOT_CONVERGED
@@ -470,8 +470,9 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
  * split the same way per face row and RHS, the digit products summed exactly
  * and the result rounded once to FP64 (error below 4 * 2^-53 * ncol *
  * max_j |K_ij| * max_j |x_jr| over the row's ncol columns); the default for
- * those shapes; cps = CTAs per SM of the grid-stride launch (0 =
- * heuristic).  Every other configuration computes the same sums; they differ
+ * those shapes, 7 = kind 3 compiled for three resident 256-thread CTAs per
+ * SM (at most 80 registers per thread; R = 8, sp in {1,2}; otherwise as
+ * kind 3); cps = CTAs per SM of the grid-stride launch (0 = heuristic).  Every other configuration computes the same sums; they differ
  * in summation order only. */
 
 /* Time every candidate configuration of every operation the problem can run

@@ -2236,8 +2236,8 @@ hdg_status hdg_solve_batch(hdg_problem* probs, int count, const hdg_solver_opts*
     DeviceGuard dg(dev);
     const int m = o->restart;
     std::vector<BatchItem> items(count);
-    std::vector<int64_t> pre(3 * count);
-    int64_t rows = 0, elems = 0, chunks = 0;
+    std::vector<int64_t> pre(4 * count);
+    int64_t rows = 0, elems = 0, chunks = 0, groups = 0;
     for (int i = 0; i < count; ++i) {
       hdg_problem p = probs[i];
       ensure_workspace(p, m);
@@ -2246,6 +2246,8 @@ hdg_status hdg_solve_batch(hdg_problem* probs, int count, const hdg_solver_opts*
       it.len = p->ndof * p->R;
       it.nchunks = batch_chunks(it.len);
       if (it.nchunks > 1024) return HDG_ERR_ARG;        // the problem's reduction scratch holds 1024 chunks
+      if (p->b > batch_max_b()) return HDG_ERR_ARG;     // a face's rows share one CTA
+      it.nfree = p->nfree;
       it.b = p->b;
       it.R = p->R;
       it.ms = p->ms;
@@ -2293,12 +2295,14 @@ hdg_status hdg_solve_batch(hdg_problem* probs, int count, const hdg_solver_opts*
       pre[i] = rows;
       pre[count + i] = elems;
       pre[2 * count + i] = chunks;
+      pre[3 * count + i] = groups;
       rows += p->nfree * p->b;
       elems += it.len;
       chunks += it.nchunks;
+      groups += batch_layout(p->nfree, p->b, p->ld32, p->R, mixed, &it.sp, &it.fpc);
     }
     // items, prefix sums and the grid-barrier words in one stream-ordered allocation
-    const size_t items_bytes = sizeof(BatchItem) * count, pre_bytes = sizeof(int64_t) * 3 * count;
+    const size_t items_bytes = sizeof(BatchItem) * count, pre_bytes = sizeof(int64_t) * 4 * count;
     const size_t bar_off = (items_bytes + pre_bytes + 255) / 256 * 256;
     CK(cudaMallocAsync(&dmem, bar_off + 256, s));
     CK(cudaMemcpyAsync(dmem, items.data(), items_bytes, cudaMemcpyHostToDevice, s));
@@ -2313,13 +2317,17 @@ hdg_status hdg_solve_batch(hdg_problem* probs, int count, const hdg_solver_opts*
     B.rows_total = rows;
     B.elems_total = elems;
     B.chunks_total = chunks;
+    B.groups_total = groups;
     const int64_t* dpre = reinterpret_cast<const int64_t*>((char*)dmem + items_bytes);
     B.row_pre = dpre;
     B.elem_pre = dpre + count;
     B.chunk_pre = dpre + 2 * count;
+    B.group_pre = dpre + 3 * count;
     B.bar = (char*)dmem + bar_off;
     B.err = probs[0]->d_err;
-    if (!batch_gmres(B, s)) {
+    int rmax = 1;
+    for (int i = 0; i < count; ++i) rmax = std::max(rmax, probs[i]->R);
+    if (!batch_gmres(B, rmax, s)) {
       cudaGetLastError();
       cudaFreeAsync(dmem, s);
       return HDG_ERR_CUDA;
@@ -2917,7 +2925,7 @@ int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap) {
 
 hdg_status hdg_set_tuning(hdg_problem p, int op, int prec, const int* cfg3) {
   if (!p || op < 0 || op > 2 || prec < 0 || prec > 2 || !cfg3) return HDG_ERR_ARG;
-  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_TC || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
+  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_VEC3 || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
     return HDG_ERR_ARG;
   p->tune[op][prec].kind = cfg3[0];
   p->tune[op][prec].sp = cfg3[1];

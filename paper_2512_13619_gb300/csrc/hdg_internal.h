@@ -162,7 +162,7 @@ struct BlockRowDesc {
 // row), BR_VEC (VR rows per thread, 16-byte loads, sp slot parts), BR_SPLIT
 // (sp threads per row, each summing every sp-th slot, shuffle reduction).
 // cps: CTAs per SM of the grid-stride launch (0 = heuristic).
-enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5, BR_TC = 6 };
+enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5, BR_TC = 6, BR_VEC3 = 7 };
 struct BrCfg {
   int kind = BR_DEFAULT, sp = 0, cps = 0;
 };
@@ -199,7 +199,9 @@ bool tc_blockrow(const BlockRowDesc& d, const unsigned char* dig, const int64_t*
 struct BatchItem {
   int64_t len;                  // n_dof * R
   int64_t nchunks;              // reduction chunks of len entries
+  int64_t nfree;                // trace face rows
   int b, R, ms, pc, kprec, ld32;
+  int sp, fpc;                  // fused K / block-Jacobi step: slot parts of a face row, faces per CTA
   const double* K64; int64_t s64;
   const float* K32; int64_t s32;
   const int64_t* rowptr; const int32_t* nbr; const int32_t* cnt;
@@ -215,14 +217,18 @@ struct BatchDesc {
   BatchItem* items;             // device, n
   int n, m, maxit;
   double rtol;
-  int64_t rows_total, elems_total, chunks_total;
-  const int64_t *row_pre, *elem_pre, *chunk_pre;   // device prefix sums (n entries)
+  int64_t rows_total, elems_total, chunks_total, groups_total;   // groups: whole faces per CTA
+  const int64_t *row_pre, *elem_pre, *chunk_pre, *group_pre;     // device prefix sums (n entries)
   void* bar;                    // device grid-barrier words (zeroed before the launch)
   unsigned* err;
 };
 int64_t batch_chunks(int64_t len);
+// fused-step layout of one system (b <= batch_max_b()): slot parts and faces
+// per CTA; returns the number of face groups
+int64_t batch_layout(int64_t nfree, int b, int ld32, int R, bool f32, int* sp, int* fpc);
+int batch_max_b();
 // one cooperative launch; false if it could not be launched
-bool batch_gmres(const BatchDesc& B, cudaStream_t s);
+bool batch_gmres(const BatchDesc& B, int rmax, cudaStream_t s);   // rmax: the largest R of the batch
 
 // --------------------------------------------------------------- assembly etc.
 struct AssembleDesc {

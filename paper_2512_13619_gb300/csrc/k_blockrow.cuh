@@ -415,8 +415,10 @@ template <> struct Vec16<__nv_bfloat16> {
 // Thread (unit, row group rg, slot part sp): rows rg*VR..rg*VR+VR-1, slots
 // sp, sp+SP, ...; the SP slot parts of a row group are adjacent lanes and
 // combine their sums with shuffles.  SP in {1, 2, 4, 8}; (ld / VR) * SP <= 256.
-template <typename T, int R, int BC, int SP>
-__global__ void __launch_bounds__(288) blockrow_vec_kernel(BlockRowDesc d, int G) {
+// MINB = 3 compiles for three resident CTAs of 256 threads per SM (at most 80
+// registers), more loads in flight per SM at R = 8.
+template <typename T, int R, int BC, int SP, int MINB = 1>
+__global__ void __launch_bounds__(MINB > 1 ? 256 : 288, MINB) blockrow_vec_kernel(BlockRowDesc d, int G) {
   constexpr int VR = Vec16<T>::N;
   if (!any_active(d.active, R)) return;
   const int tpu = (d.ld / VR) * SP;              // threads per unit; G units per CTA,
@@ -818,7 +820,7 @@ int pick_nt_direct(int b_rows) {
   return best;
 }
 
-template <typename T, int R, int BC, int SP>
+template <typename T, int R, int BC, int SP, int MINB = 1>
 void launch_vec_sp(const BlockRowDesc& d, int cps, cudaStream_t s) {
   constexpr int VR = Vec16<T>::N;
   const int tpu = (d.ld / VR) * SP;
@@ -827,16 +829,23 @@ void launch_vec_sp(const BlockRowDesc& d, int cps, cudaStream_t s) {
   int64_t ngroups = (d.n_units + G - 1) / G;
   int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * (cps > 0 ? cps : 16));
   if (grid < 1) grid = 1;
-  count_launch(); blockrow_vec_kernel<T, R, BC, SP><<<(unsigned)grid, NT, 0, s>>>(d, G);
+  count_launch(); blockrow_vec_kernel<T, R, BC, SP, MINB><<<(unsigned)grid, NT, 0, s>>>(d, G);
 }
 
 // A shuffle group is SP adjacent lanes starting at a multiple of SP, so it
 // never straddles a warp.  Heuristic: 4 parts for rows of several slots
 // (matvec, ASM), 1 for one slot (BJ).
 template <typename T, int R, int BC>
-void launch_vec(const BlockRowDesc& d, int sp, int cps, cudaStream_t s) {
+void launch_vec(const BlockRowDesc& d, int sp, int cps, bool occ3, cudaStream_t s) {
   if (sp <= 0) sp = d.max_slots >= 4 ? 4 : d.max_slots >= 2 ? 2 : 1;
   while (sp > 1 && (d.ld / Vec16<T>::N) * sp > 256) sp >>= 1;   // threads per unit <= 256
+  if constexpr (R == 8) {
+    if (occ3 && sp <= 2) {
+      if (sp == 1) launch_vec_sp<T, R, BC, 1, 3>(d, cps, s);
+      else launch_vec_sp<T, R, BC, 2, 3>(d, cps, s);
+      return;
+    }
+  }
   switch (sp) {
     case 1: launch_vec_sp<T, R, BC, 1>(d, cps, s); break;
     case 2: launch_vec_sp<T, R, BC, 2>(d, cps, s); break;
@@ -898,8 +907,8 @@ void launch_direct_bc(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
     if (cfg.kind == BR_BULK && launch_bulk<T, R, BC>(d, s)) return;
   }
   if constexpr (!std::is_same<T, double>::value && BC > 0) {
-    if ((cfg.kind == BR_DEFAULT || cfg.kind == BR_VEC) && vec_ok<T>(d)) {
-      launch_vec<T, R, BC>(d, cfg.sp, cfg.cps, s);
+    if ((cfg.kind == BR_DEFAULT || cfg.kind == BR_VEC || cfg.kind == BR_VEC3) && vec_ok<T>(d)) {
+      launch_vec<T, R, BC>(d, cfg.sp, cfg.cps, cfg.kind == BR_VEC3, s);
       return;
     }
   }
@@ -980,6 +989,10 @@ int candidates_T(const BlockRowDesc& d, BrCfg* out, int cap) {
       for (int sp : {1, 2, 4, 8})
         if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
           for (int cps : {8, 16, 32}) add(BR_VEC, sp, cps);
+      if (d.R == 8)
+        for (int sp : {1, 2})
+          if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
+            for (int cps : {16, 32}) add(BR_VEC3, sp, cps);
       BulkPlan bp;
       if ((d.bc == 9 || d.bc == 16 || d.bc == 20 || d.bc == 27) && d.R >= 4 && bulk_plan<T>(d, &bp))
         add(BR_BULK, 0, 0);

@@ -22,7 +22,9 @@ def _systems():
             (W.hex_convdiff(4, 2, 0.5, (0.0, 0.6, 0.8)), 'cd n4 k2'),
             (W.hex_convdiff(3, 3, 0.01, (0.6, 0.0, -0.8)), 'cd n3 k3'),
             (W.hex_convdiff(5, 1, 1.0, (0.0, 0.0, 1.0)), 'cd n5 k1'),
-            (W.hex_elasticity(n=2, k=1, R=2), 'elast n2 k1 R2')]
+            (W.hex_elasticity(n=2, k=1, R=2), 'elast n2 k1 R2'),
+            # several 2048-entry reduction chunks with a ragged tail, many face groups
+            (W.hex_convdiff(8, 2, 0.2, (0.8, 0.6, 0.0)), 'cd n8 k2')]
 
 
 @pytest.fixture(scope='module')
@@ -62,12 +64,15 @@ def test_batch_alone_equals_batched_and_meets_oracle(setup, mode):
         assert np.array_equal(xa, xb), label               # bitwise: alone == in the batch
         assert inf.iters == ita and inf.converged == 1, label
         # against the oracle: true FP64 residual with the oracle's K, error vs its direct solve
-        xd = s.direct()
-        xd = xd[:, None] if xd.ndim == 1 else xd
-        cond = np.linalg.cond(s.K.toarray())
         res = s.r - sparse_mv(s.K, xb)
         for r in range(w.R):
             assert np.linalg.norm(res[:, r]) / np.linalg.norm(s.r[:, r]) <= rtol, (label, r)
+        if s.K.shape[0] > 4000:
+            continue                                       # the dense condition number is too slow
+        xd = s.direct()
+        xd = xd[:, None] if xd.ndim == 1 else xd
+        cond = np.linalg.cond(s.K.toarray())
+        for r in range(w.R):
             assert np.linalg.norm(xb[:, r] - xd[:, r]) / np.linalg.norm(xd[:, r]) <= cond * rtol, (label, r)
 
 
