@@ -100,6 +100,49 @@ def parse():
     return ap.parse_args()
 
 
+# Sources of the FP32 block-row kernel (R = 8) whose DRAM traffic a committed
+# ncu summary records; the summary's figure is reported only while these files
+# hash to the value recorded beside it.
+TRAFFIC_SOURCES = ['paper_2512_13619_gb300/csrc/k_blockrow.cuh', 'paper_2512_13619_gb300/csrc/k_blockrow_f32_wide.cu',
+                   'paper_2512_13619_gb300/csrc/k_poly.cuh', 'paper_2512_13619_gb300/csrc/hdg_common.cuh']
+TRAFFIC_SUMMARY = 'profiles/blockrow_vec_fp32_elasticity_32_q2_r8_traffic.md'
+
+
+def sources_sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for rel in paths:
+        with open(os.path.join(root, rel), 'rb') as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(cfg):
+    """DRAM bytes (read + write) per launch of the FP32 block-row kernel on
+    the 32^3 elasticity workload from the committed ncu summary, or None when
+    the summary is absent, was taken with another configuration, or the
+    kernel's sources changed since."""
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(root, TRAFFIC_SUMMARY)).read()
+    except OSError:
+        return None, 'no ncu summary'
+    rec = {}
+    for line in text.splitlines():
+        if line.startswith('traffic_record:'):
+            for tok in line.split()[1:]:
+                k, _, v = tok.partition('=')
+                rec[k] = v
+    if not rec:
+        return None, 'no record in the ncu summary'
+    if rec.get('cfg') != ','.join(str(c) for c in cfg):
+        return None, 'tuned configuration %s differs from the profiled %s' % (list(cfg), rec.get('cfg'))
+    if rec.get('sources_sha256') != sources_sha256(TRAFFIC_SOURCES):
+        return None, 'kernel sources changed since the ncu capture'
+    return int(rec['dram_bytes_per_launch']), TRAFFIC_SUMMARY
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
@@ -656,10 +699,12 @@ def run_step3(args, ws, rank, local):
     tot_by = by32 * n32 + by16 * n16
     tot_ms = t32 + t16
     achieved = tot_by / tot_ms / 1e6 if tot_ms > 0 else 0.0
+    _, cfg32, _, _ = L.hdg_get_tuning(p.h, 0, 1)
+    traffic, traffic_src = profiled_traffic(cfg32) if not n16 else (None, 'BF16 launches in the step')
     roof = {'kernel': 'blockrow_vec_kernel (face-block matvec y = K x, R = 8, FP32%s blocks, FP32 accumulation)'
                       % (' and BF16' if n16 else ''),
             'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': pk['hbm_gbs'], 'unit': 'GB/s',
-            'frac': round(achieved / pk['hbm_gbs'], 4), 'traffic': None,
+            'frac': round(achieved / pk['hbm_gbs'], 4), 'traffic': traffic, 'traffic_source': traffic_src,
             'bytes_per_launch': {'fp32': int(by32), 'bf16': int(by16)},
             'launches_in_step': int(n32 + n16), 'ms_in_step': round(tot_ms, 3),
             'timing': 'CUDA events around every block-row launch of K in one mixed step run launch by launch',
@@ -1398,6 +1443,9 @@ def run_profile(args):
             print('profile run done')
             return
         for it in range(2):
+            if it == 1:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push('step2')        # the whole second step
             driver.check(L.hdg_condense_hex(p.h, 0, w.n_elem, nquad, d['verts'], d['perm'], phys, d['ru'], d['ruh'],
                                             1), 'condense_hex')
             p.set_dirichlet(np.zeros((w.n_face, w.M * w.PF, w.R)))
@@ -1413,6 +1461,9 @@ def run_profile(args):
                 torch.cuda.nvtx.range_pop()
             driver.check(st, 'solve')
             p.recover()
+            if it == 1:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         print('iterations', info.iters)
         p.close()

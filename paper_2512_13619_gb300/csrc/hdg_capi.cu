@@ -421,9 +421,15 @@ InSizes in_sizes(hdg_problem p) {
   s.total = s.Me + s.Bd + s.Cd + s.D + s.E + s.F + s.G + s.H + s.J + s.ru + s.ruh;
   return s;
 }
-int64_t tmp_per_elem(hdg_problem p) {
-  return (int64_t)p->PE * p->PE + (int64_t)p->MPE * p->MPE + (int64_t)p->MPE * p->nlb + (int64_t)p->nlb * p->MPE;
+// Condensation scratch per element (doubles): M^{-1}, Ebar, [Fbar | r_u],
+// Hbar, [X_F | X_r], [Jbar - Hbar X_F | rbar]  (the last three with nlb + R
+// columns, so that the right-hand-side columns ride in the same products).
+int64_t tmp_elems(int64_t PE, int64_t MPE, int64_t nlb, int64_t R) {
+  return PE * PE + MPE * MPE + MPE * (nlb + R) + nlb * MPE + MPE * (nlb + R) + nlb * (nlb + R);
 }
+int64_t tmp_per_elem(hdg_problem p) { return tmp_elems(p->PE, p->MPE, p->nlb, p->R); }
+// device bytes of one condensation chunk (inputs + scratch)
+constexpr int64_t kChunkBudget = 3ll << 29;   // 1.5 GiB
 
 GemmDesc gd(int M, int N, int K, const double* A, int64_t lda, int64_t sA0, int64_t sA1, const double* B,
             int64_t ldb, int64_t sB0, int64_t sB1, double* C, int64_t ldc, int64_t sC0, int64_t sC1, double alpha,
@@ -496,7 +502,10 @@ void gemm_c(hdg_problem p, const GemmDesc& d, cudaStream_t s) {
       if (ok) return;
     }
   }
-  if (p->condense_mode >= 1 && gemm_ozaki_scratch(d) <= p->oz_cap && d.N >= 16 &&
+  // Products of at most 32 rows fill a quarter or less of the 128-row
+  // tensor-core tile; measured on the condensation shapes (M = 9, 27) the FP64
+  // pipe is faster for them.
+  if (p->condense_mode >= 1 && d.M > 32 && gemm_ozaki_scratch(d) <= p->oz_cap && d.N >= 16 &&
       (d.K <= 192 || p->condense_mode == 1)) {
     timed_begin(p, s);
     if (p->condense_mode == 3) gemm_ozaki_persist(d, p->d_oz, p->oz_cap, p->d_err, s);
@@ -584,10 +593,13 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
   const int PE = p->PE, D = p->D, M = p->M, PF = p->PF, MPE = p->MPE, MDPE = p->MDPE, nlb = p->nlb,
             nlPF = p->nlPF, R = p->R;
   const int n = (int)ec;
+  const int nlbR = nlb + R;
   double* Minv = p->d_tmp;
   double* Eb = Minv + ec * PE * PE;
-  double* Fb = Eb + ec * MPE * MPE;
-  double* Hb = Fb + ec * MPE * nlb;
+  double* Fb = Eb + ec * MPE * MPE;                 // [Fbar | r_u], MPE x nlbR
+  double* Hb = Fb + ec * MPE * nlbR;
+  double* XFr = Hb + ec * nlb * MPE;                // [X_F | X_r], MPE x nlbR
+  double* Kr = XFr + ec * MPE * nlbR;               // [Kbar | rbar], nlb x nlbR
   double* MinvB = p->d_MinvB + e0 * D * PE * PE;
   double* MinvC = p->d_MinvC + e0 * D * PE * nlPF;
   double* XF = p->d_XF + e0 * MPE * nlb;
@@ -611,30 +623,31 @@ void condense_chunk(hdg_problem p, int64_t e0, int64_t ec, const double* Me, con
   copy_in(Eb, Em, (int64_t)MPE * MPE, ec, sh[4], s);
   gemm_c(p, gd(MPE, PE, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Eb, MPE,
               (int64_t)MPE * MPE, PE, -1.0, 1.0, n, M), s);
-  // Fbar = F - D A^{-1} C, output columns (l, b, j)
-  copy_in(Fb, Fm, (int64_t)MPE * nlb, ec, sh[5], s);
-  gemm_c(p, gd(MPE, nlPF, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Fb, nlb,
-              (int64_t)MPE * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
+  // Fbar = F - D A^{-1} C, output columns (l, b, j); r_u beside it
+  copy_block_f64(Fb, nlbR, (int64_t)MPE * nlbR, Fm, nlb, sh[5] ? 0 : (int64_t)MPE * nlb, MPE, nlb, ec, s);
+  copy_block_f64(Fb + nlb, nlbR, (int64_t)MPE * nlbR, ru, R, sru, MPE, R, ec, s);
+  gemm_c(p, gd(MPE, nlPF, D * PE, Dm, MDPE, sD, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Fb, nlbR,
+              (int64_t)MPE * nlbR, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
   // Hbar = H - G A^{-1} B                                       (Eq. w21)
   copy_in(Hb, Hm, (int64_t)nlb * MPE, ec, sh[7], s);
   gemm_c(p, gd(nlb, PE, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvB, PE, (int64_t)D * PE * PE, 0, Hb, MPE,
               (int64_t)nlb * MPE, PE, -1.0, 1.0, n, M), s);
-  // Jbar = J - G A^{-1} C  (written into Kbar)
-  copy_in(Kb, Jm, (int64_t)nlb * nlb, ec, sh[8], s);
-  gemm_c(p, gd(nlb, nlPF, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Kb, nlb,
-              (int64_t)nlb * nlb, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
-  // Ebar^{-1}; X_F = Ebar^{-1} Fbar; X_r = Ebar^{-1} r_u
+  // Jbar = J - G A^{-1} C, r_uh beside it
+  copy_block_f64(Kr, nlbR, (int64_t)nlb * nlbR, Jm, nlb, sh[8] ? 0 : (int64_t)nlb * nlb, nlb, nlb, ec, s);
+  copy_block_f64(Kr + nlb, nlbR, (int64_t)nlb * nlbR, ruh, R, sh[10] ? 0 : (int64_t)nlb * R, nlb, R, ec, s);
+  gemm_c(p, gd(nlb, nlPF, D * PE, Gm, MDPE, sG, (int64_t)D * PE, MinvC, nlPF, (int64_t)D * PE * nlPF, 0, Kr, nlbR,
+              (int64_t)nlb * nlbR, PF, -1.0, 1.0, n, M, PF, (int64_t)M * PF), s);
+  // Ebar^{-1}; [X_F | X_r] = Ebar^{-1} [Fbar | r_u]
   inverse_any(p, Eb, MPE, (int64_t)MPE * MPE, ec, s);
-  gemm_c(p, gd(MPE, nlb, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlb, (int64_t)MPE * nlb, 0, XF, nlb,
-              (int64_t)MPE * nlb, 0, 1.0, 0.0, n, 1), s);
-  gemm_c(p, gd(MPE, R, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, ru, R, sru, 0, Xr, R, (int64_t)MPE * R, 0, 1.0, 0.0, n, 1),
-           s);
-  // Kbar = Jbar - Hbar X_F ; rbar = r_uh - Hbar X_r              (Eq. w22)
-  gemm_c(p, gd(nlb, nlb, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, XF, nlb, (int64_t)MPE * nlb, 0, Kb, nlb,
-              (int64_t)nlb * nlb, 0, -1.0, 1.0, n, 1), s);
-  copy_in(rb, ruh, (int64_t)nlb * R, ec, sh[10], s);
-  gemm_c(p, gd(nlb, R, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, Xr, R, (int64_t)MPE * R, 0, rb, R, (int64_t)nlb * R, 0,
-              -1.0, 1.0, n, 1), s);
+  gemm_c(p, gd(MPE, nlbR, MPE, Eb, MPE, (int64_t)MPE * MPE, 0, Fb, nlbR, (int64_t)MPE * nlbR, 0, XFr, nlbR,
+              (int64_t)MPE * nlbR, 0, 1.0, 0.0, n, 1), s);
+  // [Kbar | rbar] = [Jbar | r_uh] - Hbar [X_F | X_r]            (Eq. w22)
+  gemm_c(p, gd(nlb, nlbR, MPE, Hb, MPE, (int64_t)nlb * MPE, 0, XFr, nlbR, (int64_t)MPE * nlbR, 0, Kr, nlbR,
+              (int64_t)nlb * nlbR, 0, -1.0, 1.0, n, 1), s);
+  copy_block_f64(XF, nlb, (int64_t)MPE * nlb, XFr, nlbR, (int64_t)MPE * nlbR, MPE, nlb, ec, s);
+  copy_block_f64(Xr, R, (int64_t)MPE * R, XFr + nlb, nlbR, (int64_t)MPE * nlbR, MPE, R, ec, s);
+  copy_block_f64(Kb, nlb, (int64_t)nlb * nlb, Kr, nlbR, (int64_t)nlb * nlbR, nlb, nlb, ec, s);
+  copy_block_f64(rb, R, (int64_t)nlb * R, Kr + nlb, nlbR, (int64_t)nlb * nlbR, nlb, R, ec, s);
 }
 
 // ------------------------------------------------------------------ operators
@@ -1459,7 +1472,7 @@ hdg_status hdg_problem_create(const hdg_mesh* mesh, int nrhs, int device, hdg_pr
     p->condensed.assign(p->NE, 0);
     // condensation chunk: inputs + temporaries of ~1 GiB
     const int64_t per = in_sizes(p).total + tmp_per_elem(p);
-    int64_t ch = (int64_t)((1ll << 30) / (per * 8));
+    int64_t ch = (int64_t)(kChunkBudget / (per * 8));
     ch = std::max<int64_t>(1, std::min<int64_t>(ch, p->NE));
     p->chunk = ch;
     p->chunk_cap = ch;
@@ -1528,8 +1541,8 @@ size_t hdg_workspace_bytes(const hdg_mesh* mesh, int nrhs, const hdg_solver_opts
     const int64_t MDPE = MPE * D, nlPF = nl * mesh->PF;
     const int64_t in_total = PE * PE + D * PE * PE + D * PE * nlPF + MPE * MDPE + MPE * MPE + MPE * nlb +
                              nlb * MDPE + nlb * MPE + nlb * nlb + MPE * R + nlb * R;
-    const int64_t tmp = PE * PE + MPE * MPE + MPE * nlb + nlb * MPE;
-    const int64_t ch = std::max<int64_t>(1, std::min<int64_t>((1ll << 30) / ((in_total + tmp) * 8), NE));
+    const int64_t tmp = tmp_elems(PE, MPE, nlb, R);
+    const int64_t ch = std::max<int64_t>(1, std::min<int64_t>(kChunkBudget / ((in_total + tmp) * 8), NE));
     by += ch * (in_total + tmp) * 8 + (16ll << 20);               // + small per-call buffers
     if (NE > ch) by += ch * in_total * 8;                          // second staging buffer (host inputs)
     // exponents of the tensor-core products (16-bit, as hdg_problem_create sizes them)

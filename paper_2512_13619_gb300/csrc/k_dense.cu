@@ -260,14 +260,18 @@ __global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int 
 size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)n * 4 + 16; }
 
 // dst[c][i][j] = src[c][i][j] for i < rows, j < cols (row-major, leading
-// dimensions ldd / lds, batch strides sd / ss); one CTA row per (c, i).
+// dimensions ldd / lds, batch strides sd / ss): one thread per entry over the
+// flattened (c, i, j) range, so consecutive threads move consecutive entries
+// of a row, whatever its width.
 __global__ void copy_block_kernel(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss,
-                                  int rows, int cols) {
-  const int64_t c = blockIdx.y;
-  const int i = blockIdx.x;
-  const double* a = src + c * ss + (int64_t)i * lds;
-  double* o = dst + c * sd + (int64_t)i * ldd;
-  for (int j = threadIdx.x; j < cols; j += blockDim.x) o[j] = a[j];
+                                  int rows, int cols, int64_t total) {
+  const int64_t per = (int64_t)rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / per;
+    const int64_t rem = t - c * per;
+    const int64_t i = rem / cols, j = rem - i * cols;
+    dst[c * sd + i * ldd + j] = src[c * ss + i * lds + j];
+  }
 }
 
 }  // namespace
@@ -275,13 +279,10 @@ __global__ void copy_block_kernel(double* dst, int64_t ldd, int64_t sd, const do
 void copy_block_f64(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss, int rows,
                     int cols, int64_t count, cudaStream_t s) {
   if (rows <= 0 || cols <= 0 || count <= 0) return;
-  const int threads = cols >= 128 ? 128 : (cols >= 64 ? 64 : 32);
-  for (int64_t c0 = 0; c0 < count; c0 += 65535) {
-    const int64_t c = count - c0 < 65535 ? count - c0 : 65535;
-    count_launch();
-    copy_block_kernel<<<dim3((unsigned)rows, (unsigned)c), threads, 0, s>>>(dst + c0 * sd, ldd, sd, src + c0 * ss,
-                                                                          lds, ss, rows, cols);
-  }
+  const int64_t total = count * rows * cols;
+  const int64_t grid = std::min<int64_t>((total + 255) / 256, 4096);   // grid-stride beyond
+  count_launch();
+  copy_block_kernel<<<(unsigned)grid, 256, 0, s>>>(dst, ldd, sd, src, lds, ss, rows, cols, total);
 }
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {

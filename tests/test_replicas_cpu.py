@@ -53,3 +53,22 @@ def test_single_process_max_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(4.5) == 4.5
+
+
+def test_profiled_traffic_only_for_unchanged_kernel(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from the committed ncu summary only
+    while the tuned configuration and the kernel's sources are the ones the
+    capture was taken with."""
+    import bench
+    h = bench.sources_sha256(bench.TRAFFIC_SOURCES)
+    summ = tmp_path / 'summary.md'
+    summ.write_text('# summary\n\ntraffic_record: cfg=7,1,32 dram_bytes_per_launch=123456 sources_sha256=%s\n' % h)
+    monkeypatch.setattr(bench, 'TRAFFIC_SUMMARY', str(summ))
+    assert bench.profiled_traffic((7, 1, 32)) == (123456, str(summ))
+    v, why = bench.profiled_traffic((3, 1, 32))
+    assert v is None and 'configuration' in why
+    summ.write_text('traffic_record: cfg=7,1,32 dram_bytes_per_launch=123456 sources_sha256=%s\n' % ('0' * 64))
+    v, why = bench.profiled_traffic((7, 1, 32))
+    assert v is None and 'changed' in why
+    monkeypatch.setattr(bench, 'TRAFFIC_SUMMARY', str(tmp_path / 'absent.md'))
+    assert bench.profiled_traffic((7, 1, 32))[0] is None
