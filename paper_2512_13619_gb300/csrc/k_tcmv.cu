@@ -29,11 +29,13 @@
 // (t, r) as t * R + r.  One persistent CTA per SM walks the units:
 //   warps 0-3   epilogue: tensor-memory loads of both accumulator tiles
 //               (lane quadrant = warp), integer recombination, FP64 output;
-//   warps 4-11  digits of K: the stored digit bytes of two 16-column steps
+//   warps 4-7   digits of K: the stored digit bytes of two 16-column steps
 //               from the copy ring, converted to BF16 (a byte c as the bits
-//               of 128 + c, minus 128 or 192) into a ring of A stages;
-//   warps 12-19 x: per-RHS exponents of the unit's gathered columns, split
-//               into the B operand of the whole unit (double-buffered);
+//               of 128 + c, minus 128 or 192) into a ring of A stages; a
+//               thread owns up to two (digit, row) pairs for the whole kernel;
+//   warps 8-19  x: per-RHS exponents of the unit's gathered columns, split
+//               into the B operand of the whole unit (double-buffered); a
+//               thread keeps one RHS;
 //   warp 20     tensor-memory allocation and, on one lane, the MMAs (two
 //               per 16-column step) with commits to the rings' mbarriers;
 //   warp 21     one lane copies each unit's x slots (b x R doubles each,
@@ -54,9 +56,9 @@ namespace hdg {
 
 namespace {
 
-constexpr int kAW = 256;                     // digit converters (warps 4 ..)
+constexpr int kAW = 128;                     // digit converters (warps 4 ..)
 constexpr int kBBase = 128 + kAW;            // first thread of the x splitters
-constexpr int kBW = 256;                     // x splitters
+constexpr int kBW = 384;                     // x splitters
 constexpr int kMmaWarp = (kBBase + kBW) / 32;           // then the MMA warp and two copy warps
 constexpr int kTcThreads = kBBase + kBW + 96;           // 23 warps
 constexpr int kCK = 2;                       // 16-column steps per A stage
@@ -337,7 +339,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
     __syncwarp();
   } else if (warp >= 4 && warp < 4 + kAW / 32) {
     // ------------------------------------------------------- digits of K: raw ring -> A stages
+    // thread tq < 8 b owns digit sd of row i for the whole kernel (raw piece
+    // (kk, sd, i) at ((kk * 8 + sd) * b + i) * 16 bytes), so only the column
+    // step moves its source and destination
     const int tq = tid - 128;
+    int npc = 0;                       // (digit, row) pairs of this thread: tq, tq + kAW
+    uint32_t drow[2] = {0u, 0u};
+    bool lead[2] = {false, false};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int pr = tq + h * kAW;
+      if (pr < 8 * b) {
+        const int sd = pr / b, ci = pr - sd * b;
+        drow[h] = tc_core(sd * 32 + ci, 0, kASBO);
+        lead[h] = sd == 0;
+        npc = h + 1;
+      }
+    }
+    const int raw_step = 8 * b * 16;
     int64_t seq = 0;
     for (int64_t u = blockIdx.x; u < d.n_units && !tc_aborted(bars); u += gridDim.x) {
       const int nks = nks_of(u);
@@ -350,19 +369,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
           break;
         }
         const int nk = min(kCK, nks - k0);
-        const unsigned char* raw = rawbuf + (size_t)rs * raw_bytes;
-        unsigned char* dst = astage + as * kAStageBytes;
-        // piece = (k, s, i): 16 stored bytes = 16 columns of digit s of row i
-        const int npieces = nk * 8 * b;
-        for (int pc = tq; pc < npieces; pc += kAW) {
-          const int i = pc % b;
-          const int sd = (pc / b) & 7;
-          const int kk = pc / (8 * b);
-          const uint4 q = *reinterpret_cast<const uint4*>(raw + (size_t)pc * 16);
-          const int row = sd * 32 + i;
-          *reinterpret_cast<uint4*>(dst + tc_core(row, 2 * kk, kASBO)) = tc_bytes_to_bf16(make_uint2(q.x, q.y), sd == 0);
-          *reinterpret_cast<uint4*>(dst + tc_core(row, 2 * kk + 1, kASBO)) =
-              tc_bytes_to_bf16(make_uint2(q.z, q.w), sd == 0);
+        // 16 stored bytes = 16 columns of one digit of one row, per 16-column step kk
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h < npc) {
+            const unsigned char* raw = rawbuf + (size_t)rs * raw_bytes + (tq + h * kAW) * 16;
+            unsigned char* dst = astage + as * kAStageBytes + drow[h];
+#pragma unroll
+            for (int kk = 0; kk < kCK; ++kk) {
+              if (kk < nk) {
+                const uint4 q = *reinterpret_cast<const uint4*>(raw + kk * raw_step);
+                *reinterpret_cast<uint4*>(dst + kk * 256) = tc_bytes_to_bf16(make_uint2(q.x, q.y), lead[h]);
+                *reinterpret_cast<uint4*>(dst + kk * 256 + 128) = tc_bytes_to_bf16(make_uint2(q.z, q.w), lead[h]);
+              }
+            }
+          }
         }
         fence_async_smem();
         mbar_arrive(&bars->a_full[as]);
@@ -403,12 +424,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
         if (lane < R) s_fmax[tq >> 5][lane] = m ? ef - 1022 : -100000;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(kBW) : "memory");
-      int fr[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
+      // this thread's RHS is tq % R in every work item below (kBW is a multiple of R)
+      const int my_r = tq % R;
+      int my_f;
+      {
         int a = -100000;
-        for (int q = 0; q < kBW / 32; ++q) a = max(a, s_fmax[q][r]);
-        fr[r] = a < -90000 ? 0 : a;
+        for (int q = 0; q < kBW / 32; ++q) a = max(a, s_fmax[q][my_r]);
+        my_f = a < -90000 ? 0 : a;
       }
       if (tc_aborted(bars) || !mbar_wait_bounded(&bars->b_empty[bb], ph ^ 1u)) {
         tc_give_up(bars, d.err);
@@ -419,12 +441,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
       unsigned char* bdst = bbuf + bb * b_bytes;
       // work item (8-column group jg, r): 8 values -> 8 digit planes t, 16 bytes each
       for (int w = tq; w < (kp / 8) * R; w += kBW) {
-        const int jg = w / R, r = w - jg * R;
+        const int jg = w / R, r = my_r;
         unsigned dg[8][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = jg * 8 + q;
-          tc_digits(j < ncol ? tc_fixed(xs[j * R + r], fr[r]) : 0ll, dg[q]);
+          tc_digits(j < ncol ? tc_fixed(xs[j * R + r], my_f) : 0ll, dg[q]);
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -434,9 +456,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_blockrow_kernel(BlockRowDesc
           *reinterpret_cast<uint4*>(bdst + tc_core(t * R + r, jg, b_sbo)) = tc_bytes_to_bf16(raw, t == 0);
         }
       }
-      if (tq == 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) bars->fexp[n & 3][r] = fr[r];
+      if (tq < R) {
+        bars->fexp[n & 3][tq] = my_f;
       }
       fence_async_smem();
       mbar_arrive(&bars->b_full[bb]);
