@@ -470,9 +470,10 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
  * split the same way per face row and RHS, the digit products summed exactly
  * and the result rounded once to FP64 (error below 4 * 2^-53 * ncol *
  * max_j |K_ij| * max_j |x_jr| over the row's ncol columns); the default for
- * those shapes, 7 = kind 3 compiled for three resident 256-thread CTAs per
- * SM (at most 80 registers per thread; R = 8, sp in {1,2}; otherwise as
- * kind 3); cps = CTAs per SM of the grid-stride launch (0 = heuristic).  Every other configuration computes the same sums; they differ
+ * those shapes, 7 = kind 3 compiled for more resident 256-thread CTAs per
+ * SM: three (at most 80 registers per thread) at R = 8 with sp in {1,2}, four
+ * (at most 64) for FP32 blocks at R <= 2 with sp in {1,2,4}; otherwise as
+ * kind 3; cps = CTAs per SM of the grid-stride launch (0 = heuristic).  Every other configuration computes the same sums; they differ
  * in summation order only. */
 
 /* Time every candidate configuration of every operation the problem can run

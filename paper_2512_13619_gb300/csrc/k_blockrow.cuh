@@ -415,8 +415,9 @@ template <> struct Vec16<__nv_bfloat16> {
 // Thread (unit, row group rg, slot part sp): rows rg*VR..rg*VR+VR-1, slots
 // sp, sp+SP, ...; the SP slot parts of a row group are adjacent lanes and
 // combine their sums with shuffles.  SP in {1, 2, 4, 8}; (ld / VR) * SP <= 256.
-// MINB = 3 compiles for three resident CTAs of 256 threads per SM (at most 80
-// registers), more loads in flight per SM at R = 8.
+// MINB > 1 compiles for MINB resident CTAs of 256 threads per SM: 3 (at most
+// 80 registers) for more loads in flight at R = 8, 4 (at most 64 registers)
+// for small problems at R <= 2, whose few face rows give few threads.
 template <typename T, int R, int BC, int SP, int MINB = 1>
 __global__ void __launch_bounds__(MINB > 1 ? 256 : 288, MINB) blockrow_vec_kernel(BlockRowDesc d, int G) {
   constexpr int VR = Vec16<T>::N;
@@ -846,6 +847,14 @@ void launch_vec(const BlockRowDesc& d, int sp, int cps, bool occ3, cudaStream_t 
       return;
     }
   }
+  if constexpr (R <= 2 && std::is_same<T, float>::value) {
+    if (occ3 && sp <= 4) {
+      if (sp == 1) launch_vec_sp<T, R, BC, 1, 4>(d, cps, s);
+      else if (sp == 2) launch_vec_sp<T, R, BC, 2, 4>(d, cps, s);
+      else launch_vec_sp<T, R, BC, 4, 4>(d, cps, s);
+      return;
+    }
+  }
   switch (sp) {
     case 1: launch_vec_sp<T, R, BC, 1>(d, cps, s); break;
     case 2: launch_vec_sp<T, R, BC, 2>(d, cps, s); break;
@@ -991,6 +1000,10 @@ int candidates_T(const BlockRowDesc& d, BrCfg* out, int cap) {
           for (int cps : {8, 16, 32}) add(BR_VEC, sp, cps);
       if (d.R == 8)
         for (int sp : {1, 2})
+          if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
+            for (int cps : {16, 32}) add(BR_VEC3, sp, cps);
+      if (d.R <= 2 && std::is_same<T, float>::value)
+        for (int sp : {1, 2, 4})
           if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
             for (int cps : {16, 32}) add(BR_VEC3, sp, cps);
       BulkPlan bp;
