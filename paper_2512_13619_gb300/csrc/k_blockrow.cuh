@@ -498,15 +498,18 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 288, MINB) blockrow_vec_kerne
 // Kernel "bulk": persistent CTAs (one per SM) stream G whole units per stage
 // with ONE bulk copy (a unit's blocks are contiguous in HBM; the copy is
 // tagged evict-first in L2 so that the gathered x stays resident there) into
-// a ring of shared-memory stages that a single producer lane keeps full.
-// Eight consumer warps read K from shared memory, VR rows of a column per
-// 16-byte vector, and x directly through L1/L2.  Consumer thread (unit g,
+// a ring of shared-memory stages that a single producer lane keeps full; the
+// same lane copies each unit's x slots (b x R floats each, through the
+// neighbour table) into the stage, on the same mbarrier.  Eight consumer
+// warps read K and x from shared memory, VR rows of a column per 16-byte
+// vector.  Consumer thread (unit g,
 // row group rg, column part cp) sums the columns c = cp, cp + NCP, ... of the
 // unit's concatenated slot columns; the NSUB parts inside a warp meet by
 // shuffles, the WPU warps of a unit in shared memory.  FP32/BF16 blocks.
 struct BulkPlan {
   int G, NS, WPU, NSUB, NRG;
-  int stage_bytes;     // bytes of one stage (a multiple of 128)
+  int stage_bytes;     // bytes of one stage (a multiple of 128): blocks, then the x slots
+  int x_off;           // offset of the x slots in a stage (G * max_slots slots of b x R floats)
   int red_floats;      // reduction area
   int64_t ntasks;
 };
@@ -536,32 +539,63 @@ __global__ void __launch_bounds__(kBulkConsumers + 32, 1) blockrow_bulk_kernel(B
   const size_t blk_bytes = (size_t)d.blk_stride * sizeof(T);
   const T* blk = static_cast<const T*>(d.blk);
   if (tid >= kBulkConsumers) {
-    // ------------------------------------------------------------ producer
-    if (tid == kBulkConsumers) {
-      uint64_t pol;
-      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-      int64_t k = 0;
-      for (int64_t t = blockIdx.x; t < pl.ntasks; t += gridDim.x, ++k) {
-        const int st = (int)(k % pl.NS);
-        const unsigned ph = (unsigned)((k / pl.NS) & 1);
-        if (s_abort || !mbar_wait_bounded(&empty[st], ph ^ 1u)) {
+    // ------------------------------------------------------------ producer warp
+    // Per stage: the lanes load the stage's neighbour indices (before waiting
+    // for the stage to be free, so the loads overlap the wait), lane 0 sets the
+    // byte count and copies the blocks, and the lanes copy the x slots, pair
+    // p = (unit p / max_slots, slot p % max_slots).
+    const int lane = tid - kBulkConsumers;
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    const unsigned xbytes = (unsigned)(d.bc * R * sizeof(float));
+    const int npairs = pl.G * d.max_slots;
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < pl.ntasks; t += gridDim.x, ++k) {
+      const int st = (int)(k % pl.NS);
+      const unsigned ph = (unsigned)((k / pl.NS) & 1);
+      const int64_t u0 = t * pl.G;
+      const int64_t u1 = min(u0 + pl.G, d.n_units);
+      const int64_t b0 = d.rowptr[u0], b1 = d.rowptr[u1];
+      int32_t src[4];                    // x slot of pair lane + 32 q, or -1
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int pr = lane + 32 * q;
+        src[q] = -1;
+        if (pr < npairs) {
+          const int64_t u = u0 + pr / d.max_slots;
+          const int sl = pr % d.max_slots;
+          if (u < u1 && sl < d.cnt[u]) src[q] = d.nbr[u * d.max_slots + sl];
+        }
+      }
+      bool ok = true;
+      if (lane == 0) ok = !s_abort && mbar_wait_bounded(&empty[st], ph ^ 1u);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) {
           if (!s_abort) atomicOr(d.err, ERRBIT_TIMEOUT);
           s_abort = 1;
-          break;
         }
-        const int64_t u0 = t * pl.G;
-        const int64_t u1 = min(u0 + pl.G, d.n_units);
-        const int64_t b0 = d.rowptr[u0];
-        const unsigned bytes = (unsigned)((d.rowptr[u1] - b0) * blk_bytes);
-        unsigned char* dst = stages + (size_t)st * pl.stage_bytes;
+        break;
+      }
+      unsigned char* dst = stages + (size_t)st * pl.stage_bytes;
+      if (lane == 0) {
+        const unsigned bytes = (unsigned)((b1 - b0) * blk_bytes);
         s_issued[st] = k;
-        mbar_arrive_expect_tx(&full[st], bytes);
+        mbar_arrive_expect_tx(&full[st], bytes + xbytes * (unsigned)(b1 - b0));
         if (bytes)
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
               "%4;" ::"r"(smem_u32(dst)),
               "l"(blk + b0 * d.blk_stride), "r"(bytes), "r"(smem_u32(&full[st])), "l"(pol)
               : "memory");
+      }
+      __syncwarp();
+      float* xdst = reinterpret_cast<float*>(dst + pl.x_off);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int pr = lane + 32 * q;
+        if (src[q] >= 0)
+          bulk_g2s(xdst + (size_t)pr * d.bc * R, d.in32 + (int64_t)src[q] * d.bc * R, xbytes, &full[st]);
       }
     }
   } else {
@@ -594,8 +628,10 @@ __global__ void __launch_bounds__(kBulkConsumers + 32, 1) blockrow_bulk_kernel(B
         const int64_t off = d.rowptr[u] - d.rowptr[u0];
         const T* sb = reinterpret_cast<const T*>(stages + (size_t)st * pl.stage_bytes) + off * d.blk_stride +
                       rg * VR;
-        const int32_t* nbr = d.nbr + u * d.max_slots;
+        const float* sx = reinterpret_cast<const float*>(stages + (size_t)st * pl.stage_bytes + pl.x_off) +
+                          (size_t)g * d.max_slots * BC * R;
         const int ncol = n * BC;
+#pragma unroll 4
         for (int c = cp; c < ncol; c += NCP) {
           const int sl = c / BC;
           const int col = c - sl * BC;
@@ -613,17 +649,17 @@ __global__ void __launch_bounds__(kBulkConsumers + 32, 1) blockrow_bulk_kernel(B
               kv[2 * i + 1] = f.y;
             }
           }
-          const float* xin = d.in32 + ((int64_t)nbr[sl] * BC + col) * R;
+          const float* xin = sx + c * R;      // slot sl, column col: (sl * BC + col) * R
           float xv[R];
           if constexpr (R % 4 == 0) {
 #pragma unroll
             for (int r4 = 0; r4 < R; r4 += 4) {
-              const float4 q = __ldg(reinterpret_cast<const float4*>(xin + r4));
+              const float4 q = *reinterpret_cast<const float4*>(xin + r4);
               xv[r4] = q.x; xv[r4 + 1] = q.y; xv[r4 + 2] = q.z; xv[r4 + 3] = q.w;
             }
           } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) xv[r] = __ldg(xin + r);
+            for (int r = 0; r < R; ++r) xv[r] = xin[r];
           }
 #pragma unroll
           for (int r = 0; r < R; ++r)
@@ -750,7 +786,7 @@ Plan make_plan(const BlockRowDesc& d) {
 
 // Plan of the bulk kernel; false when a unit's blocks do not fit a stage of
 // kBulkStageMax bytes or the rows do not divide into 16-byte vectors.
-constexpr size_t kBulkStageMax = 48 * 1024;
+constexpr size_t kBulkStageMax = 96 * 1024;
 template <typename T>
 bool bulk_plan(const BlockRowDesc& d, BulkPlan* pl) {
   if constexpr (std::is_same<T, double>::value) {
@@ -768,11 +804,15 @@ bool bulk_plan(const BlockRowDesc& d, BulkPlan* pl) {
     while (q.NSUB * 2 * q.NRG <= 32) q.NSUB *= 2;
     // units per stage: as many as fit the stage size, with a whole number of
     // consumer warps each (G * WPU = 8)
+    // x slots: whole 16-byte rows (b R floats) so that each is one bulk copy;
+    // at most 128 (unit, slot) pairs per stage (four per producer lane)
+    if ((d.bc * d.R * sizeof(float)) % 16 != 0 || d.max_slots > 128) return false;
     int G = 1;
-    while (G * 2 <= 8 && (size_t)G * 2 * row_bytes <= kBulkStageMax) G *= 2;
+    while (G * 2 <= 8 && (size_t)G * 2 * row_bytes <= kBulkStageMax && G * 2 * d.max_slots <= 128) G *= 2;
     q.G = G;
     q.WPU = (kBulkConsumers / 32) / G;
-    q.stage_bytes = (int)(((size_t)G * row_bytes + 127) / 128 * 128);
+    q.x_off = (int)(((size_t)G * row_bytes + 127) / 128 * 128);
+    q.stage_bytes = (int)((q.x_off + (size_t)G * d.max_slots * d.bc * d.R * sizeof(float) + 127) / 128 * 128);
     q.red_floats = q.WPU > 1 ? G * q.WPU * q.NRG * VR * d.R : 0;
     const size_t red_bytes = ((size_t)q.red_floats * 4 + 127) / 128 * 128;
     q.NS = (int)std::min<size_t>(8, (kSmemCap - red_bytes) / q.stage_bytes);
