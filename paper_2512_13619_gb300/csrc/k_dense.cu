@@ -50,8 +50,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
       Bs[br][bcol] = (gbr < d.K && gbc < d.N) ? B[(int64_t)gbr * d.ldb + gbc] : 0.0;
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
+    auto step = [&](int kk) {
       double a[TM], bv[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
@@ -61,6 +60,14 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    };
+    // the last tile runs over its real depth only (the FP64 pipe is the bound)
+    const int kc = d.K - k0 < BK ? d.K - k0 : BK;
+    if (kc == BK) {
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) step(kk);
+    } else {
+      for (int kk = 0; kk < kc; ++kk) step(kk);
     }
     __syncthreads();
   }
@@ -134,9 +141,9 @@ void gemm_smalln_launch(const GemmDesc& d, cudaStream_t s) {
   }
 }
 
-// tile factor (2, 3, 4 or 6) that pads n least, preferring the larger tile on ties
+// tile factor (1, 2, 3, 4 or 6) that pads n least, preferring the larger tile on ties
 int pick_tile(int n) {
-  const int cand[4] = {6, 4, 3, 2};
+  const int cand[5] = {6, 4, 3, 2, 1};
   int best = 2, bestpad = 1 << 30;
   for (int t : cand) {
     const int b = 16 * t;
@@ -171,6 +178,7 @@ void gemm_launch(const GemmDesc& d, cudaStream_t s) {
 template <int TM>
 void gemm_tn(const GemmDesc& d, int tn, cudaStream_t s) {
   switch (tn) {
+    case 1: gemm_launch<TM, 1>(d, s); break;
     case 2: gemm_launch<TM, 2>(d, s); break;
     case 3: gemm_launch<TM, 3>(d, s); break;
     case 4: gemm_launch<TM, 4>(d, s); break;
@@ -292,6 +300,7 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.N <= 8) { gemm_smalln_launch<8>(d, s); return; }
   const int tm = pick_tile(d.M), tn = pick_tile(d.N);
   switch (tm) {
+    case 1: gemm_tn<1>(d, tn, s); break;
     case 2: gemm_tn<2>(d, tn, s); break;
     case 3: gemm_tn<3>(d, tn, s); break;
     case 4: gemm_tn<4>(d, tn, s); break;
