@@ -238,11 +238,19 @@ __global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int 
     const double inv = 1.0 / pv;
     for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * inv;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-      int i = idx / n, j = idx - i * n;
-      if (i == k) continue;
-      double v = (j == k) ? 0.0 : a[idx];
-      a[idx] = fma(-col[i], a[k * n + j], v);
+    // rows i = ty, ty + 16, ..., columns j = tx, tx + 16, ... (16 x 16 threads)
+    {
+      const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+      const double* pk = a + k * n;
+      for (int i = ty; i < n; i += kInvThreads / 16) {
+        if (i == k) continue;
+        const double ci = col[i];
+        double* ai = a + i * n;
+        for (int j = tx; j < n; j += 16) {
+          const double v = (j == k) ? 0.0 : ai[j];
+          ai[j] = fma(-ci, pk[j], v);
+        }
+      }
     }
     __syncthreads();
   }
