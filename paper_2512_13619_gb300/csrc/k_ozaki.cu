@@ -386,16 +386,33 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int
     const int ab = (d.alpha == 1.0 && d.beta == 0.0) ? 0 : (d.alpha == -1.0 && d.beta == 1.0) ? 1 : 2;
     for (int cb = part * 8; cb < NT; cb += kWR * 8) {
       const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)cb;
+      // the block's column exponents and (for C -= AB and the general case)
+      // the old C values first, so that their loads overlap the TMEM reads
+      int fbv[8];
+      double cv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gc = col0 + cb + j;
+        const bool in = gr < d.M && cb + j < NT && gc < d.N;
+        fbv[j] = in ? (int)fb[(int64_t)z * d.N + gc] : 0;
+        cv[j] = 0.0;
+        if (in && ab != 0) cv[j] = C[(int64_t)gr * d.ldc + (int64_t)(gc / d.cg) * d.cgs + (gc % d.cg)];
+      }
+      // the 8 accumulators' columns: all loads issued, one wait
+      uint32_t raw[kAcc][8];
+#pragma unroll
+      for (int a = 0; a < kAcc; ++a) tmem_ld8_nowait(tbase + (uint32_t)(a * NT), raw[a]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int a = 0; a < kAcc; ++a) reg_order8(raw[a]);
       long long H[8], L[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) { H[j] = 0; L[j] = 0; }
 #pragma unroll
       for (int a = 0; a < kAcc; ++a) {
-        float v[8];
-        tmem_ld8(tbase + (uint32_t)(a * NT), v);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const long long iv = (long long)__float2int_rn(v[j]);     // integral, |v| < 2^31
+          const long long iv = (long long)__float2int_rn(__uint_as_float(raw[a][j]));   // integral, |v| < 2^31
           if (a < 4) H[j] = (H[j] << 7) + iv;
           else L[j] = (L[j] << 7) + iv;
         }
@@ -405,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int
         for (int j = 0; j < 8; ++j) {
           const int gc = col0 + cb + j;
           if (cb + j >= NT || gc >= d.N) continue;
-          const int fbj = (int)fb[(int64_t)z * d.N + gc];
+          const int fbj = fbv[j];
           double val = 0.0;
           if (ea_r > 0 && fbj > 0) {
             // (H 2^28 + L) 2^E with E = ea + fb - 2107, one rounding
@@ -421,8 +438,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_ozaki_kernel(GemmDesc d, int
           const int64_t cc = (int64_t)(gc / d.cg) * d.cgs + (gc % d.cg);
           double* p = C + (int64_t)gr * d.ldc + cc;
           if (ab == 0) *p = val;
-          else if (ab == 1) *p = *p - val;
-          else *p = (d.beta == 0.0 ? 0.0 : d.beta * *p) + d.alpha * val;
+          else if (ab == 1) *p = cv[j] - val;
+          else *p = (d.beta == 0.0 ? 0.0 : d.beta * cv[j]) + d.alpha * val;
         }
       }
     }
