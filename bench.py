@@ -694,9 +694,17 @@ def run_step3(args, ws, rank, local):
     _, t32, n32 = L.hdg_get_timing(p.h, 1)
     _, t16, n16 = L.hdg_get_timing(p.h, 2)
     L.hdg_set_timing(p.h, 0)
-    by32 = nnzb * b * ((b + 3) // 4 * 4) * 4 + p.n_dof * R * 12
-    by16 = nnzb * b * ((b + 7) // 8 * 8) * 2 + p.n_dof * R * 12
-    tot_by = by32 * n32 + by16 * n16
+    # algorithmic bytes: the blocks, the FP32 x read, and the product written
+    # in FP32 (the polynomial steps: 4 + 4 bytes per vector entry) or in FP64
+    # and FP32 (the GMRES iteration's product: 4 + 8 + 4)
+    its = infos.get('mixed_timed', infos.get('mixed', (0, 0, 0.0)))[0]
+    blk32 = nnzb * b * ((b + 3) // 4 * 4) * 4
+    blk16 = nnzb * b * ((b + 7) // 8 * 8) * 2
+    by32 = blk32 + p.n_dof * R * 12
+    by16 = blk16 + p.n_dof * R * 12
+    it32 = min(its, n32) if not n16 else 0
+    tot_by = (blk32 * n32 + p.n_dof * R * (16 * it32 + 8 * (n32 - it32)) +
+              blk16 * n16 + p.n_dof * R * 8 * n16)
     tot_ms = t32 + t16
     achieved = tot_by / tot_ms / 1e6 if tot_ms > 0 else 0.0
     _, cfg32, _, _ = L.hdg_get_tuning(p.h, 0, 1)
@@ -705,7 +713,8 @@ def run_step3(args, ws, rank, local):
                       % (' and BF16' if n16 else ''),
             'bound': 'hbm', 'achieved': round(achieved, 1), 'peak': pk['hbm_gbs'], 'unit': 'GB/s',
             'frac': round(achieved / pk['hbm_gbs'], 4), 'traffic': traffic, 'traffic_source': traffic_src,
-            'bytes_per_launch': {'fp32': int(by32), 'bf16': int(by16)},
+            'bytes_per_launch': {'fp32_polynomial': int(blk32 + p.n_dof * R * 8),
+                                 'fp32_iteration': int(blk32 + p.n_dof * R * 16), 'bf16': int(blk16 + p.n_dof * R * 8)},
             'launches_in_step': int(n32 + n16), 'ms_in_step': round(tot_ms, 3),
             'timing': 'CUDA events around every block-row launch of K in one mixed step run launch by launch',
             'peak_source': 'MEASURED_PEAKS.json hbm_gbs' if not pk.get('_fallback') else 'fallback 6.8 TB/s'}
