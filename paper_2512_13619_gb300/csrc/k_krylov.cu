@@ -110,6 +110,33 @@ __host__ __device__ __forceinline__ int64_t dots_chunk(int64_t len) {
   const int64_t lo = (int64_t)kDotsThreads * kDotsPerThread;
   return per < lo ? lo : per;
 }
+// acc[t] += sum over this thread's elements of V_{ig+t}[e] w[e], t < NG (the
+// group's basis vectors; predicated-off FMAs would still take the FP64 pipe)
+template <int NG>
+__device__ __forceinline__ void dots_body(const GmresView& k, const double* w, int ig, int64_t start, int64_t stop,
+                                          int64_t len, double (&acc)[kGroup]) {
+  // four elements per step: 4 * (NG + 1) independent loads in flight
+  int64_t e = start + threadIdx.x;
+  for (; e + 3 * kDotsThreads < stop; e += 4 * kDotsThreads) {
+    double we[4], vv[4][NG];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) we[q] = w[e + q * kDotsThreads];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int t = 0; t < NG; ++t) vv[q][t] = k.V[(int64_t)(ig + t) * len + e + q * kDotsThreads];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int t = 0; t < NG; ++t) acc[t] = fma(vv[q][t], we[q], acc[t]);
+  }
+  for (; e < stop; e += kDotsThreads) {
+    const double we1 = w[e];
+#pragma unroll
+    for (int t = 0; t < NG; ++t) acc[t] = fma(k.V[(int64_t)(ig + t) * len + e], we1, acc[t]);
+  }
+}
+
 __global__ void __launch_bounds__(kDotsThreads) dots_kernel(GmresView k, const double* w, int i0, int i1) {
   if (!any_running(k.running, k.R)) return;
   const int R = k.R;
@@ -124,28 +151,15 @@ __global__ void __launch_bounds__(kDotsThreads) dots_kernel(GmresView k, const d
   double acc[kGroup];
 #pragma unroll
   for (int t = 0; t < kGroup; ++t) acc[t] = 0.0;
-  // four elements per step: 4 * (kGroup + 1) independent loads in flight
-  int64_t e = start + threadIdx.x;
-  for (; e + 3 * kDotsThreads < stop; e += 4 * kDotsThreads) {
-    double we[4], vv[4][kGroup];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) we[q] = w[e + q * kDotsThreads];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int t = 0; t < kGroup; ++t)
-        vv[q][t] = (t < ng) ? k.V[(int64_t)(ig + t) * len + e + q * kDotsThreads] : 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int t = 0; t < kGroup; ++t)
-        if (t < ng) acc[t] = fma(vv[q][t], we[q], acc[t]);
-  }
-  for (; e < stop; e += kDotsThreads) {
-    const double we1 = w[e];
-#pragma unroll
-    for (int t = 0; t < kGroup; ++t)
-      if (t < ng) acc[t] = fma(k.V[(int64_t)(ig + t) * len + e], we1, acc[t]);
+  switch (ng) {     // uniform over the CTA
+    case 1: dots_body<1>(k, w, ig, start, stop, len, acc); break;
+    case 2: dots_body<2>(k, w, ig, start, stop, len, acc); break;
+    case 3: dots_body<3>(k, w, ig, start, stop, len, acc); break;
+    case 4: dots_body<4>(k, w, ig, start, stop, len, acc); break;
+    case 5: dots_body<5>(k, w, ig, start, stop, len, acc); break;
+    case 6: dots_body<6>(k, w, ig, start, stop, len, acc); break;
+    case 7: dots_body<7>(k, w, ig, start, stop, len, acc); break;
+    default: dots_body<8>(k, w, ig, start, stop, len, acc); break;
   }
 #pragma unroll
   for (int t = 0; t < kGroup; ++t) {
