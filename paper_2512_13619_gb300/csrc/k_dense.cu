@@ -86,6 +86,56 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmDesc d) {
   }
 }
 
+// Small products (M <= 32, N <= 64, at most 8 outputs per thread): the 256
+// threads own outputs o = tid, tid + 256, ... of the exact M x N product (no
+// padding rows or columns computed: a partly masked FP64 instruction costs a
+// full one), A and B staged through shared memory in K tiles of 32.
+constexpr int kFlatK = 32;
+template <int NO>
+__global__ void __launch_bounds__(256) gemm_f64_flat_kernel(GemmDesc d) {
+  __shared__ double As[32][kFlatK + 1];
+  __shared__ double Bs[kFlatK][64 + 1];
+  const int b0 = blockIdx.z / d.nb1, b1 = blockIdx.z % d.nb1;
+  const double* A = d.A + b0 * d.sA0 + b1 * d.sA1;
+  const double* B = d.B + b0 * d.sB0 + b1 * d.sB1;
+  double* C = d.C + b0 * d.sC0 + b1 * d.sC1;
+  const int MN = d.M * d.N;
+  int rr[NO], cc[NO];
+  double acc[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    const int idx = threadIdx.x + 256 * o;
+    rr[o] = idx < MN ? idx / d.N : 0;
+    cc[o] = idx < MN ? idx - rr[o] * d.N : 0;
+    acc[o] = 0.0;
+  }
+  for (int k0 = 0; k0 < d.K; k0 += kFlatK) {
+    const int kc = d.K - k0 < kFlatK ? d.K - k0 : kFlatK;
+    for (int t = threadIdx.x; t < d.M * kc; t += 256) {
+      const int r = t / kc, c = t - r * kc;
+      As[r][c] = A[(int64_t)r * d.lda + k0 + c];
+    }
+    for (int t = threadIdx.x; t < kc * d.N; t += 256) {
+      const int r = t / d.N, c = t - r * d.N;
+      Bs[r][c] = B[(int64_t)(k0 + r) * d.ldb + c];
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (threadIdx.x + 256 * o < MN) acc[o] = fma(As[rr[o]][kk], Bs[kk][cc[o]], acc[o]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    if (threadIdx.x + 256 * o >= MN) continue;
+    const int64_t c = (int64_t)(cc[o] / d.cg) * d.cgs + (cc[o] % d.cg);
+    double* p = C + (int64_t)rr[o] * d.ldc + c;
+    *p = (d.beta == 0.0 ? 0.0 : d.beta * *p) + d.alpha * acc[o];
+  }
+}
+
 // Products with few columns (N <= 8: the right-hand-side columns of
 // Eqs. w19 and w22): one warp per output row, lanes striding over K, the N
 // partial sums reduced with shuffles.
@@ -175,6 +225,21 @@ void gemm_launch(const GemmDesc& d, cudaStream_t s) {
   }
 }
 
+template <int NO>
+void gemm_flat_launch(const GemmDesc& d, cudaStream_t s) {
+  const int64_t nb = (int64_t)d.nb0 * d.nb1;
+  const int per = (int)(65535 / d.nb1);
+  for (int b0 = 0; b0 < d.nb0; b0 += per) {
+    GemmDesc e = d;
+    e.nb0 = (d.nb0 - b0 < per) ? d.nb0 - b0 : per;
+    e.A = d.A + b0 * d.sA0;
+    e.B = d.B + b0 * d.sB0;
+    e.C = d.C + b0 * d.sC0;
+    (void)nb;
+    count_launch(); gemm_f64_flat_kernel<NO><<<dim3(1, 1, (unsigned)((int64_t)e.nb0 * d.nb1)), 256, 0, s>>>(e);
+  }
+}
+
 template <int TM>
 void gemm_tn(const GemmDesc& d, int tn, cudaStream_t s) {
   switch (tn) {
@@ -202,6 +267,7 @@ __global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int 
   for (int i = threadIdx.x; i < nn; i += blockDim.x) a[i] = A[i];
   __syncthreads();
   bool singular = false;
+  const int step_i = kInvThreads / n, step_j = kInvThreads - step_i * n;   // kInvThreads = step_i n + step_j
   for (int k = 0; k < n; ++k) {
     // pivot search (warp 0): largest |a[i][k]|, i >= k, lowest index on ties
     if (threadIdx.x < 32) {
@@ -238,17 +304,22 @@ __global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int 
     const double inv = 1.0 / pv;
     for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * inv;
     __syncthreads();
-    // rows i = ty, ty + 16, ..., columns j = tx, tx + 16, ... (16 x 16 threads)
+    // entries idx = tid, tid + 256, ... of the row-major matrix, so every warp
+    // but the last is full (a partly masked FP64 instruction costs a full
+    // one); (i, j) advance by the fixed step without a division
     {
-      const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
       const double* pk = a + k * n;
-      for (int i = ty; i < n; i += kInvThreads / 16) {
-        if (i == k) continue;
-        const double ci = col[i];
-        double* ai = a + i * n;
-        for (int j = tx; j < n; j += 16) {
-          const double v = (j == k) ? 0.0 : ai[j];
-          ai[j] = fma(-ci, pk[j], v);
+      int i = threadIdx.x / n, j = threadIdx.x - i * n;
+      for (int idx = threadIdx.x; idx < nn; idx += kInvThreads) {
+        if (i != k) {
+          const double v = (j == k) ? 0.0 : a[idx];
+          a[idx] = fma(-col[i], pk[j], v);
+        }
+        j += step_j;
+        i += step_i;
+        if (j >= n) {
+          j -= n;
+          ++i;
         }
       }
     }
@@ -306,6 +377,17 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.N <= 2) { gemm_smalln_launch<2>(d, s); return; }
   if (d.N <= 4) { gemm_smalln_launch<4>(d, s); return; }
   if (d.N <= 8) { gemm_smalln_launch<8>(d, s); return; }
+  if (d.M <= 32 && d.N <= 64) {
+    const int no = (d.M * d.N + 255) / 256;       // <= 8
+    switch (no) {
+      case 1: gemm_flat_launch<1>(d, s); return;
+      case 2: gemm_flat_launch<2>(d, s); return;
+      case 3: gemm_flat_launch<3>(d, s); return;
+      case 4: gemm_flat_launch<4>(d, s); return;
+      case 5: case 6: gemm_flat_launch<6>(d, s); return;
+      default: gemm_flat_launch<8>(d, s); return;
+    }
+  }
   const int tm = pick_tile(d.M), tn = pick_tile(d.N);
   switch (tm) {
     case 1: gemm_tn<1>(d, tn, s); break;
