@@ -473,7 +473,9 @@ hdg_status hdg_set_condense_mode(hdg_problem p, int mode);
  * those shapes, 7 = kind 3 compiled for more resident 256-thread CTAs per
  * SM: three (at most 80 registers per thread) at R = 8 with sp in {1,2}, four
  * (at most 64) for FP32 blocks at R <= 2 with sp in {1,2,4}; otherwise as
- * kind 3; cps = CTAs per SM of the grid-stride launch (0 = heuristic).  Every other configuration computes the same sums; they differ
+ * kind 3; 8 = kind 7 at R = 8 with the right-hand sides split over two
+ * threads (4 each), sp in {1,2}; cps = CTAs per SM of the grid-stride launch
+ * (0 = heuristic).  Every other configuration computes the same sums; they differ
  * in summation order only. */
 
 /* Time every candidate configuration of every operation the problem can run

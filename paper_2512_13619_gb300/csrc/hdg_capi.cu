@@ -2938,7 +2938,7 @@ int hdg_tuning_candidates(hdg_problem p, int op, int prec, int* cfg3, int cap) {
 
 hdg_status hdg_set_tuning(hdg_problem p, int op, int prec, const int* cfg3) {
   if (!p || op < 0 || op > 2 || prec < 0 || prec > 2 || !cfg3) return HDG_ERR_ARG;
-  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_VEC3 || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
+  if (cfg3[0] < BR_DEFAULT || cfg3[0] > BR_VEC3R || cfg3[1] < 0 || cfg3[1] > 8 || cfg3[2] < 0 || cfg3[2] > 64)
     return HDG_ERR_ARG;
   p->tune[op][prec].kind = cfg3[0];
   p->tune[op][prec].sp = cfg3[1];

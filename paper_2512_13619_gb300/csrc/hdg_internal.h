@@ -162,7 +162,8 @@ struct BlockRowDesc {
 // row), BR_VEC (VR rows per thread, 16-byte loads, sp slot parts), BR_SPLIT
 // (sp threads per row, each summing every sp-th slot, shuffle reduction).
 // cps: CTAs per SM of the grid-stride launch (0 = heuristic).
-enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5, BR_TC = 6, BR_VEC3 = 7 };
+enum { BR_DEFAULT = 0, BR_TMA = 1, BR_DIRECT = 2, BR_VEC = 3, BR_SPLIT = 4, BR_BULK = 5, BR_TC = 6, BR_VEC3 = 7,
+       BR_VEC3R = 8 };
 struct BrCfg {
   int kind = BR_DEFAULT, sp = 0, cps = 0;
 };

@@ -418,50 +418,52 @@ template <> struct Vec16<__nv_bfloat16> {
 // MINB > 1 compiles for MINB resident CTAs of 256 threads per SM: 3 (at most
 // 80 registers) for more loads in flight at R = 8, 4 (at most 64 registers)
 // for small problems at R <= 2, whose few face rows give few threads.
-template <typename T, int R, int BC, int SP, int MINB = 1>
+template <typename T, int R, int BC, int SP, int MINB = 1, int RS = 1>
 __global__ void __launch_bounds__(MINB > 1 ? 256 : 288, MINB) blockrow_vec_kernel(BlockRowDesc d, int G) {
   constexpr int VR = Vec16<T>::N;
+  constexpr int RR = R / RS;                     // right-hand sides of this thread: r0 .. r0 + RR - 1
   if (!any_active(d.active, R)) return;
-  const int tpu = (d.ld / VR) * SP;              // threads per unit; G units per CTA,
+  const int tpu = (d.ld / VR) * SP * RS;         // threads per unit; G units per CTA,
                                                  // threads past G*tpu only join the shuffles
   const int gu = threadIdx.x / tpu;
   const int q = threadIdx.x - gu * tpu;
-  const int sp = q % SP, rg = q / SP;
+  const int sp = q % SP, rg = q / (SP * RS);
+  const int r0 = ((q / SP) % RS) * RR;
   const bool valid = gu < G;
   const T* blk = static_cast<const T*>(d.blk);
   const int64_t ngroups = (d.n_units + G - 1) / G;
   for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const int64_t u = grp * G + gu;
     const bool act = valid && u < d.n_units;
-    float acc[VR][R];
+    float acc[VR][RR];
 #pragma unroll
     for (int v = 0; v < VR; ++v)
 #pragma unroll
-      for (int r = 0; r < R; ++r) acc[v][r] = 0.f;
+      for (int r = 0; r < RR; ++r) acc[v][r] = 0.f;
     if (act) {
       const int n = d.cnt[u];
       const int64_t rp = d.rowptr[u];
       const int32_t* nbr = d.nbr + u * d.max_slots;
       for (int s = sp; s < n; s += SP) {
-        const float* xin = d.in32 + (int64_t)nbr[s] * BC * R;
+        const float* xin = d.in32 + (int64_t)nbr[s] * BC * R + r0;
         const T* bs = blk + (rp + s) * d.blk_stride + rg * VR;
 #pragma unroll
         for (int c = 0; c < BC; ++c) {
           float kv[VR];
           Vec16<T>::load(bs + (size_t)c * d.ld, kv);
-          float xv[R];
-          if constexpr (R % 4 == 0) {
+          float xv[RR];
+          if constexpr (RR % 4 == 0) {
 #pragma unroll
-            for (int r4 = 0; r4 < R; r4 += 4) {
+            for (int r4 = 0; r4 < RR; r4 += 4) {
               const float4 q = __ldg(reinterpret_cast<const float4*>(xin + c * R + r4));
               xv[r4] = q.x; xv[r4 + 1] = q.y; xv[r4 + 2] = q.z; xv[r4 + 3] = q.w;
             }
           } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) xv[r] = __ldg(xin + c * R + r);
+            for (int r = 0; r < RR; ++r) xv[r] = __ldg(xin + c * R + r);
           }
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
+          for (int r = 0; r < RR; ++r) {
 #pragma unroll
             for (int v = 0; v < VR; ++v) acc[v][r] = fmaf(kv[v], xv[r], acc[v][r]);
           }
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 288, MINB) blockrow_vec_kerne
 #pragma unroll
       for (int v = 0; v < VR; ++v)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RR; ++r) {
 #pragma unroll
           for (int o = 1; o < SP; o <<= 1) acc[v][r] += __shfl_xor_sync(0xffffffffu, acc[v][r], o);
         }
@@ -481,13 +483,14 @@ __global__ void __launch_bounds__(MINB > 1 ? 256 : 288, MINB) blockrow_vec_kerne
 #pragma unroll
       for (int v = 0; v < VR; ++v)
         if (rg * VR + v < d.b_rows) {
-          if constexpr (R % 4 == 0) {
+          if constexpr (RR % 4 == 0) {
 #pragma unroll
-            for (int r = 0; r < R; r += 4)
-              epi_store4(d, u, rg * VR + v, r, make_float4(acc[v][r], acc[v][r + 1], acc[v][r + 2], acc[v][r + 3]));
+            for (int r = 0; r < RR; r += 4)
+              epi_store4(d, u, rg * VR + v, r0 + r,
+                         make_float4(acc[v][r], acc[v][r + 1], acc[v][r + 2], acc[v][r + 3]));
           } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) epi_store(d, u, rg * VR + v, r, (double)acc[v][r]);
+            for (int r = 0; r < RR; ++r) epi_store(d, u, rg * VR + v, r0 + r, (double)acc[v][r]);
           }
         }
     }
@@ -861,25 +864,32 @@ int pick_nt_direct(int b_rows) {
   return best;
 }
 
-template <typename T, int R, int BC, int SP, int MINB = 1>
+template <typename T, int R, int BC, int SP, int MINB = 1, int RS = 1>
 void launch_vec_sp(const BlockRowDesc& d, int cps, cudaStream_t s) {
   constexpr int VR = Vec16<T>::N;
-  const int tpu = (d.ld / VR) * SP;
+  const int tpu = (d.ld / VR) * SP * RS;
   const int G = std::max(1, 256 / tpu);
   const int NT = (G * tpu + 31) / 32 * 32;        // whole warps for the full-mask shuffles
   int64_t ngroups = (d.n_units + G - 1) / G;
   int64_t grid = std::min<int64_t>(ngroups, (int64_t)num_sms() * (cps > 0 ? cps : 16));
   if (grid < 1) grid = 1;
-  count_launch(); blockrow_vec_kernel<T, R, BC, SP, MINB><<<(unsigned)grid, NT, 0, s>>>(d, G);
+  count_launch(); blockrow_vec_kernel<T, R, BC, SP, MINB, RS><<<(unsigned)grid, NT, 0, s>>>(d, G);
 }
 
 // A shuffle group is SP adjacent lanes starting at a multiple of SP, so it
 // never straddles a warp.  Heuristic: 4 parts for rows of several slots
 // (matvec, ASM), 1 for one slot (BJ).
 template <typename T, int R, int BC>
-void launch_vec(const BlockRowDesc& d, int sp, int cps, bool occ3, cudaStream_t s) {
+void launch_vec(const BlockRowDesc& d, int sp, int cps, bool occ3, cudaStream_t s, bool rsplit = false) {
   if (sp <= 0) sp = d.max_slots >= 4 ? 4 : d.max_slots >= 2 ? 2 : 1;
   while (sp > 1 && (d.ld / Vec16<T>::N) * sp > 256) sp >>= 1;   // threads per unit <= 256
+  if constexpr (R == 8) {
+    if (rsplit && sp <= 2 && (d.ld / Vec16<T>::N) * sp * 2 <= 256) {
+      if (sp == 1) launch_vec_sp<T, R, BC, 1, 3, 2>(d, cps, s);
+      else launch_vec_sp<T, R, BC, 2, 3, 2>(d, cps, s);
+      return;
+    }
+  }
   if constexpr (R == 8) {
     if (occ3 && sp <= 2) {
       if (sp == 1) launch_vec_sp<T, R, BC, 1, 3>(d, cps, s);
@@ -956,8 +966,9 @@ void launch_direct_bc(const BlockRowDesc& d, BrCfg cfg, cudaStream_t s) {
     if (cfg.kind == BR_BULK && launch_bulk<T, R, BC>(d, s)) return;
   }
   if constexpr (!std::is_same<T, double>::value && BC > 0) {
-    if ((cfg.kind == BR_DEFAULT || cfg.kind == BR_VEC || cfg.kind == BR_VEC3) && vec_ok<T>(d)) {
-      launch_vec<T, R, BC>(d, cfg.sp, cfg.cps, cfg.kind == BR_VEC3, s);
+    if ((cfg.kind == BR_DEFAULT || cfg.kind == BR_VEC || cfg.kind == BR_VEC3 || cfg.kind == BR_VEC3R) &&
+        vec_ok<T>(d)) {
+      launch_vec<T, R, BC>(d, cfg.sp, cfg.cps, cfg.kind == BR_VEC3 || cfg.kind == BR_VEC3R, s, cfg.kind == BR_VEC3R);
       return;
     }
   }
@@ -1042,6 +1053,10 @@ int candidates_T(const BlockRowDesc& d, BrCfg* out, int cap) {
         for (int sp : {1, 2})
           if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
             for (int cps : {16, 32}) add(BR_VEC3, sp, cps);
+      if (d.R == 8)
+        for (int sp : {1, 2})
+          if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp * 2 <= 256)
+            for (int cps : {16, 32}) add(BR_VEC3R, sp, cps);
       if (d.R <= 2 && std::is_same<T, float>::value)
         for (int sp : {1, 2, 4})
           if ((sp == 1 || sp <= d.max_slots) && (d.ld / Vec16<T>::N) * sp <= 256)
