@@ -105,6 +105,7 @@ struct hdg_problem_s {
   double* d_stage2 = nullptr;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr}, ev_start = nullptr;
+  cudaEvent_t ev_read = nullptr;   // after the last copy from caller memory of a host-input call
   double* d_tmp = nullptr;
 
   // assembled system
@@ -208,6 +209,8 @@ struct hdg_problem_s {
   int64_t gen_cap = 0;
   unsigned char* d_genin = nullptr;
   int64_t genin_cap = 0;
+  unsigned char* d_hexin[2] = {nullptr, nullptr};   // host inputs of hdg_condense_hex, double-buffered
+  int64_t hexin_cap[2] = {0, 0};
   double* d_phys = nullptr;
   int hex_sf = 1;                  // M^e, B_d of generated blocks by sum factorisation (0: dense products)
   // autotuned launch configurations [operation: K, BJ, ASM][precision]
@@ -1385,6 +1388,18 @@ GmresResult gmres(hdg_problem p, const hdg_solver_opts& o, int kprec, int mprec,
   return out;
 }
 
+// Host inputs: the caller's buffers are not retained after a call returns,
+// so the call waits for its last copy from them (not for the work that uses
+// the copies): mark_inputs_read after the copies on their stream `cs`,
+// wait_inputs_read before returning.
+void mark_inputs_read(hdg_problem p, cudaStream_t cs) {
+  if (!p->ev_read) CK(cudaEventCreateWithFlags(&p->ev_read, cudaEventDisableTiming));
+  CK(cudaEventRecord(p->ev_read, cs));
+}
+void wait_inputs_read(hdg_problem p) {
+  if (p->ev_read) CK(cudaEventSynchronize(p->ev_read));
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1511,6 +1526,7 @@ hdg_status hdg_problem_destroy(hdg_problem p) {
   }
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->ev_read) cudaEventDestroy(p->ev_read);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
     if (p->ev_freed[i]) cudaEventDestroy(p->ev_freed[i]);
@@ -1648,6 +1664,7 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
         CK(cudaEventRecord(p->ev_copied[bsel], cs));
         CK(cudaStreamWaitEvent(s, p->ev_copied[bsel], 0));
       }
+      if (!on_device) mark_inputs_read(p, cs);
       condense_chunk(p, e0 + c0, ec, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], dev[7], dev[8], dev[9],
                      dev[10], sh, s);
       if (overlap) CK(cudaEventRecord(p->ev_freed[bsel], s));
@@ -1659,6 +1676,7 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
         }
       }
     }
+    if (!on_device) wait_inputs_read(p);
     collect_timing(p, s);
     p->assembled = false;
     return HDG_OK;
@@ -1820,6 +1838,7 @@ void hex_inputs(hdg_problem p, int64_t c0, int64_t ec, const double* verts, cons
   *dp = (const int32_t*)(b + sizeof(double) * nv);
 }
 
+
 }  // namespace
 extern "C" {
 
@@ -1837,8 +1856,30 @@ hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad,
     const InSizes z = in_sizes(p);
     const int64_t sz[11] = {z.Me, z.Bd, z.Cd, z.D, z.E, z.F, z.G, z.H, z.J, z.ru, z.ruh};
     const bool sh[11] = {false, false, false, false, false, false, false, false, false, false, false};
-    for (int64_t c0 = 0; c0 < count; c0 += p->chunk) {
-      const int64_t ec = std::min<int64_t>(p->chunk, count - c0);
+    // host inputs with several chunks: each chunk's vertices, load vectors and
+    // face permutations go to one of two device buffers on the copy stream,
+    // ordered against the generation and condensation by events; the first
+    // chunks ramp up (1/8, 1/4, 1/2 of a chunk) so that only a small first
+    // copy is exposed
+    const bool overlap = !on_device && count > p->chunk;
+    const int64_t in_per = 24 + sz[9] + sz[10];                 // doubles per element, then the permutation
+    if (overlap) {
+      for (int i = 0; i < 2; ++i)
+        grow(p, p->d_hexin[i], p->hexin_cap[i],
+             p->chunk * (int64_t)(sizeof(double) * in_per + sizeof(int32_t) * 6 * p->PF));
+      if (!p->copy_stream) CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+      for (int i = 0; i < 2; ++i) {
+        if (!p->ev_copied[i]) CK(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
+        if (!p->ev_freed[i]) CK(cudaEventCreateWithFlags(&p->ev_freed[i], cudaEventDisableTiming));
+      }
+      if (!p->ev_start) CK(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+      CK(cudaEventRecord(p->ev_start, s));                  // earlier work on the buffers
+      CK(cudaStreamWaitEvent(p->copy_stream, p->ev_start, 0));
+    }
+    int64_t ci = 0, ec = 0;
+    for (int64_t c0 = 0; c0 < count; c0 += ec, ++ci) {
+      const int64_t cap = (overlap && ci < 3) ? std::max<int64_t>(1, p->chunk >> (3 - ci)) : p->chunk;
+      ec = std::min<int64_t>(cap, count - c0);
       double* stg = p->d_stage;
       double* out[11];
       for (int i = 0; i < 11; ++i) {
@@ -1847,18 +1888,43 @@ hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad,
       }
       const double* dv;
       const int32_t* dp;
-      hex_inputs(p, c0, ec, verts, face_perm, on_device, &dv, &dp, s);
-      hex_generate_chunk(p, dev, ec, dv, dp, phys, out, s);
       const double* dru = ru + c0 * sz[9];
       const double* druh = ruh + c0 * sz[10];
-      if (!on_device) {
-        CK(cudaMemcpyAsync(out[9], dru, sizeof(double) * ec * sz[9], cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(out[10], druh, sizeof(double) * ec * sz[10], cudaMemcpyHostToDevice, s));
-        dru = out[9];
-        druh = out[10];
+      const int bsel = (int)(ci & 1);
+      if (overlap) {
+        cudaStream_t cs = p->copy_stream;
+        if (ci >= 2) CK(cudaStreamWaitEvent(cs, p->ev_freed[bsel], 0));    // chunk ci-2 is done with it
+        double* b = reinterpret_cast<double*>(p->d_hexin[bsel]);
+        double* bv = b;
+        double* bru = bv + ec * 24;
+        double* bruh = bru + ec * sz[9];
+        int32_t* bp = reinterpret_cast<int32_t*>(bruh + ec * sz[10]);
+        CK(cudaMemcpyAsync(bv, verts + c0 * 24, sizeof(double) * ec * 24, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(bru, dru, sizeof(double) * ec * sz[9], cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(bruh, druh, sizeof(double) * ec * sz[10], cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(bp, face_perm + c0 * 6 * (int64_t)p->PF, sizeof(int32_t) * ec * 6 * p->PF,
+                           cudaMemcpyHostToDevice, cs));
+        CK(cudaEventRecord(p->ev_copied[bsel], cs));
+        CK(cudaStreamWaitEvent(s, p->ev_copied[bsel], 0));
+        mark_inputs_read(p, cs);
+        dv = bv;
+        dp = bp;
+        dru = bru;
+        druh = bruh;
+      } else {
+        hex_inputs(p, c0, ec, verts, face_perm, on_device, &dv, &dp, s);
+        if (!on_device) {
+          CK(cudaMemcpyAsync(out[9], dru, sizeof(double) * ec * sz[9], cudaMemcpyHostToDevice, s));
+          CK(cudaMemcpyAsync(out[10], druh, sizeof(double) * ec * sz[10], cudaMemcpyHostToDevice, s));
+          dru = out[9];
+          druh = out[10];
+          mark_inputs_read(p, s);
+        }
       }
+      hex_generate_chunk(p, dev, ec, dv, dp, phys, out, s);
       condense_chunk(p, e0 + c0, ec, out[0], out[1], out[2], out[3], out[4], out[5], out[6], out[7], out[8], dru,
                      druh, sh, s);
+      if (overlap) CK(cudaEventRecord(p->ev_freed[bsel], s));
       CK(cudaGetLastError());
       for (int64_t e = e0 + c0; e < e0 + c0 + ec; ++e) {
         if (!p->condensed[e]) {
@@ -1867,6 +1933,7 @@ hdg_status hdg_condense_hex(hdg_problem p, int64_t e0, int64_t count, int nquad,
         }
       }
     }
+    if (!on_device) wait_inputs_read(p);
     collect_timing(p, s);
     p->assembled = false;
     return HDG_OK;
