@@ -249,7 +249,11 @@ hdg_status hdg_condense_strided(hdg_problem p, int64_t e0, int64_t count, const 
 
 /* Dirichlet trace values u_D (b_hat = uhat - u_D on Dirichlet faces, Sec.
  * 2.1): host or device, n_face x b x R; rows of free faces are ignored.
- * Defaults to zero.  Must be set before hdg_assemble. */
+ * Defaults to zero.  Must be set before hdg_assemble.  From host memory the
+ * copy runs on the problem's copy stream as soon as the earlier operations
+ * on the stored values are done, overlapping other work still queued on
+ * `stream`; the call returns once the caller's buffer has been read, and
+ * later work on `stream` sees the new values. */
 hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhat_dirichlet, int on_device, void* stream);
 
 /* Face-based assembly (Sec. 4.2): for every free face f the face row of K,
@@ -307,12 +311,17 @@ hdg_status hdg_solve_batch(hdg_problem* problems, int count, const hdg_solver_op
                            hdg_solve_info* infos);
 
 /* Full trace uhat (host or device): n_face x b x R, Dirichlet faces filled
- * with u_D. */
+ * with u_D.  A host buffer in pinned, mapped memory is written by the kernel
+ * directly; a pageable one through a device buffer and a copy. */
 hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* stream);
 
 /* Element recovery (Eq. w19, Eq. w16): u^e = Ebar^{-1}(r_u - Fbar uhat^e),
  * q^e_{a,d} = -(M^e)^{-1}(B_d u^e_a + C_d uhat^e_a).  Outputs host or device:
- * u  n_elem x M*P_E x R,  q  n_elem x M*D*P_E x R. */
+ * u  n_elem x M*P_E x R,  q  n_elem x M*D*P_E x R.  Host outputs in
+ * pinned, mapped memory are written by the kernel directly.  Pageable host
+ * outputs of at least 2048 elements are recovered in up to 8 pieces, each
+ * piece's copy to the host overlapping the next piece's computation.  Every
+ * way gives the same values. */
 hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void* stream);
 
 /* y = K x with K stored in `prec` (FP64, FP32 or BF16 blocks; products

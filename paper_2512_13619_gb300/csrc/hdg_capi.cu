@@ -106,6 +106,9 @@ struct hdg_problem_s {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr}, ev_start = nullptr;
   cudaEvent_t ev_read = nullptr;   // after the last copy from caller memory of a host-input call
+  cudaEvent_t ev_uD_used = nullptr;    // after the last stream operation on d_uhatD
+  cudaEvent_t ev_uD_copied = nullptr;  // after a host copy into d_uhatD on the copy stream
+  cudaEvent_t ev_rec = nullptr;        // recovery pieces handed to the copy stream
   double* d_tmp = nullptr;
 
   // assembled system
@@ -433,6 +436,9 @@ int64_t tmp_elems(int64_t PE, int64_t MPE, int64_t nlb, int64_t R) {
 int64_t tmp_per_elem(hdg_problem p) { return tmp_elems(p->PE, p->MPE, p->nlb, p->R); }
 // device bytes of one condensation chunk (inputs + scratch)
 constexpr int64_t kChunkBudget = 3ll << 29;   // 1.5 GiB
+// recovery into host buffers: up to 8 pieces of at least 1024 elements
+constexpr int64_t kRecoverPieces = 8, kRecoverPieceMin = 1024;
+inline int64_t pieces_run(int64_t n, int64_t per) { return (n + per - 1) / per; }
 
 GemmDesc gd(int M, int N, int K, const double* A, int64_t lda, int64_t sA0, int64_t sA1, const double* B,
             int64_t ldb, int64_t sB0, int64_t sB1, double* C, int64_t ldc, int64_t sC0, int64_t sC1, double alpha,
@@ -1400,6 +1406,33 @@ void wait_inputs_read(hdg_problem p) {
   if (p->ev_read) CK(cudaEventSynchronize(p->ev_read));
 }
 
+cudaStream_t copy_stream_of(hdg_problem p) {
+  if (!p->copy_stream) CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  return p->copy_stream;
+}
+cudaEvent_t event_of(cudaEvent_t& e) {
+  if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return e;
+}
+// Device address of a caller's host buffer in pinned, mapped memory (the
+// kernels then write host outputs directly, their many warps taking the
+// translation misses of a buffer not touched for a while in parallel, where
+// a copy engine takes them one after another), or nullptr for pageable
+// memory.
+double* mapped_host(double* ptr) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<double*>(a.devicePointer) : nullptr;
+}
+
+// Every stream operation that reads or writes the device copy of the
+// Dirichlet values records this event after it, so that a host copy into it
+// on the copy stream waits for exactly those operations.
+void mark_uD_used(hdg_problem p, cudaStream_t s) { CK(cudaEventRecord(event_of(p->ev_uD_used), s)); }
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1527,6 +1560,9 @@ hdg_status hdg_problem_destroy(hdg_problem p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   if (p->ev_read) cudaEventDestroy(p->ev_read);
+  if (p->ev_uD_used) cudaEventDestroy(p->ev_uD_used);
+  if (p->ev_uD_copied) cudaEventDestroy(p->ev_uD_copied);
+  if (p->ev_rec) cudaEventDestroy(p->ev_rec);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
     if (p->ev_freed[i]) cudaEventDestroy(p->ev_freed[i]);
@@ -1979,9 +2015,24 @@ hdg_status hdg_set_dirichlet(hdg_problem p, const double* uhatD, int on_device, 
   if (!p || !uhatD) return HDG_ERR_ARG;
   try {
     DeviceGuard dg(p->device);
-    CK(cudaMemcpyAsync(p->d_uhatD, uhatD, sizeof(double) * p->NF * p->b * p->R,
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, (cudaStream_t)stream));
-    if (!on_device) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * p->NF * p->b * p->R;
+    if (on_device) {
+      CK(cudaMemcpyAsync(p->d_uhatD, uhatD, bytes, cudaMemcpyDeviceToDevice, s));
+      mark_uD_used(p, s);
+    } else {
+      // host values: copied on the copy stream once the earlier operations on
+      // the device copy are done, so the copy overlaps whatever else is still
+      // queued on `stream` (the end of a condensation); `stream` waits for it,
+      // and the call returns once the caller's buffer has been read
+      cudaStream_t cs = copy_stream_of(p);
+      if (p->ev_uD_used) CK(cudaStreamWaitEvent(cs, p->ev_uD_used, 0));
+      CK(cudaMemcpyAsync(p->d_uhatD, uhatD, bytes, cudaMemcpyHostToDevice, cs));
+      CK(cudaEventRecord(event_of(p->ev_uD_copied), cs));
+      CK(cudaStreamWaitEvent(s, p->ev_uD_copied, 0));
+      mark_uD_used(p, s);
+      CK(cudaEventSynchronize(p->ev_uD_copied));
+    }
     p->assembled = false;
     return HDG_OK;
   } catch (const CudaError& e) {
@@ -2037,6 +2088,7 @@ hdg_status hdg_assemble(hdg_problem p, const hdg_solver_opts* opts, void* stream
     d.ld16 = p->ld16;
     d.r = p->d_r;
     assemble(d, s);
+    mark_uD_used(p, s);
     // FP64 products with several right-hand sides run on the tensor cores
     // from the blocks as exact digits (rebuilt with every assembly)
     p->kdig_ready = false;
@@ -2454,10 +2506,14 @@ hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* strea
   try {
     DeviceGuard dg(p->device);
     const int64_t n = p->NF * p->b * p->R;
-    if (!on_device && !p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * n);
-    double* full = on_device ? uhat : p->d_full;
+    double* mapped = on_device ? nullptr : mapped_host(uhat);
+    if (!on_device && !mapped && !p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * n);
+    double* full = on_device ? uhat : (mapped ? mapped : p->d_full);
     expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
-    if (!on_device) {
+    mark_uD_used(p, s);
+    if (mapped) {
+      CK(cudaStreamSynchronize(s));
+    } else if (!on_device) {
       CK(cudaMemcpyAsync(uhat, full, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
     }
@@ -2476,13 +2532,18 @@ hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void*
   try {
     DeviceGuard dg(p->device);
     const int64_t nu = p->NE * p->MPE * p->R, nq = p->NE * p->MDPE * p->R, nt = p->NF * p->b * p->R;
+    // host outputs in pinned, mapped memory are written by the kernel itself
+    double* mu = on_device ? nullptr : mapped_host(u);
+    double* mq = on_device ? nullptr : mapped_host(q);
+    const bool direct = on_device || (mu && mq);
     if (!p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * nt);
-    if (!on_device && !p->d_uout) p->d_uout = (double*)p->dalloc(sizeof(double) * nu);
-    if (!on_device && !p->d_qout) p->d_qout = (double*)p->dalloc(sizeof(double) * nq);
+    if (!direct && !p->d_uout) p->d_uout = (double*)p->dalloc(sizeof(double) * nu);
+    if (!direct && !p->d_qout) p->d_qout = (double*)p->dalloc(sizeof(double) * nq);
     double* full = p->d_full;
-    double* du = on_device ? u : p->d_uout;
-    double* dq = on_device ? q : p->d_qout;
+    double* du = on_device ? u : (direct ? mu : p->d_uout);
+    double* dq = on_device ? q : (direct ? mq : p->d_qout);
     expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
+    mark_uD_used(p, s);
     RecoverDesc d{};
     d.XF = p->d_XF;
     d.Xr = p->d_Xr;
@@ -2499,11 +2560,47 @@ hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void*
     d.n_elem = p->NE;
     d.u = du;
     d.q = dq;
-    recover(d, s);
-    CK(cudaGetLastError());
-    if (!on_device) {
-      CK(cudaMemcpyAsync(u, du, sizeof(double) * nu, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(q, dq, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+    // host outputs in pageable memory: the elements are recovered in pieces,
+    // and the copy stream brings each piece's u and q to the host while the
+    // next one is computed
+    const int64_t pieces = direct ? 1 : std::min<int64_t>(kRecoverPieces, p->NE / kRecoverPieceMin);
+    if (pieces < 2) {
+      recover(d, s);
+      CK(cudaGetLastError());
+      if (!direct) {
+        CK(cudaMemcpyAsync(u, du, sizeof(double) * nu, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(q, dq, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+      }
+    } else {
+      cudaStream_t cs = copy_stream_of(p);
+      const int64_t per = (p->NE + pieces - 1) / pieces;
+      const int64_t su = (int64_t)p->MPE * p->R, sq = (int64_t)p->MDPE * p->R, nlb = (int64_t)p->nl * p->b;
+      const int64_t sB = (int64_t)p->D * p->PE * p->PE, sC = (int64_t)p->D * p->PE * p->nl * p->PF;
+      // piece i's copies are issued after piece i+1's launch: a copy to
+      // pageable memory returns only when done, and the GPU keeps computing
+      auto copy_piece = [&](int64_t e0) {
+        const int64_t n = std::min(per, p->NE - e0);
+        CK(cudaMemcpyAsync(u + e0 * su, du + e0 * su, sizeof(double) * n * su, cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemcpyAsync(q + e0 * sq, dq + e0 * sq, sizeof(double) * n * sq, cudaMemcpyDeviceToHost, cs));
+      };
+      for (int64_t e0 = 0; e0 < p->NE; e0 += per) {
+        RecoverDesc c = d;
+        c.XF = d.XF + e0 * p->MPE * nlb;
+        c.Xr = d.Xr + e0 * su;
+        c.MinvB = d.MinvB + e0 * sB;
+        c.MinvC = d.MinvC + e0 * sC;
+        c.elem_face = d.elem_face + e0 * p->nl;
+        c.u = du + e0 * su;
+        c.q = dq + e0 * sq;
+        c.n_elem = std::min(per, p->NE - e0);
+        recover(c, s);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(event_of(p->ev_rec), s));
+        if (e0 > 0) copy_piece(e0 - per);
+        CK(cudaStreamWaitEvent(cs, p->ev_rec, 0));     // orders the next copy_piece after this piece
+      }
+      copy_piece((pieces_run(p->NE, per) - 1) * per);
+      CK(cudaStreamSynchronize(cs));
     }
     CK(cudaStreamSynchronize(s));
     return HDG_OK;

@@ -87,3 +87,41 @@ def test_fullsize_solve_and_recover(full, inner, rtol):
         scale_u = np.abs(blk['E'][e]).max() * np.abs(u[e]).max() + np.abs(blk['F'][e]).max() * np.abs(uh).max()
         assert np.abs(res_q).max() <= 1e-11 * scale_q
         assert np.abs(res_u).max() <= 1e-11 * scale_u
+
+
+def test_fullsize_recover_host_outputs_match_device(full):
+    """Host outputs of the trace and the recovery, both ways the library
+    writes them, equal the device outputs bit for bit on every element:
+    pageable buffers (recovery in 4 pieces of 1024 elements, each piece's
+    copies overlapping the next piece's kernel) and pinned buffers (written
+    by the kernels directly).  The Dirichlet values set from host memory on
+    the copy stream reach the trace: its Dirichlet rows equal u_D."""
+    import torch
+    from paper_2512_13619_gb300 import driver, _lib as L
+    w, p = full['w'], full['p']
+    o = driver.opts(restart=50, rtol=1e-10, pc='bj', inner='fp64', max_iters=5000)
+    p.set_dirichlet(full['uD'])
+    p.assemble(o)
+    p.setup_precond(o)
+    st, info = p.solve(o)
+    assert st == 0
+    u_h, q_h = p.recover()
+    u_d = torch.empty(u_h.shape, dtype=torch.float64, device='cuda')
+    q_d = torch.empty(q_h.shape, dtype=torch.float64, device='cuda')
+    driver.check(L.hdg_recover(p.h, u_d, q_d, 1, None), 'hdg_recover')
+    torch.cuda.synchronize()
+    assert np.array_equal(u_h, u_d.cpu().numpy())
+    assert np.array_equal(q_h, q_d.cpu().numpy())
+    u_p = torch.full(u_h.shape, np.nan, dtype=torch.float64).pin_memory()
+    q_p = torch.full(q_h.shape, np.nan, dtype=torch.float64).pin_memory()
+    driver.check(L.hdg_recover(p.h, u_p, q_p, 0, None), 'hdg_recover')
+    assert np.array_equal(u_h, u_p.numpy()) and np.array_equal(q_h, q_p.numpy())
+    tr = p.trace()
+    tr_p = torch.full(tr.shape, np.nan, dtype=torch.float64).pin_memory()
+    tr_d = torch.empty(tr.shape, dtype=torch.float64, device='cuda')
+    driver.check(L.hdg_get_trace(p.h, tr_p, 0, None), 'hdg_get_trace')
+    driver.check(L.hdg_get_trace(p.h, tr_d, 1, None), 'hdg_get_trace')
+    torch.cuda.synchronize()
+    assert np.array_equal(tr, tr_p.numpy()) and np.array_equal(tr, tr_d.cpu().numpy())
+    dir_rows = w.face_dirichlet.astype(bool)
+    assert np.array_equal(tr[dir_rows], np.asarray(full['uD']).reshape(tr.shape)[dir_rows])
