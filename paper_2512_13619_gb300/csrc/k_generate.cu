@@ -16,6 +16,7 @@
 //    ((v & 1 ? 1 : -1), (v & 2 ? 1 : -1), (v & 4 ? 1 : -1));
 //  - face_perm[e][l][j] = the local face-node index of element e's face l
 //    that carries the face's global node j.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -435,8 +436,8 @@ __global__ void hex_face_geom_kernel(HexGenDesc d) {
 }
 
 // The blocks of Eq. matrixform from the element integrals and the physics
-// tensors, one output entry per thread (grid-stride), written in the
-// row-major per-element layout of the condensation inputs:
+// tensors, written in the row-major per-element layout of the condensation
+// inputs:
 //   Cd[d][i][l PF + j]   = -EFN[l,d][i,j]
 //   D[(a,i),(b,c,k)]     = sum_d Cq[a,d,b,c] Sd[d][k][i]
 //   E[(a,i),(b,j)]       = -sum_d Cu[a,d,b] Sd[d][i][j] + tau d_ab Mf[i][j] + Rr[a,b] Me[i][j]
@@ -444,90 +445,137 @@ __global__ void hex_face_geom_kernel(HexGenDesc d) {
 //   G[(l,a,j),(b,c,k)]   = sum_d Cq[a,d,b,c] EFN[l,d][k,j]
 //   H[(l,a,j),(b,k)]     = tau d_ab EF[l][k,j]
 //   J[(l,a,j),(l',b,k)]  = d_ll' (sum_d Cu[a,d,b] FFN[l,d][k,j] - tau d_ab FF[l][k,j])
+// EF4 holds EF[l] and EFN[l,d] side by side per row (l, i): columns j, PF + j,
+// 2 PF + j, 3 PF + j; FF4 likewise per row (l, k).
+// One CTA per element (grid-stride), one warp per output row: the row's
+// indices are decoded once per warp, the columns' once per CTA into a
+// shared table (two ints per column), so the inner loop holds loads, three
+// FMAs and a coalesced store.
 template <int WHICH>
-__global__ void hex_expand_kernel(HexGenDesc d) {
+__global__ void __launch_bounds__(256) hex_expand_kernel(HexGenDesc d) {
+  extern __shared__ int2 ctab[];
   const int M = d.M, PE = d.PE, PF = d.PF, F4 = 4 * PF;
   const int MPE = M * PE, MDPE = 3 * MPE, nlb = 6 * M * PF;
-  int64_t per;
+  int nrows, ncols;
+  double* out;
   switch (WHICH) {
-    case 0: per = (int64_t)3 * PE * 6 * PF; break;
-    case 1: per = (int64_t)MPE * MDPE; break;
-    case 2: per = (int64_t)MPE * MPE; break;
-    case 3: per = (int64_t)MPE * nlb; break;
-    case 4: per = (int64_t)nlb * MDPE; break;
-    case 5: per = (int64_t)nlb * MPE; break;
-    default: per = (int64_t)nlb * nlb; break;
+    case 0: nrows = 3 * PE; ncols = 6 * PF; out = d.Cd; break;
+    case 1: nrows = MPE; ncols = MDPE; out = d.Dm; break;
+    case 2: nrows = MPE; ncols = MPE; out = d.Em; break;
+    case 3: nrows = MPE; ncols = nlb; out = d.Fm; break;
+    case 4: nrows = nlb; ncols = MDPE; out = d.Gm; break;
+    case 5: nrows = nlb; ncols = MPE; out = d.Hm; break;
+    default: nrows = nlb; ncols = nlb; out = d.Jm; break;
   }
-  const int64_t total = per * d.count;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    int2 t;
+    if (WHICH == 0) {                     // (l, j): offset of EFN[l,.][., j]
+      const int l = c / PF, j = c - l * PF;
+      t = make_int2(l * PE * F4 + j, 0);
+    } else if (WHICH == 1 || WHICH == 4) {   // (b c, k)
+      const int bc = c / PE, k = c - bc * PE;
+      t = make_int2(bc, WHICH == 1 ? k * PE : k * F4);
+    } else if (WHICH == 2 || WHICH == 5) {   // (b, k)
+      const int b = c / PE, k = c - b * PE;
+      t = make_int2(b, WHICH == 2 ? k : k * F4);
+    } else {                              // (l, b, j): l 256 + b and the table offset
+      const int lb = c / PF, j = c - lb * PF;
+      const int l = lb / M, b = lb - l * M;
+      t = make_int2((l << 8) | b, WHICH == 3 ? l * PE * F4 + j : j * F4);
+    }
+    ctab[c] = t;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t per = (int64_t)nrows * ncols;
   const double tau = d.tau;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = t / per;
-    const int64_t o = t - e * per;
+  for (int64_t e = blockIdx.x; e < d.count; e += gridDim.x) {
     const double* Me = d.Me + e * (int64_t)PE * PE;
     const double* Sd = d.Sd + e * (int64_t)3 * PE * PE;
     const double* Mf = d.Mf + e * (int64_t)PE * PE;
     const double* EF4 = d.EF4 + e * (int64_t)6 * PE * F4;
     const double* FF4 = d.FF4 + e * (int64_t)6 * PF * F4;
-    double v = 0.0;
-    if (WHICH == 0) {                                           // Cd
-      const int dd = (int)(o / (PE * 6 * PF));
-      const int rem = (int)(o - (int64_t)dd * PE * 6 * PF);
-      const int i = rem / (6 * PF), c = rem - i * 6 * PF;
-      const int l = c / PF, j = c - l * PF;
-      v = -EF4[((int64_t)l * PE + i) * F4 + (1 + dd) * PF + j];
-      d.Cd[e * per + o] = v;
-    } else if (WHICH == 1) {                                    // D
-      const int row = (int)(o / MDPE), col = (int)(o - (int64_t)row * MDPE);
-      const int a = row / PE, i = row - a * PE;
-      const int bc = col / PE, k = col - bc * PE;
-      const int b = bc / 3, c = bc - b * 3;
-      for (int dd = 0; dd < 3; ++dd) v += d.Cq[((a * 3 + dd) * M + b) * 3 + c] * Sd[((int64_t)dd * PE + k) * PE + i];
-      d.Dm[e * per + o] = v;
-    } else if (WHICH == 2) {                                    // E
-      const int row = (int)(o / MPE), col = (int)(o - (int64_t)row * MPE);
-      const int a = row / PE, i = row - a * PE;
-      const int b = col / PE, j = col - b * PE;
-      for (int dd = 0; dd < 3; ++dd) v -= d.Cu[(a * 3 + dd) * M + b] * Sd[((int64_t)dd * PE + i) * PE + j];
-      if (a == b) v += tau * Mf[i * PE + j];
-      v += d.Rr[a * M + b] * Me[i * PE + j];
-      d.Em[e * per + o] = v;
-    } else if (WHICH == 3) {                                    // F
-      const int row = (int)(o / nlb), col = (int)(o - (int64_t)row * nlb);
-      const int a = row / PE, i = row - a * PE;
-      const int lb = col / PF, j = col - lb * PF;
-      const int l = lb / M, b = lb - l * M;
-      const double* ef = EF4 + ((int64_t)l * PE + i) * F4;
-      for (int dd = 0; dd < 3; ++dd) v += d.Cu[(a * 3 + dd) * M + b] * ef[(1 + dd) * PF + j];
-      if (a == b) v -= tau * ef[j];
-      d.Fm[e * per + o] = v;
-    } else if (WHICH == 4) {                                    // G
-      const int row = (int)(o / MDPE), col = (int)(o - (int64_t)row * MDPE);
-      const int la = row / PF, j = row - la * PF;
-      const int l = la / M, a = la - l * M;
-      const int bc = col / PE, k = col - bc * PE;
-      const int b = bc / 3, c = bc - b * 3;
-      const double* ef = EF4 + ((int64_t)l * PE + k) * F4;
-      for (int dd = 0; dd < 3; ++dd) v += d.Cq[((a * 3 + dd) * M + b) * 3 + c] * ef[(1 + dd) * PF + j];
-      d.Gm[e * per + o] = v;
-    } else if (WHICH == 5) {                                    // H
-      const int row = (int)(o / MPE), col = (int)(o - (int64_t)row * MPE);
-      const int la = row / PF, j = row - la * PF;
-      const int l = la / M, a = la - l * M;
-      const int b = col / PE, k = col - b * PE;
-      if (a == b) v = tau * EF4[((int64_t)l * PE + k) * F4 + j];
-      d.Hm[e * per + o] = v;
-    } else {                                                    // J
-      const int row = (int)(o / nlb), col = (int)(o - (int64_t)row * nlb);
-      const int la = row / PF, j = row - la * PF;
-      const int l = la / M, a = la - l * M;
-      const int lb = col / PF, k = col - lb * PF;
-      const int l2 = lb / M, b = lb - l2 * M;
-      if (l == l2) {
-        const double* ff = FF4 + ((int64_t)l * PF + k) * F4;
-        for (int dd = 0; dd < 3; ++dd) v += d.Cu[(a * 3 + dd) * M + b] * ff[(1 + dd) * PF + j];
-        if (a == b) v -= tau * ff[j];
+    double* oe = out + e * per;
+    for (int r = warp; r < nrows; r += nw) {
+      double* orow = oe + (int64_t)r * ncols;
+      if (WHICH == 0) {
+        const int dd = r / PE, i = r - dd * PE;
+        const double* src = EF4 + i * F4 + (1 + dd) * PF;
+        for (int c = lane; c < ncols; c += 32) orow[c] = -src[ctab[c].x];
+      } else if (WHICH == 1) {
+        const int a = r / PE, i = r - a * PE;
+        const double* cq = d.Cq + a * 9 * M;
+        for (int c = lane; c < ncols; c += 32) {
+          const int2 t = ctab[c];
+          double v = 0.0;
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) v += cq[dd * 3 * M + t.x] * Sd[dd * PE * PE + t.y + i];
+          orow[c] = v;
+        }
+      } else if (WHICH == 2) {
+        const int a = r / PE, i = r - a * PE;
+        const double* cu = d.Cu + a * 3 * M;
+        for (int c = lane; c < ncols; c += 32) {
+          const int2 t = ctab[c];
+          const int b = t.x, j = t.y;
+          double v = 0.0;
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) v -= cu[dd * M + b] * Sd[(dd * PE + i) * PE + j];
+          if (a == b) v += tau * Mf[i * PE + j];
+          v += d.Rr[a * M + b] * Me[i * PE + j];
+          orow[c] = v;
+        }
+      } else if (WHICH == 3) {
+        const int a = r / PE, i = r - a * PE;
+        const double* cu = d.Cu + a * 3 * M;
+        for (int c = lane; c < ncols; c += 32) {
+          const int2 t = ctab[c];
+          const int b = t.x & 255;
+          const double* ef = EF4 + t.y + i * F4;
+          double v = 0.0;
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) v += cu[dd * M + b] * ef[(1 + dd) * PF];
+          if (a == b) v -= tau * ef[0];
+          orow[c] = v;
+        }
+      } else if (WHICH == 4) {
+        const int la = r / PF, j = r - la * PF;
+        const int l = la / M, a = la - l * M;
+        const double* cq = d.Cq + a * 9 * M;
+        const double* ef = EF4 + l * PE * F4 + j;
+        for (int c = lane; c < ncols; c += 32) {
+          const int2 t = ctab[c];
+          double v = 0.0;
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) v += cq[dd * 3 * M + t.x] * ef[t.y + (1 + dd) * PF];
+          orow[c] = v;
+        }
+      } else if (WHICH == 5) {
+        const int la = r / PF, j = r - la * PF;
+        const int l = la / M, a = la - l * M;
+        const double* ef = EF4 + l * PE * F4 + j;
+        for (int c = lane; c < ncols; c += 32) {
+          const int2 t = ctab[c];
+          orow[c] = (t.x == a) ? tau * ef[t.y] : 0.0;
+        }
+      } else {
+        const int la = r / PF, j = r - la * PF;
+        const int l = la / M, a = la - l * M;
+        const double* cu = d.Cu + a * 3 * M;
+        const double* ff = FF4 + l * PF * F4 + j;
+        for (int c = lane; c < ncols; c += 32) {
+          const int2 t = ctab[c];
+          const int l2 = t.x >> 8, b = t.x & 255;
+          double v = 0.0;
+          if (l2 == l) {
+            const double* f = ff + t.y;
+#pragma unroll
+            for (int dd = 0; dd < 3; ++dd) v += cu[dd * M + b] * f[(1 + dd) * PF];
+            if (a == b) v -= tau * f[0];
+          }
+          orow[c] = v;
+        }
       }
-      d.Jm[e * per + o] = v;
     }
   }
 }
@@ -541,8 +589,10 @@ int sm_count() {
 
 template <int W>
 void launch_expand(const HexGenDesc& d, cudaStream_t s) {
+  const int MPE = d.M * d.PE, cols_max = std::max(std::max(3 * MPE, 6 * d.M * d.PF), 6 * d.PF);
+  const int64_t grid = std::min<int64_t>(d.count, (int64_t)sm_count() * 8);
   count_launch();
-  hex_expand_kernel<W><<<sm_count() * 8, 256, 0, s>>>(d);
+  hex_expand_kernel<W><<<(unsigned)grid, 256, sizeof(int2) * (size_t)cols_max, s>>>(d);
 }
 
 }  // namespace
