@@ -449,11 +449,43 @@ __global__ void hex_face_geom_kernel(HexGenDesc d) {
 // 2 PF + j, 3 PF + j; FF4 likewise per row (l, k).
 // One CTA per element (grid-stride), one warp per output row: the row's
 // indices are decoded once per warp, the columns' once per CTA into a
-// shared table (two ints per column), so the inner loop holds loads, three
-// FMAs and a coalesced store.
+// shared table (two ints per column).  When they fit (kExpandStageMax), the
+// element's tables that the block needs are first copied into shared memory
+// with odd row strides (EF4/FF4 rows of 4 PF + 1, Sd rows of P_E + 1 for
+// even sizes), so that the gathers along the columns are free of bank
+// conflicts and no load waits behind a global store.
+constexpr int kExpandStageMax = 96 * 1024;
+
+// The nonzero terms of a physics coefficient over d for one (a, column
+// group): isotropic elasticity has at most one of the three Cq[a,d,b,c]
+// nonzero and Cu = 0, so most FP64 FMAs of the blocks can go.  The kept
+// terms run in increasing d, and a skipped term has an exact zero
+// coefficient, so the sums are the same as over all three.
+struct NzTerms {
+  double c[3];
+  int n;    // kept terms
+  int dd;   // their d, 2 bits each
+};
+__host__ __device__ inline int expand_groups(int which, int M) {
+  return (which == 1 || which == 4) ? 3 * M * M : (which == 2 || which == 3 || which == 6) ? M * M : 0;
+}
+
+__host__ __device__ inline int odd_up(int n) { return n | 1; }
+
+// doubles of the staged tables of block WHICH
+__host__ __device__ inline int expand_stage_doubles(int which, int M, int PE, int PF) {
+  const int fs = odd_up(4 * PF);
+  switch (which) {
+    case 1: return 3 * PE * odd_up(PE);
+    case 2: return 3 * PE * odd_up(PE) + 2 * PE * PE;
+    case 6: return 6 * PF * fs;
+    default: return 6 * PE * fs;
+  }
+}
+
 template <int WHICH>
-__global__ void __launch_bounds__(256) hex_expand_kernel(HexGenDesc d) {
-  extern __shared__ int2 ctab[];
+__global__ void __launch_bounds__(256) hex_expand_kernel(HexGenDesc d, int staged) {
+  extern __shared__ double smx[];
   const int M = d.M, PE = d.PE, PF = d.PF, F4 = 4 * PF;
   const int MPE = M * PE, MDPE = 3 * MPE, nlb = 6 * M * PF;
   int nrows, ncols;
@@ -467,25 +499,52 @@ __global__ void __launch_bounds__(256) hex_expand_kernel(HexGenDesc d) {
     case 5: nrows = nlb; ncols = MPE; out = d.Hm; break;
     default: nrows = nlb; ncols = nlb; out = d.Jm; break;
   }
+  int2* ctab = reinterpret_cast<int2*>(smx);
+  const int ngr = expand_groups(WHICH, M);
+  NzTerms* nz = reinterpret_cast<NzTerms*>(smx + ncols);
+  double* stg = smx + ncols + 4 * ngr;       // staged tables after the column and term tables
+  for (int g = threadIdx.x; g < ngr; g += blockDim.x) {
+    NzTerms z;
+    z.n = 0;
+    z.dd = 0;
+    for (int dd = 0; dd < 3; ++dd) {
+      double c;
+      if (WHICH == 1 || WHICH == 4) {        // g = a 3M + (b c): Cq[a][d][b c]
+        const int a = g / (3 * M), bc = g - a * 3 * M;
+        c = d.Cq[a * 9 * M + dd * 3 * M + bc];
+      } else {                               // g = a M + b: Cu[a][d][b]
+        const int a = g / M, b = g - a * M;
+        c = d.Cu[(a * 3 + dd) * M + b];
+      }
+      if (c != 0.0) {
+        z.c[z.n] = c;
+        z.dd |= dd << (2 * z.n);
+        ++z.n;
+      }
+    }
+    for (int q = z.n; q < 3; ++q) z.c[q] = 0.0;
+    nz[g] = z;
+  }
+  const int fs = staged ? odd_up(F4) : F4;   // row stride of EF4 / FF4
+  const int ss = staged ? odd_up(PE) : PE;   // row stride of Sd
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
     int2 t;
     if (WHICH == 0) {                     // (l, j): offset of EFN[l,.][., j]
       const int l = c / PF, j = c - l * PF;
-      t = make_int2(l * PE * F4 + j, 0);
+      t = make_int2(l * PE * fs + j, 0);
     } else if (WHICH == 1 || WHICH == 4) {   // (b c, k)
       const int bc = c / PE, k = c - bc * PE;
-      t = make_int2(bc, WHICH == 1 ? k * PE : k * F4);
+      t = make_int2(bc, WHICH == 1 ? k * ss : k * fs);
     } else if (WHICH == 2 || WHICH == 5) {   // (b, k)
       const int b = c / PE, k = c - b * PE;
-      t = make_int2(b, WHICH == 2 ? k : k * F4);
+      t = make_int2(b, WHICH == 2 ? k : k * fs);
     } else {                              // (l, b, j): l 256 + b and the table offset
       const int lb = c / PF, j = c - lb * PF;
       const int l = lb / M, b = lb - l * M;
-      t = make_int2((l << 8) | b, WHICH == 3 ? l * PE * F4 + j : j * F4);
+      t = make_int2((l << 8) | b, WHICH == 3 ? l * PE * fs + j : j * fs);
     }
     ctab[c] = t;
   }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int64_t per = (int64_t)nrows * ncols;
   const double tau = d.tau;
@@ -495,65 +554,100 @@ __global__ void __launch_bounds__(256) hex_expand_kernel(HexGenDesc d) {
     const double* Mf = d.Mf + e * (int64_t)PE * PE;
     const double* EF4 = d.EF4 + e * (int64_t)6 * PE * F4;
     const double* FF4 = d.FF4 + e * (int64_t)6 * PF * F4;
+    if (staged) {
+      __syncthreads();                       // the previous element's reads are done
+      if (WHICH == 1 || WHICH == 2) {
+        for (int x = threadIdx.x; x < 3 * PE * PE; x += blockDim.x) {
+          const int r = x / PE;
+          stg[r * ss + (x - r * PE)] = Sd[x];
+        }
+        if (WHICH == 2) {
+          double* sme = stg + 3 * PE * ss;
+          for (int x = threadIdx.x; x < PE * PE; x += blockDim.x) {
+            sme[x] = Me[x];
+            sme[PE * PE + x] = Mf[x];
+          }
+          Me = sme;
+          Mf = sme + PE * PE;
+        }
+        Sd = stg;
+      } else {
+        const double* src = (WHICH == 6) ? FF4 : EF4;
+        const int rows = (WHICH == 6) ? 6 * PF : 6 * PE;
+        for (int x = threadIdx.x; x < rows * F4; x += blockDim.x) {
+          const int r = x / F4;
+          stg[r * fs + (x - r * F4)] = src[x];
+        }
+        if (WHICH == 6) FF4 = stg; else EF4 = stg;
+      }
+    }
+    __syncthreads();                         // tables (and, first, the column table) ready
     double* oe = out + e * per;
     for (int r = warp; r < nrows; r += nw) {
       double* orow = oe + (int64_t)r * ncols;
       if (WHICH == 0) {
         const int dd = r / PE, i = r - dd * PE;
-        const double* src = EF4 + i * F4 + (1 + dd) * PF;
+        const double* src = EF4 + i * fs + (1 + dd) * PF;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) orow[c] = -src[ctab[c].x];
       } else if (WHICH == 1) {
         const int a = r / PE, i = r - a * PE;
-        const double* cq = d.Cq + a * 9 * M;
+        const NzTerms* za = nz + a * 3 * M;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) {
           const int2 t = ctab[c];
+          const NzTerms& z = za[t.x];
           double v = 0.0;
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) v += cq[dd * 3 * M + t.x] * Sd[dd * PE * PE + t.y + i];
+          for (int q = 0; q < z.n; ++q) v += z.c[q] * Sd[((z.dd >> (2 * q)) & 3) * PE * ss + t.y + i];
           orow[c] = v;
         }
       } else if (WHICH == 2) {
         const int a = r / PE, i = r - a * PE;
-        const double* cu = d.Cu + a * 3 * M;
+        const NzTerms* za = nz + a * M;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) {
           const int2 t = ctab[c];
           const int b = t.x, j = t.y;
+          const NzTerms& z = za[b];
           double v = 0.0;
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) v -= cu[dd * M + b] * Sd[(dd * PE + i) * PE + j];
+          for (int q = 0; q < z.n; ++q) v -= z.c[q] * Sd[(((z.dd >> (2 * q)) & 3) * PE + i) * ss + j];
           if (a == b) v += tau * Mf[i * PE + j];
-          v += d.Rr[a * M + b] * Me[i * PE + j];
+          const double rr = d.Rr[a * M + b];
+          if (rr != 0.0) v += rr * Me[i * PE + j];
           orow[c] = v;
         }
       } else if (WHICH == 3) {
         const int a = r / PE, i = r - a * PE;
-        const double* cu = d.Cu + a * 3 * M;
+        const NzTerms* za = nz + a * M;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) {
           const int2 t = ctab[c];
           const int b = t.x & 255;
-          const double* ef = EF4 + t.y + i * F4;
+          const NzTerms& z = za[b];
+          const double* ef = EF4 + t.y + i * fs;
           double v = 0.0;
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) v += cu[dd * M + b] * ef[(1 + dd) * PF];
+          for (int q = 0; q < z.n; ++q) v += z.c[q] * ef[(1 + ((z.dd >> (2 * q)) & 3)) * PF];
           if (a == b) v -= tau * ef[0];
           orow[c] = v;
         }
       } else if (WHICH == 4) {
         const int la = r / PF, j = r - la * PF;
         const int l = la / M, a = la - l * M;
-        const double* cq = d.Cq + a * 9 * M;
-        const double* ef = EF4 + l * PE * F4 + j;
+        const NzTerms* za = nz + a * 3 * M;
+        const double* ef = EF4 + l * PE * fs + j;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) {
           const int2 t = ctab[c];
+          const NzTerms& z = za[t.x];
           double v = 0.0;
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) v += cq[dd * 3 * M + t.x] * ef[t.y + (1 + dd) * PF];
+          for (int q = 0; q < z.n; ++q) v += z.c[q] * ef[t.y + (1 + ((z.dd >> (2 * q)) & 3)) * PF];
           orow[c] = v;
         }
       } else if (WHICH == 5) {
         const int la = r / PF, j = r - la * PF;
         const int l = la / M, a = la - l * M;
-        const double* ef = EF4 + l * PE * F4 + j;
+        const double* ef = EF4 + l * PE * fs + j;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) {
           const int2 t = ctab[c];
           orow[c] = (t.x == a) ? tau * ef[t.y] : 0.0;
@@ -561,16 +655,17 @@ __global__ void __launch_bounds__(256) hex_expand_kernel(HexGenDesc d) {
       } else {
         const int la = r / PF, j = r - la * PF;
         const int l = la / M, a = la - l * M;
-        const double* cu = d.Cu + a * 3 * M;
-        const double* ff = FF4 + l * PF * F4 + j;
+        const NzTerms* za = nz + a * M;
+        const double* ff = FF4 + l * PF * fs + j;
+#pragma unroll 4
         for (int c = lane; c < ncols; c += 32) {
           const int2 t = ctab[c];
           const int l2 = t.x >> 8, b = t.x & 255;
           double v = 0.0;
           if (l2 == l) {
+            const NzTerms& z = za[b];
             const double* f = ff + t.y;
-#pragma unroll
-            for (int dd = 0; dd < 3; ++dd) v += cu[dd * M + b] * f[(1 + dd) * PF];
+            for (int q = 0; q < z.n; ++q) v += z.c[q] * f[(1 + ((z.dd >> (2 * q)) & 3)) * PF];
             if (a == b) v -= tau * f[0];
           }
           orow[c] = v;
@@ -589,10 +684,16 @@ int sm_count() {
 
 template <int W>
 void launch_expand(const HexGenDesc& d, cudaStream_t s) {
-  const int MPE = d.M * d.PE, cols_max = std::max(std::max(3 * MPE, 6 * d.M * d.PF), 6 * d.PF);
+  const int MPE = d.M * d.PE, nlb = 6 * d.M * d.PF;
+  const int ncols = (W == 0) ? 6 * d.PF : (W == 1 || W == 4) ? 3 * MPE : (W == 2 || W == 5) ? MPE : nlb;
+  const size_t tab = sizeof(int2) * (size_t)ncols + sizeof(NzTerms) * (size_t)expand_groups(W, d.M);
+  const size_t stage = sizeof(double) * (size_t)expand_stage_doubles(W, d.M, d.PE, d.PF);
+  const int staged = (tab + stage <= (size_t)kExpandStageMax) ? 1 : 0;
+  const size_t smem = tab + (staged ? stage : 0);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(hex_expand_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t grid = std::min<int64_t>(d.count, (int64_t)sm_count() * 8);
   count_launch();
-  hex_expand_kernel<W><<<(unsigned)grid, 256, sizeof(int2) * (size_t)cols_max, s>>>(d);
+  hex_expand_kernel<W><<<(unsigned)grid, 256, smem, s>>>(d, staged);
 }
 
 }  // namespace
