@@ -293,6 +293,8 @@ __global__ void hex_vol_geom_kernel(HexGenDesc d) {
 // (X = A the values, or the derivatives D on one axis).  M^e takes W = w |det J|
 // with X = A; B_c[i,j] = int (grad phi_i)_c phi_j sums, over the axis b of the
 // derivative, the fields W_bc = w |det J| (J^{-1})_bc with D on axis b.
+// The 1D products X[q,i] A[q,j] are tabulated once per CTA, so each term is
+// one FP64 FMA (the same rounded product as computed in place).
 constexpr int kSfN1 = 5, kSfNQ = 8;
 template <int n1, int m>
 __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, const double* b1g, const double* d1g,
@@ -303,7 +305,9 @@ __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, con
   double* X8 = sm;                          // 24
   double* b1 = X8 + 24;                     // m x n1
   double* d1 = b1 + m * n1;                 // m x n1
-  double* geo = d1 + m * n1;                // nq x 10: w |det J| and w |det J| (J^{-1})_bc ([b][c])
+  double* Pb = d1 + m * n1;                 // m x n1 x n1: A[q,i] A[q,j]
+  double* Pd = Pb + m * n2;                 // m x n1 x n1: D[q,i] A[q,j]
+  double* geo = Pd + m * n2;                // nq x 10: w |det J| and w |det J| (J^{-1})_bc ([b][c])
   double* T1 = geo + nq * 10;               // 3 fields x m^2 x n2
   double* T2 = T1 + 3 * n2 * m * m;         // 3 fields x m x n2^2
   const int64_t e = blockIdx.x;
@@ -311,6 +315,11 @@ __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, con
   for (int i = threadIdx.x; i < m * n1; i += blockDim.x) {
     b1[i] = b1g[i];
     d1[i] = d1g[i];
+  }
+  for (int t = threadIdx.x; t < m * n2; t += blockDim.x) {
+    const int q = t / n2, i = (t / n1) % n1, j = t % n1;
+    Pb[t] = b1g[q * n1 + i] * b1g[q * n1 + j];
+    Pd[t] = d1g[q * n1 + i] * b1g[q * n1 + j];
   }
   __syncthreads();
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
@@ -335,13 +344,11 @@ __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, con
       const int ij1 = t % n2;
       const int r = t / n2;
       const int q2 = r % m, q3 = (r / m) % m, f = r / (m * m);
-      const int i1 = ij1 / n1, j1 = ij1 - i1 * n1;
-      const double* X = (pass > 0 && f == 0) ? d1 : b1;
+      const double* P = (pass > 0 && f == 0) ? Pd : Pb;
       const int wf = pass == 0 ? 0 : 1 + f * 3 + c;
       double acc = 0.0;
 #pragma unroll
-      for (int q1 = 0; q1 < m; ++q1)
-        acc += X[q1 * n1 + i1] * b1[q1 * n1 + j1] * geo[((q3 * m + q2) * m + q1) * 10 + wf];
+      for (int q1 = 0; q1 < m; ++q1) acc += P[q1 * n2 + ij1] * geo[((q3 * m + q2) * m + q1) * 10 + wf];
       T1[t] = acc;
     }
     __syncthreads();
@@ -350,12 +357,11 @@ __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, con
       const int ij1 = t % n2;
       const int r = t / n2;
       const int ij2 = r % n2, q3 = (r / n2) % m, f = r / (n2 * m);
-      const int i2 = ij2 / n1, j2 = ij2 - i2 * n1;
-      const double* X = (pass > 0 && f == 1) ? d1 : b1;
+      const double* P = (pass > 0 && f == 1) ? Pd : Pb;
       const double* t1 = T1 + (f * m + q3) * m * n2 + ij1;
       double acc = 0.0;
 #pragma unroll
-      for (int q2 = 0; q2 < m; ++q2) acc += X[q2 * n1 + i2] * b1[q2 * n1 + j2] * t1[q2 * n2];
+      for (int q2 = 0; q2 < m; ++q2) acc += P[q2 * n2 + ij2] * t1[q2 * n2];
       T2[t] = acc;
     }
     __syncthreads();
@@ -367,11 +373,12 @@ __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, con
       const int j3 = j / n2, j2 = (j / n1) % n1, j1 = j % n1;
       const int ij1 = i1 * n1 + j1, ij2 = i2 * n1 + j2;
       double acc = 0.0;
+      const int ij3 = i3 * n1 + j3;
       for (int f = 0; f < nf; ++f) {
-        const double* X = (pass > 0 && f == 2) ? d1 : b1;
+        const double* P = (pass > 0 && f == 2) ? Pd : Pb;
         const double* t2 = T2 + (f * m * n2 + ij2) * n2 + ij1;
 #pragma unroll
-        for (int q3 = 0; q3 < m; ++q3) acc += X[q3 * n1 + i3] * b1[q3 * n1 + j3] * t2[q3 * n2 * n2];
+        for (int q3 = 0; q3 < m; ++q3) acc += P[q3 * n2 + ij3] * t2[q3 * n2 * n2];
       }
       out[t] = acc;
     }
@@ -381,7 +388,8 @@ __global__ void __launch_bounds__(256) hex_mass_grad_sf_kernel(HexGenDesc d, con
 
 size_t sf_smem(int n1, int m) {
   const int n2 = n1 * n1;
-  return sizeof(double) * (24 + 2 * (size_t)m * n1 + (size_t)m * m * m * 10 + 3 * (size_t)n2 * m * m +
+  return sizeof(double) * (24 + 2 * (size_t)m * n1 + 2 * (size_t)m * n2 + (size_t)m * m * m * 10 +
+                           3 * (size_t)n2 * m * m +
                            3 * (size_t)n2 * n2 * m);
 }
 
