@@ -350,14 +350,27 @@ size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)
 // dimensions ldd / lds, batch strides sd / ss): one thread per entry over the
 // flattened (c, i, j) range, so consecutive threads move consecutive entries
 // of a row, whatever its width.
+// One CTA per matrix (grid-stride), one warp per row, the columns over the
+// lanes: no index divisions, coalesced rows.
 __global__ void copy_block_kernel(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss,
-                                  int rows, int cols, int64_t total) {
-  const int64_t per = (int64_t)rows * cols;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = t / per;
-    const int64_t rem = t - c * per;
-    const int64_t i = rem / cols, j = rem - i * cols;
-    dst[c * sd + i * ldd + j] = src[c * ss + i * lds + j];
+                                  int rows, int cols, int64_t count) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t c = blockIdx.x; c < count; c += gridDim.x) {
+    const double* sc = src + c * ss;
+    double* dc = dst + c * sd;
+    if (cols < 32) {                       // narrow blocks (right-hand-side columns): flat over the matrix
+      for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+        const int i = t / cols, j = t - i * cols;
+        dc[i * ldd + j] = sc[i * lds + j];
+      }
+      continue;
+    }
+    for (int i = warp; i < rows; i += nw) {
+      const double* sr = sc + i * lds;
+      double* dr = dc + i * ldd;
+#pragma unroll 4
+      for (int j = lane; j < cols; j += 32) dr[j] = sr[j];
+    }
   }
 }
 
@@ -366,10 +379,9 @@ __global__ void copy_block_kernel(double* dst, int64_t ldd, int64_t sd, const do
 void copy_block_f64(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss, int rows,
                     int cols, int64_t count, cudaStream_t s) {
   if (rows <= 0 || cols <= 0 || count <= 0) return;
-  const int64_t total = count * rows * cols;
-  const int64_t grid = std::min<int64_t>((total + 255) / 256, 4096);   // grid-stride beyond
+  const int64_t grid = std::min<int64_t>(count, 4096);   // grid-stride beyond
   count_launch();
-  copy_block_kernel<<<(unsigned)grid, 256, 0, s>>>(dst, ldd, sd, src, lds, ss, rows, cols, total);
+  copy_block_kernel<<<(unsigned)grid, 256, 0, s>>>(dst, ldd, sd, src, lds, ss, rows, cols, count);
 }
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {
