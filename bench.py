@@ -88,6 +88,9 @@ def parse():
                          'Newton with BJ, BJ-PP(10), ASM, ASM-PP(10) GMRES(50) to 1e-6)')
     ap.add_argument('--beam-cases', default='4:1,4:2,4:3,4:4,2:3,6:3,8:3',
                     help='n:k pairs of --workload beam (5n x n x n hexahedra, Q^k)')
+    ap.add_argument('--k32-config', default='',
+                    help='with --profile matvec3: run the FP32 product of K in this launch configuration '
+                         '(kind,slot parts,CTAs per SM, e.g. 8,1,32) instead of the tuned one')
     ap.add_argument('--profile', choices=['condense', 'matvec', 'solve-mixed', 'solve-fp64', 'generate', 'step3',
                                           'matvec3'],
                     default=None,
@@ -1440,6 +1443,11 @@ def run_profile(args):
             p.assemble(o16)
             p.setup_precond(o16)
             driver.check(L.hdg_autotune(p.h, 5, 0, None), 'autotune')
+            if args.k32_config:
+                # the FP32 product in a given launch configuration (kind, slot
+                # parts, CTAs per SM), e.g. the one tuned at another mesh size
+                cfg = [int(v) for v in args.k32_config.split(',')]
+                driver.check(L.hdg_set_tuning(p.h, 0, L.HDG_FP32, cfg), 'set_tuning')
             x = torch.randn(p.n_dof * w.R, dtype=torch.float64, device='cuda')
             y = torch.empty_like(x)
             torch.cuda.synchronize()
