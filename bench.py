@@ -696,6 +696,7 @@ def run_step3(args, ws, rank, local):
     kp = 2 if args.poly_prec == 'bf16' else 1
     _, t32, n32 = L.hdg_get_timing(p.h, 1)
     _, t16, n16 = L.hdg_get_timing(p.h, 2)
+    _, tbj, nbj = L.hdg_get_timing(p.h, 4)        # FP32 block-Jacobi applies of the polynomial
     L.hdg_set_timing(p.h, 0)
     # algorithmic bytes: the blocks, the FP32 x read, and the product written
     # in FP32 (the polynomial steps: 4 + 4 bytes per vector entry) or in FP64
@@ -721,6 +722,29 @@ def run_step3(args, ws, rank, local):
             'launches_in_step': int(n32 + n16), 'ms_in_step': round(tot_ms, 3),
             'timing': 'CUDA events around every block-row launch of K in one mixed step run launch by launch',
             'peak_source': 'MEASURED_PEAKS.json hbm_gbs' if not pk.get('_fallback') else 'fallback 6.8 TB/s'}
+
+    # the block-Jacobi applies of the same step: Chebyshev(4) is 5 applies per
+    # preconditioner application, each reading the FP32 diagonal blocks
+    # (stored columns padded to 16 bytes) and the FP32 input vector once;
+    # their epilogues read and write the FP32 recurrence vectors r, d, z:
+    # first apply writes 3 (16 bytes per entry with the input), the middle
+    # ones read and write 3 (28), the last reads 3 and writes the FP64 result
+    # (24)
+    deg = 4
+    pc_roof = None
+    if nbj > 0 and nbj % (deg + 1) == 0:
+        ents = p.n_dof * R
+        bj_blocks = p.n_dof * ((b + 3) // 4 * 4) * 4
+        by_app = (deg + 1) * bj_blocks + ents * (16 + 28 * (deg - 1) + 24)
+        pc_ach = by_app * (nbj // (deg + 1)) / tbj / 1e6
+        pc_roof = {'kernel': 'blockrow_vec_kernel (block-Jacobi apply z = D^-1 v, R = 8, FP32 blocks, Chebyshev '
+                             'recurrence in the epilogue)',
+                   'bound': 'hbm', 'achieved': round(pc_ach, 1), 'peak': pk['hbm_gbs'], 'unit': 'GB/s',
+                   'frac': round(pc_ach / pk['hbm_gbs'], 4), 'bytes_per_application': int(by_app),
+                   'launches_in_step': int(nbj), 'ms_in_step': round(tbj, 3),
+                   'timing': 'CUDA events around every block-Jacobi launch of the polynomial in one mixed step '
+                             'run launch by launch',
+                   'peak_source': roof['peak_source']}
 
     # end to end through the C ABI from pinned host buffers: vertices, face
     # permutations, load vectors and Dirichlet values in; trace, u and q out
@@ -775,6 +799,7 @@ def run_step3(args, ws, rank, local):
         'block_matvec': mv,
         'autotuned': tuning,
         'roofline': roof,
+        'precond_roofline': pc_roof,
         'gpu_launches': int(round(launches)),
         'clocks': clocks,
         'input_generation_s': round(t_in, 2),

@@ -359,7 +359,10 @@ hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n);
  *             polynomial steps) with blocks in precision HDG_FP64, HDG_FP32,
  *             HDG_BF16 (the block-row kernel only, not the FP32 copy of x);
  *   kind 3:   the tensor-core condensation products of hdg_condense (each
- *             the exponent pass plus the product kernel).
+ *             the exponent pass plus the product kernel);
+ *   kind 4-5: the block-Jacobi applies of the low-precision polynomial
+ *             preconditioner (each with the recurrence step in its
+ *             epilogue) with blocks in FP32, BF16.
  * The events are recorded on the caller's stream around each launch;
  * hdg_condense then synchronizes the stream to read them. */
 hdg_status hdg_set_timing(hdg_problem p, int enable);

@@ -189,8 +189,10 @@ struct hdg_problem_s {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  double t_mv_ms[4] = {0.0, 0.0, 0.0, 0.0};   // [0..2] matvec per precision, [3] tensor-core GEMMs
-  int64_t n_mv[4] = {0, 0, 0, 0};
+  // [0..2] matvec per precision, [3] tensor-core GEMMs, [4..5] block-Jacobi
+  // applies of the low-precision polynomial with FP32 / BF16 blocks
+  double t_mv_ms[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int64_t n_mv[6] = {0, 0, 0, 0, 0, 0};
   std::vector<int> ev_prec;
   int br_variant = 0;              // 1: bulk-copy staging for every block-row product
   int condense_mode = 1;           // condensation GEMMs: 1 tensor cores (digits split per tile), 2 digit
@@ -746,7 +748,9 @@ struct Ops {
       d.max_slots = 1;
       d.epi = EPI_POLY;
       d.pe = e;
+      timed_begin(p, s);
       blockrow(d, cfg_of(p, TUNE_BJ, prec), s);
+      timed_end(p, s, prec == HDG_FP32 ? 4 : 5);
     } else {
       d.blk = prec == HDG_FP32 ? (const void*)p->as32 : (const void*)p->as16;
       d.blk_stride = prec == HDG_FP32 ? p->as_s32 : p->as_s16;
@@ -2725,7 +2729,7 @@ hdg_status hdg_get_poly(hdg_problem p, double* re, double* im, int cap, int* n) 
 hdg_status hdg_set_timing(hdg_problem p, int enable) {
   if (!p) return HDG_ERR_ARG;
   p->timing = enable != 0;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 6; ++i) {
     p->t_mv_ms[i] = 0.0;
     p->n_mv[i] = 0;
   }
@@ -2735,7 +2739,7 @@ hdg_status hdg_set_timing(hdg_problem p, int enable) {
 }
 
 hdg_status hdg_get_timing(hdg_problem p, int kind, double* total_ms, int64_t* launches) {
-  if (!p || kind < 0 || kind > 3) return HDG_ERR_ARG;
+  if (!p || kind < 0 || kind > 5) return HDG_ERR_ARG;
   if (total_ms) *total_ms = p->t_mv_ms[kind];
   if (launches) *launches = p->n_mv[kind];
   return HDG_OK;
