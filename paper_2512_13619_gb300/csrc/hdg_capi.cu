@@ -1418,18 +1418,19 @@ cudaEvent_t event_of(cudaEvent_t& e) {
   if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return e;
 }
-// Device address of a caller's host buffer in pinned, mapped memory (the
-// kernels then write host outputs directly, their many warps taking the
-// translation misses of a buffer not touched for a while in parallel, where
-// a copy engine takes them one after another), or nullptr for pageable
-// memory.
-double* mapped_host(double* ptr) {
+// Device address of a caller's host buffer in pinned, mapped memory of the
+// problem's device (the kernels then write host outputs directly, their many
+// warps taking the translation misses of a buffer not touched for a while in
+// parallel, where a copy engine takes them one after another), or nullptr
+// for pageable memory and for memory pinned against another device.
+double* mapped_host(hdg_problem p, double* ptr) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
-  return a.type == cudaMemoryTypeHost ? static_cast<double*>(a.devicePointer) : nullptr;
+  if (a.type != cudaMemoryTypeHost || a.device != p->device) return nullptr;
+  return static_cast<double*>(a.devicePointer);
 }
 
 // Every stream operation that reads or writes the device copy of the
@@ -2510,7 +2511,7 @@ hdg_status hdg_get_trace(hdg_problem p, double* uhat, int on_device, void* strea
   try {
     DeviceGuard dg(p->device);
     const int64_t n = p->NF * p->b * p->R;
-    double* mapped = on_device ? nullptr : mapped_host(uhat);
+    double* mapped = on_device ? nullptr : mapped_host(p, uhat);
     if (!on_device && !mapped && !p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * n);
     double* full = on_device ? uhat : (mapped ? mapped : p->d_full);
     expand_trace(p->d_x, p->d_uhatD, p->d_free_of_face, p->NF, p->b, p->R, full, s);
@@ -2537,8 +2538,8 @@ hdg_status hdg_recover(hdg_problem p, double* u, double* q, int on_device, void*
     DeviceGuard dg(p->device);
     const int64_t nu = p->NE * p->MPE * p->R, nq = p->NE * p->MDPE * p->R, nt = p->NF * p->b * p->R;
     // host outputs in pinned, mapped memory are written by the kernel itself
-    double* mu = on_device ? nullptr : mapped_host(u);
-    double* mq = on_device ? nullptr : mapped_host(q);
+    double* mu = on_device ? nullptr : mapped_host(p, u);
+    double* mq = on_device ? nullptr : mapped_host(p, q);
     const bool direct = on_device || (mu && mq);
     if (!p->d_full) p->d_full = (double*)p->dalloc(sizeof(double) * nt);
     if (!direct && !p->d_uout) p->d_uout = (double*)p->dalloc(sizeof(double) * nu);
