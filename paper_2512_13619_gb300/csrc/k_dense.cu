@@ -347,11 +347,10 @@ __global__ void __launch_bounds__(kInvThreads) inverse_kernel(double* Aall, int 
 size_t inverse_smem(int n) { return (size_t)n * n * 8 + (size_t)n * 8 + (size_t)n * 4 + 16; }
 
 // dst[c][i][j] = src[c][i][j] for i < rows, j < cols (row-major, leading
-// dimensions ldd / lds, batch strides sd / ss): one thread per entry over the
-// flattened (c, i, j) range, so consecutive threads move consecutive entries
-// of a row, whatever its width.
-// One CTA per matrix (grid-stride), one warp per row, the columns over the
-// lanes: no index divisions, coalesced rows.
+// dimensions ldd / lds, batch strides sd / ss).  One CTA per matrix
+// (grid-stride), one warp per row, the columns over the lanes: no index
+// divisions, coalesced rows; blocks narrower than a warp go flat over the
+// matrix instead.
 __global__ void copy_block_kernel(double* dst, int64_t ldd, int64_t sd, const double* src, int64_t lds, int64_t ss,
                                   int rows, int cols, int64_t count) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
