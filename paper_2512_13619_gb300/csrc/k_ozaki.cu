@@ -179,14 +179,26 @@ __global__ void __launch_bounds__(256) ozaki_exponents_kernel(GemmDesc d, uint16
   const double* B = d.B + b0 * d.sB0 + b1 * d.sB1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   bool bad = false;
-  for (int r = warp; r < d.M; r += 8) {
-    int m = 0;
-    const double* row = A + (int64_t)r * d.lda;
-#pragma unroll 8
-    for (int k = lane; k < d.K; k += 32) m = max(m, exp_field(__ldg(row + k)));
-    bad |= (m == 0x7FF);
-    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
-    if (lane == 0) ea[(int64_t)z * d.M + r] = (uint16_t)m;
+  // rows r0, r0 + 8, r0 + 16, r0 + 24 per warp, their loads interleaved so
+  // that four rows' loads are in flight together
+  const int nk = (d.K + 31) / 32;
+  for (int r0 = warp; r0 < d.M; r0 += 32) {
+    int m[4] = {0, 0, 0, 0};
+    for (int j = 0; j < nk; ++j) {
+      const int k = j * 32 + lane;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 8 * u;
+        if (r < d.M && k < d.K) m[u] = max(m[u], exp_field(__ldg(A + (int64_t)r * d.lda + k)));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + 8 * u;
+      bad |= (m[u] == 0x7FF);
+      const int mm = (int)__reduce_max_sync(0xffffffffu, (unsigned)m[u]);
+      if (lane == 0 && r < d.M) ea[(int64_t)z * d.M + r] = (uint16_t)mm;
+    }
   }
   // columns in blocks of 64: thread (n, q) scans rows k = q, q + 4, ...
   for (int n0 = 0; n0 < d.N; n0 += 64) {
